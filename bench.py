@@ -1,0 +1,384 @@
+"""Benchmark of the guaranteed-error-bound quantizers on B300.
+
+One step = the quantize+verify sweep on the float32 512^3 sinusoid field
+(sum of 8 random 3-D sinusoids + N(0, 0.01)): ABS, REL and NOA at bounds 1e-2,
+1e-3, 1e-4 and 1e-5, i.e. 12 lcq_quantize calls (12 quantize kernels and 4
+NOA range kernels), outlier compaction included.  Throughput is input bytes
+per second (the paper's convention, Sec. 5), inputs resident in HBM; the
+input (512 MiB) is larger than L2 (126 MB), so no L2 flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle on the host cores on a bounded sample of
+the same workload.  Under torchrun every rank runs its own replica (the
+quantizer has no cross-rank data dependency; weak scaling) and the timing is
+the maximum over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "quantize+verify GB/s & % HBM peak; residual bits/value learned vs plain"
+BOUNDS = ["abs", "rel", "noa"]
+EBS = [1e-2, 1e-3, 1e-4, 1e-5]
+SHAPE = (512, 512, 512)
+WORKLOAD = ("quantize+verify sweep {ABS,REL,NOA} x eb {1e-2,1e-3,1e-4,1e-5} on a float32 "
+            "512^3 field (8 random 3-D sinusoids + N(0,0.01)), outlier compaction included")
+KERNEL_SOURCES = ["paper_2407_15037_b300/csrc/lcq_quant.cu", "paper_2407_15037_b300/csrc/lcq_device.cuh"]
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def ncu_traffic(name):
+    """DRAM bytes per launch recorded by an ncu capture, from the summary in
+    profiles/<name>.md (line 'traffic_bytes_per_launch: B kernel_src_sha: S');
+    None if absent or if the kernel sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", name + ".md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                parts = line.split()
+                b, sha = float(parts[1]), parts[3]
+                return b if sha == kernel_sha() else None
+    except (OSError, IndexError, ValueError):
+        return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device):
+    if world == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------ oracle arm --
+
+def oracle_sweep_seconds(xh, passes=None):
+    """Time the CPU oracle (single thread, as it stands) over the sweep."""
+    import oracle as O
+    t0 = time.perf_counter()
+    for bound in BOUNDS:
+        for eb in EBS:
+            c = O.consts(bound, xh.dtype, eb, x=xh)
+            O.quantize_with(c, xh)
+    return time.perf_counter() - t0
+
+
+def cpu_sample(n):
+    import synth
+    x = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device="cpu") \
+        if n >= np.prod(SHAPE) else synth.smooth_field((n,), dtype=torch.float32, seed=0)
+    return x.numpy()[:n]
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n = 1 << 21
+    xh = cpu_sample(n)
+    for _ in range(args.warmup):
+        oracle_sweep_seconds(xh)
+    t = 0.0
+    for _ in range(args.steps):
+        t += oracle_sweep_seconds(xh)
+    gbs = args.steps * len(BOUNDS) * len(EBS) * xh.nbytes / t / 1e9
+    sample = ("2^21 values of a 1-D float32 sinusoid field, the 12-pass sweep, per step; "
+              "oracle single-threaded")
+    line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_values": n},
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm --
+
+def run_ours(args, world, rank, local):
+    import paper_2407_15037_b300 as P
+    import synth
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    x = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device=dev)
+    n = x.numel()
+    q = P.alloc_outputs(n, x.dtype, dev)
+    ws = P.new_workspace(n, dev)
+
+    def step():
+        for bound in BOUNDS:
+            for eb in EBS:
+                P.quantize_into(x, bound, eb, q, ws, stream)
+
+    launches_per_step = len(BOUNDS) * len(EBS) + len(EBS)  # + NOA range kernels
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, world, dev)
+    bytes_step = len(BOUNDS) * len(EBS) * x.numel() * 4
+    value = world * args.steps * bytes_step / (ms / 1e3) / 1e9
+
+    # ---- per-call times (live, CUDA events on the launching stream) ----
+    per = {}
+    reps = 5
+    for bound in BOUNDS:
+        for eb in EBS:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                P.quantize_into(x, bound, eb, q, ws, stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            h = q.read_header()
+            t = a.elapsed_time(b) / reps / 1e3
+            per["%s_%g" % (bound, eb)] = {"ms": t * 1e3, "outliers": int(h.outlier_count),
+                                         "in_GBps": n * 4 / t / 1e9}
+    peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    # dominant kernel: k_quantize<float, ABS> (ABS and NOA calls, 8 of 12 per step)
+    abs_keys = ["abs_%g" % e for e in EBS]
+    t_abs = float(np.mean([per[k]["ms"] for k in abs_keys])) / 1e3
+    outl_abs = float(np.mean([per[k]["outliers"] for k in abs_keys]))
+    alg_bytes = n * (4 + 4) + (n + 31) // 32 * 4 + 4 * outl_abs  # in + bins + mask + payload
+    achieved = alg_bytes / t_abs / 1e9
+    traffic = ncu_traffic("k_quantize_f32_abs_512")
+    for k, v in per.items():
+        v["hbm_GBps"] = (n * 8 + (n + 31) // 32 * 4 + 4 * v["outliers"] +
+                         (n * 4 if k.startswith("noa") else 0)) / (v["ms"] / 1e3) / 1e9
+        v["pct_hbm_peak"] = 100 * v["hbm_GBps"] / hbm_peak
+
+    # ---- dequantize (device) ----
+    out = torch.empty_like(x)
+    dstat = torch.zeros(1, dtype=torch.int32, device=dev)
+    P.quantize_into(x, "abs", 1e-3, q, ws, stream)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P.dequantize_into(q, out, ws, dstat, stream)
+    a.record(stream)
+    for _ in range(reps):
+        P.dequantize_into(q, out, ws, dstat, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    t_deq = a.elapsed_time(b) / reps / 1e3
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if args.e2e_steps > 0:
+        xh = x.cpu().pin_memory()
+        outs = P.Quantized(torch.empty(n, dtype=torch.int32).pin_memory(),
+                           torch.empty((n + 31) // 32, dtype=torch.int32).pin_memory(),
+                           torch.empty(n, dtype=torch.int32).pin_memory(),
+                           torch.empty(P.lcq.HEADER_BYTES, dtype=torch.uint8).pin_memory(), n,
+                           x.dtype)
+        stage = torch.empty(P.host_stage_size(P.F32, n, n), dtype=torch.uint8, device=dev)
+        del q
+        d2h = 0
+
+        def e2e_step():
+            nonlocal d2h
+            d2h = 0
+            for bound in BOUNDS:
+                for eb in EBS:
+                    P.quantize_host(xh, bound, eb, outs, stage, ws, stream, dev)
+                    hdr = P.Header.from_buffer_copy(outs.header.numpy().tobytes())
+                    d2h += n * 4 + (n + 31) // 32 * 4 + P.lcq.HEADER_BYTES + 4 * hdr.outlier_count
+        e2e_step()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        te = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": world * args.e2e_steps * bytes_step / te / 1e9, "unit": "GB/s",
+               "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": int(d2h),
+               "steps": args.e2e_steps, "api": "lcq_quantize_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and args.cpu_baseline:
+        nb = 1 << 27
+        xs = x.reshape(-1)[:nb].cpu().numpy()
+        tc = oracle_sweep_seconds(xs)
+        cpu = {"value": len(BOUNDS) * len(EBS) * xs.nbytes / tc / 1e9, "unit": "GB/s", "cores": 1,
+               "kind": "oracle",
+               "sample": "first 2^27 values (half) of the same 512^3 field, the full 12-pass "
+                         "sweep, oracle single-threaded (%.1f s)" % tc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_values": n, "bound_types": BOUNDS, "bounds": EBS,
+                       "parallelism": "replicas x%d" % world,
+                       "l2": "inputs larger than L2 (512 MiB per pass vs 126 MB), no flush"},
+            "pct_hbm_peak_in": 100 * value / world / hbm_peak,
+            "roofline": {"bound": "hbm", "kernel": "k_quantize<float,ABS> (ABS/NOA calls)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "peak_source": peak_kind,
+                         "alg_bytes_per_launch": alg_bytes, "traffic": traffic,
+                         "avg_launch_ms": t_abs * 1e3},
+            "clocks": clocks,
+            "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "per_call": per,
+            "dequantize_f32_abs_1e-3": {"ms": t_deq * 1e3, "out_GBps": n * 4 / t_deq / 1e9},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_profile(args):
+    """A short, fixed sequence of calls for ncu captures: three warm-up calls
+    and one measured call of the chosen kind on the 512^3 float32 field."""
+    import paper_2407_15037_b300 as P
+    import synth
+    dev = torch.device("cuda", 0)
+    shape = SHAPE if args.profile_dtype == "f32" else (256, 256, 256)
+    dt = torch.float32 if args.profile_dtype == "f32" else torch.float64
+    x = synth.smooth_field(shape, dtype=dt, seed=0, device=dev)
+    q = P.alloc_outputs(x.numel(), x.dtype, dev)
+    ws = P.new_workspace(x.numel(), dev)
+    out = torch.empty_like(x)
+    kind = args.profile
+    if kind == "deq":
+        P.quantize_into(x, "abs", 1e-3, q, ws)
+    for _ in range(4):
+        if kind == "deq":
+            P.dequantize_into(q, out, ws)
+        else:
+            P.quantize_into(x, kind, 1e-3, q, ws)
+    torch.cuda.synchronize()
+    print("profile run done", kind, args.profile_dtype)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq"], default=None)
+    ap.add_argument("--profile-dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.profile:
+        run_profile(args)
+        return
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

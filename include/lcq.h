@@ -1,0 +1,183 @@
+/*
+ * lcq.h -- C ABI of liblcq.so: guaranteed-error-bound ABS / REL / NOA
+ * quantizers on NVIDIA B300 (sm_103a).
+ *
+ * The method is that of Fallin & Burtscher, "Lessons Learned on the Path to
+ * Guaranteeing the Error Bound in Lossy Quantizers" (arXiv 2407.15037):
+ *   - error-bound types ABS, REL and NOA as defined in Sec. 2.1.1-2.1.3;
+ *   - ABS quantization by multiplying with the inverse of twice the bound and
+ *     rounding to the nearest bin (Sec. 2.2);
+ *   - an immediate reconstruction of every value and a check against the
+ *     bound; values that fail are stored losslessly (Sec. 3.1);
+ *   - IEEE-754 operations only, no FMA contraction (Sec. 3.2);
+ *   - the bit-level log2/pow2 approximations for REL (Sec. 3.2);
+ *   - a two-sided bin-range test instead of abs() (Sec. 2.4, 3.3).
+ * Results are bit-identical to a plain CPU implementation of the same recipe.
+ *
+ * Conventions shared by every entry point
+ *   - Ownership: the caller allocates and owns every buffer; the library never
+ *     allocates device or host memory and never synchronises inside the
+ *     device-buffer entry points (they only enqueue work on `stream`).
+ *   - Pointers named d_* are device pointers, h_* host pointers.  Every device
+ *     array pointer must be 16-byte aligned (LCQ_ERR_ARG otherwise).
+ *   - Argument and bound errors are returned synchronously.  Errors found on
+ *     the device are OR-ed into a status word (lcq_header.status or the
+ *     d_status argument) as LCQ_STATUS_* bits; read them after the stream has
+ *     reached the call, e.g. with lcq_sync_status().
+ *   - A workspace (d_ws) must be zero-filled once before its first use
+ *     (lcq_workspace_init or cudaMemsetAsync); the kernels leave it ready for
+ *     the next call.  One workspace must not be used by two calls that can run
+ *     concurrently.  After a call that reported LCQ_STATUS_TIMEOUT, or a CUDA
+ *     error, re-initialise the workspace.
+ *   - n = 0 is legal.
+ *
+ * Compressed representation of an array of n values of type T (float or double):
+ *   bins     int32[n]      quantization bins; 0 where the value is an outlier.
+ *                          ABS/NOA: the bin b; REL: 2*b + signbit(x).
+ *   mask     uint32[ceil(n/32)]  bit (i & 31) of word (i >> 5) is 1 iff value i
+ *                          is an outlier; unused bits of the last word are 0.
+ *   outliers T-sized raw bit patterns of the outliers, in ascending index
+ *                          order (NaN payloads and the sign of zero preserved).
+ *   header   lcq_header    the exact constants used, so the decoder
+ *                          reconstructs exactly what the encoder verified.
+ */
+#ifndef LCQ_H
+#define LCQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { LCQ_F32 = 0, LCQ_F64 = 1 } lcq_dtype;
+
+/* Error-bound types, Sec. 2.1: point-wise absolute (ABS), relative (REL) and
+ * normalised absolute (NOA, the ABS bound eb * (max - min)). */
+typedef enum { LCQ_ABS = 0, LCQ_REL = 1, LCQ_NOA = 2 } lcq_bound_type;
+
+typedef enum {
+    LCQ_OK = 0,
+    LCQ_ERR_ARG = 1,       /* null/misaligned pointer, bad enum, size too large */
+    LCQ_ERR_BOUND = 2,     /* eb <= 0, NaN or Inf; ABS/REL: derived constants not finite-normal */
+    LCQ_ERR_CAPACITY = 3,  /* more outliers than outlier_capacity (device-side) */
+    LCQ_ERR_TIMEOUT = 4,   /* a bounded wait in the outlier scan gave up (device-side) */
+    LCQ_ERR_CUDA = 5,      /* a CUDA launch or copy failed */
+    LCQ_ERR_WORKSPACE = 6, /* workspace smaller than lcq_workspace_size() */
+    LCQ_ERR_HEADER = 7     /* header does not describe the arrays given to the decoder */
+} lcq_status;
+
+/* Device-side status bits (lcq_header.status, dequantize d_status). */
+#define LCQ_STATUS_CAPACITY 1u
+#define LCQ_STATUS_TIMEOUT 2u
+#define LCQ_STATUS_HEADER 4u
+
+#define LCQ_MAGIC 0x3151434Cu /* "LCQ1" */
+
+/* Quantizer header, written to device memory by lcq_quantize.  Float
+ * constants are stored as raw bits (a float's bits in the low 32 bits). */
+typedef struct lcq_header {
+    uint32_t magic;         /* LCQ_MAGIC */
+    uint32_t dtype;         /* lcq_dtype */
+    uint32_t bound_type;    /* lcq_bound_type */
+    uint32_t mode;          /* 0: quantized; 1: every value stored as an outlier
+                               (NOA without a usable range) */
+    uint64_t n;             /* number of values */
+    double eb;              /* the bound passed by the caller */
+    double range;           /* NOA: R = RD(max - min) over the finite values, else 0 */
+    double eb_abs;          /* ABS: eb; NOA: RD(eb * R); REL: 0 */
+    uint64_t ebT_bits;      /* ABS/NOA: eb_T = RD_T(eb_abs); REL: RD_T(eb) */
+    uint64_t scale_bits;    /* ABS/NOA: eb2 = 2 eb_T; REL: log-domain step */
+    uint64_t inv_bits;      /* ABS/NOA: RN_T(1 / eb2); REL: RN_T(1 / step) */
+    uint64_t chk_bits;      /* REL: acceptance factor RN_T(eb_T (1 - 2^-p)); else 0 */
+    uint64_t outlier_count; /* total outliers (complete even past capacity) */
+    uint32_t status;        /* OR of LCQ_STATUS_* */
+    uint32_t reserved;
+} lcq_header;
+
+/* Bytes of workspace needed by lcq_quantize / lcq_dequantize for n values. */
+size_t lcq_workspace_size(lcq_dtype dtype, lcq_bound_type bound_type, uint64_t n);
+
+/* Zero-fill a workspace on `stream` (needed once before first use). */
+lcq_status lcq_workspace_init(void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Quantize and verify n values (Sec. 2.1-3.3).
+ *   dtype, bound_type, eb  the problem as the paper states it: data type, bound
+ *                          type and bound (ABS: |x - x'| <= eb; REL:
+ *                          |x|/(1+eb) <= |x'| <= |x|(1+eb) with the sign kept;
+ *                          NOA: |x - x'| <= eb * (max - min) over finite x).
+ *   d_in         T[n]      input values.
+ *   d_bins       int32[n]  output bins.
+ *   d_mask       uint32[ceil(n/32)] output outlier mask.
+ *   d_outliers   T[outlier_capacity] output outlier bit patterns.  Writes stop
+ *                          at the capacity; header.outlier_count is complete and
+ *                          LCQ_STATUS_CAPACITY is set if it exceeds the capacity.
+ *   d_hdr        lcq_header* output header (device memory).
+ *   d_ws, ws_bytes         workspace of at least lcq_workspace_size(...) bytes.
+ * Each value becomes either a bin whose reconstruction was verified against
+ * the bound with the exact IEEE operations the decoder uses, or an outlier
+ * (NaN, Inf, values whose bin is out of range, values that fail the check;
+ * for REL also zeros and denormals).  Stream-ordered; no host synchronisation.
+ * Returns LCQ_ERR_BOUND synchronously for an unusable ABS/REL bound; a NOA
+ * range that gives no usable bound makes every value an outlier instead.
+ */
+lcq_status lcq_quantize(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* d_in,
+                        uint64_t n, int32_t* d_bins, uint32_t* d_mask, void* d_outliers,
+                        uint64_t outlier_capacity, lcq_header* d_hdr, void* d_ws, size_t ws_bytes,
+                        cudaStream_t stream);
+
+/*
+ * Reconstruct n values from a header written by lcq_quantize (the decoder of
+ * Sec. 3.1, without a double-check, Sec. 6): x'_i is the outlier bit pattern
+ * if mask bit i is set, else bin_i * eb2 (ABS/NOA) or the pow2 approximation
+ * of the stored log-domain bin with the stored sign (REL).  dtype and n must
+ * match the header; if they do not, d_status gets LCQ_STATUS_HEADER and
+ * d_out is not written.  d_status (uint32, device) may be NULL.
+ */
+lcq_status lcq_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
+                          const int32_t* d_bins, const uint32_t* d_mask, const void* d_outliers,
+                          void* d_out, uint32_t* d_status, void* d_ws, size_t ws_bytes,
+                          cudaStream_t stream);
+
+/* Synchronise `stream`, read d_hdr->status and map it to an lcq_status
+ * (LCQ_ERR_TIMEOUT before LCQ_ERR_CAPACITY before LCQ_ERR_HEADER).
+ * Optionally returns the outlier count.  This one does block the host. */
+lcq_status lcq_sync_status(const lcq_header* d_hdr, uint64_t* h_outlier_count,
+                           cudaStream_t stream);
+
+/* Static description of a status code. */
+const char* lcq_status_string(lcq_status status);
+
+/*
+ * End-to-end form for host-resident data: copies h_in to the device, runs
+ * lcq_quantize, and copies bins, mask, header and the outliers back into
+ * the host buffers; returns once everything is back on the host (it
+ * synchronises `stream`).  d_stage is a device buffer of at least
+ * lcq_host_stage_size(dtype, n, outlier_capacity) bytes (caller-owned).
+ * For full copy bandwidth the host buffers should be page-locked.
+ */
+size_t lcq_host_stage_size(lcq_dtype dtype, uint64_t n, uint64_t outlier_capacity);
+lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double eb,
+                             const void* h_in, uint64_t n, int32_t* h_bins, uint32_t* h_mask,
+                             void* h_outliers, uint64_t outlier_capacity, lcq_header* h_hdr,
+                             void* d_stage, size_t stage_bytes, void* d_ws, size_t ws_bytes,
+                             cudaStream_t stream);
+
+/*
+ * Test hook for the bounded waits of the outlier scan (no counterpart in the
+ * paper).  spin_limit: maximum polls of one predecessor's scan descriptor
+ * before the wait gives up with LCQ_STATUS_TIMEOUT (0 restores the default,
+ * about one second).  drop_tile: index of a tile that does not publish its
+ * descriptor, so that its successor's wait runs out (UINT64_MAX: none).
+ * Affects subsequent launches from this process.
+ */
+void lcq_debug_set_scan(uint32_t spin_limit, uint64_t drop_tile);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCQ_H */

@@ -1,0 +1,322 @@
+// lcq_device.cuh -- device-side building blocks of liblcq: per-value quantize /
+// verify / reconstruct recipes (one IEEE operation per step, explicit
+// round-to-nearest intrinsics, so nothing can be contracted into an FMA), the
+// workspace layout, and the bounded decoupled-lookback scan used to compact
+// outliers in index order.
+//
+// Method: Fallin & Burtscher, arXiv 2407.15037.  ABS bin (Sec. 2.2), the
+// reconstruct-and-check step (Sec. 3.1), IEEE-only arithmetic (Sec. 3.2), the
+// log2/pow2 approximations for REL (Sec. 3.2), the two-sided bin-range test
+// (Sec. 3.3).  Points the paper leaves open are settled as follows:
+//   rounding to a bin is round-half-even; the range test |q| < maxbin runs on
+//   the floating-point q before any integer conversion; maxbin = 2^30 for
+//   ABS/NOA and 2^29 for REL; for float32 data the ABS threshold is the
+//   largest float not above the user's double bound; REL treats zero,
+//   denormals, Inf and NaN as outliers and accepts a reconstruction m of
+//   a = |x| iff m/2 <= a <= 2m and |a - m| * sc <= RN(RN(min(a, m) * sc) * chk)
+//   with that product normal, chk = RN(eb_T (1 - 2^-p)) and sc an exact
+//   power-of-two rescale for tiny values; the REL bin stores 2b + signbit.
+#pragma once
+
+#include <cfloat>
+#include <cstdint>
+
+#include "../../include/lcq.h"
+
+namespace lcq {
+
+constexpr int32_t kMaxBinAbs = 1 << 30;
+constexpr int32_t kMaxBinRel = 1 << 29;
+
+// ---------------------------------------------------------------------------
+// Type traits: every arithmetic step is a single correctly rounded IEEE op.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Ty;
+
+template <>
+struct Ty<float> {
+    using U = uint32_t;
+    static constexpr int kP = 23;
+    static constexpr int kBias = 127;
+    static constexpr U kExpAll = 0xFFu;
+    static constexpr U kMant = 0x007FFFFFu;
+    static constexpr U kOneBits = 0x3F800000u;
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ int32_t rint_i(float a) { return __float2int_rn(a); }
+    static __device__ __forceinline__ int64_t trunc_i(float a) { return __float2int_rz(a); }
+    static __device__ __forceinline__ float from_i(int32_t a) { return __int2float_rn(a); }
+    static __device__ __forceinline__ float from_i64(int64_t a) { return __int2float_rn((int)a); }
+    static __device__ __forceinline__ U bits(float a) { return __float_as_uint(a); }
+    static __device__ __forceinline__ float from_bits(U u) { return __uint_as_float(u); }
+    static __device__ __forceinline__ float fabs_(float a) { return fabsf(a); }
+    static __device__ __forceinline__ float nmin() { return FLT_MIN; }
+    static __device__ __forceinline__ float one_minus_ulp() { return 0x1.fffffcp-1f; }  // 1 - 2^-23
+    static __device__ __forceinline__ float tiny() { return 0x1p-62f; }
+    static __device__ __forceinline__ float rescale() { return 0x1p64f; }
+    static __device__ __forceinline__ float top_bb() { return 255.0f; }
+    static __device__ __forceinline__ float bias_f() { return 127.0f; }
+};
+
+template <>
+struct Ty<double> {
+    using U = uint64_t;
+    static constexpr int kP = 52;
+    static constexpr int kBias = 1023;
+    static constexpr U kExpAll = 0x7FFull;
+    static constexpr U kMant = 0x000FFFFFFFFFFFFFull;
+    static constexpr U kOneBits = 0x3FF0000000000000ull;
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ int32_t rint_i(double a) { return __double2int_rn(a); }
+    static __device__ __forceinline__ int64_t trunc_i(double a) { return __double2ll_rz(a); }
+    static __device__ __forceinline__ double from_i(int32_t a) { return __int2double_rn(a); }
+    static __device__ __forceinline__ double from_i64(int64_t a) { return __ll2double_rn(a); }
+    static __device__ __forceinline__ U bits(double a) { return (U)__double_as_longlong(a); }
+    static __device__ __forceinline__ double from_bits(U u) { return __longlong_as_double((long long)u); }
+    static __device__ __forceinline__ double fabs_(double a) { return fabs(a); }
+    static __device__ __forceinline__ double nmin() { return DBL_MIN; }
+    static __device__ __forceinline__ double one_minus_ulp() { return 0x1.ffffffffffffep-1; }  // 1 - 2^-52
+    static __device__ __forceinline__ double tiny() { return 0x1p-511; }
+    static __device__ __forceinline__ double rescale() { return 0x1p512; }
+    static __device__ __forceinline__ double top_bb() { return 2047.0; }
+    static __device__ __forceinline__ double bias_f() { return 1023.0; }
+};
+
+// Constants of one quantization, in the data type.
+template <typename T>
+struct Consts {
+    T ebT;     // ABS/NOA: threshold eb_T; REL: eb_T
+    T scale;   // ABS/NOA: eb2; REL: step
+    T inv;     // ABS/NOA: 1/eb2; REL: 1/step
+    T chk;     // REL acceptance factor
+    uint32_t all_outliers;
+};
+
+template <typename T>
+__device__ __forceinline__ Consts<T> consts_from_header(const lcq_header* h) {
+    using U = typename Ty<T>::U;
+    Consts<T> c;
+    c.ebT = Ty<T>::from_bits((U)h->ebT_bits);
+    c.scale = Ty<T>::from_bits((U)h->scale_bits);
+    c.inv = Ty<T>::from_bits((U)h->inv_bits);
+    c.chk = Ty<T>::from_bits((U)h->chk_bits);
+    c.all_outliers = h->mode;
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Per-value recipes
+// ---------------------------------------------------------------------------
+
+// ABS / NOA: bin = rint(x * inv) (Sec. 2.2); reconstruct and check (Sec. 3.1);
+// two-sided range test (Sec. 3.3).  Returns false for an outlier.
+template <typename T>
+__device__ __forceinline__ bool abs_quant(T x, const Consts<T>& c, int32_t& bin) {
+    using F = Ty<T>;
+    const T q = F::mul(x, c.inv);
+    if (!(F::fabs_(q) < T(kMaxBinAbs))) return false;
+    const int32_t b = F::rint_i(q);
+    if ((b >= kMaxBinAbs) || (b <= -kMaxBinAbs)) return false;
+    const T recon = F::mul(F::from_i(b), c.scale);
+    if (!(F::fabs_(F::sub(x, recon)) <= c.ebT)) return false;
+    bin = b;
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T abs_recon(int32_t bin, const Consts<T>& c) {
+    return Ty<T>::mul(Ty<T>::from_i(bin), c.scale);
+}
+
+// log2approx (Sec. 3.2): one addition of the float 1.mantissa and E - (bias+1).
+template <typename T>
+__device__ __forceinline__ T log2approx(typename Ty<T>::U u) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const int32_t E = (int32_t)((u >> F::kP) & F::kExpAll);
+    const T one_frac = F::from_bits(F::kOneBits | (u & F::kMant));
+    return F::add(one_frac, F::from_i(E - (F::kBias + 1)));
+}
+
+// pow2approx (Sec. 3.2) of bb = RN(Lr + bias), bb in [1, 2 bias + 1):
+// 2^(k - bias) (1 + bb - k), k = floor(bb).
+template <typename T>
+__device__ __forceinline__ typename Ty<T>::U pow2approx_bits(T bb) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const int64_t k = F::trunc_i(bb);
+    const T fr = F::sub(bb, F::from_i64(k - 1));
+    return ((U)k << F::kP) | (F::bits(fr) & F::kMant);
+}
+
+// REL: returns false for an outlier; the stored bin is 2b + signbit.
+template <typename T>
+__device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const U u = F::bits(x);
+    const U E = (u >> F::kP) & F::kExpAll;
+    if (E == 0 || E == F::kExpAll) return false;  // zero, denormal, Inf, NaN
+    const U sign_bit = u >> (sizeof(U) * 8 - 1);
+    const T a = F::from_bits(u & ~((U)1 << (sizeof(U) * 8 - 1)));
+    const T L = log2approx<T>(u);
+    const T q = F::mul(L, c.inv);
+    if (!(F::fabs_(q) < T(kMaxBinRel))) return false;
+    const int32_t b = F::rint_i(q);
+    if ((b >= kMaxBinRel) || (b <= -kMaxBinRel)) return false;
+    const T Lr = F::mul(F::from_i(b), c.scale);
+    const T bb = F::add(Lr, F::bias_f());
+    if (!(bb >= T(1) && bb < F::top_bb())) return false;
+    const T m = F::from_bits(pow2approx_bits<T>(bb));
+    if (!(a <= F::mul(T(2), m) && m <= F::mul(T(2), a))) return false;
+    const T d = F::fabs_(F::sub(a, m));  // exact (Sterbenz)
+    const T lo = (a < m) ? a : m;
+    const T sc = (lo < F::tiny()) ? F::rescale() : T(1);
+    const T t = F::mul(F::mul(lo, sc), c.chk);
+    if (!(t >= F::nmin())) return false;
+    if (!(F::mul(d, sc) <= t)) return false;
+    bin = (int32_t)(((uint32_t)b << 1) | (uint32_t)sign_bit);
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T rel_recon(int32_t bin, const Consts<T>& c) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const U s = (U)(bin & 1);
+    const int32_t b = bin >> 1;  // arithmetic shift: (bin - s) / 2
+    const T Lr = F::mul(F::from_i(b), c.scale);
+    const T bb = F::add(Lr, F::bias_f());
+    return F::from_bits(pow2approx_bits<T>(bb) | (s << (sizeof(U) * 8 - 1)));
+}
+
+// ---------------------------------------------------------------------------
+// Workspace and bounded decoupled lookback
+// ---------------------------------------------------------------------------
+
+// Workspace layout: a 256-byte head, then one 64-bit scan descriptor per tile
+// of the largest chunk, then per-block partials of the range reduction.
+struct WsHead {
+    uint32_t ticket;  // next tile index (dynamic, so predecessors are resident)
+    uint32_t done;    // CTAs finished; the last one resets ticket/done
+    uint32_t epoch;   // launch counter; descriptors of older launches are stale
+    uint32_t err;     // LCQ_STATUS_* bits gathered during one launch
+    uint64_t carry;   // running outlier count across chunks (decoder)
+};
+
+constexpr size_t kWsHeadBytes = 256;
+constexpr int kMinmaxMaxBlocks = 1184;  // 8 x 148
+constexpr size_t kMinmaxPartialBytes = (size_t)kMinmaxMaxBlocks * 2 * sizeof(uint64_t);
+
+// Descriptor: [63:62] state (1 aggregate, 2 inclusive prefix), [61:32] epoch,
+// [31:0] count.  A chunk holds at most 2^31 values, so counts fit 32 bits.
+constexpr uint32_t kEpochMask = 0x3FFFFFFFu;
+constexpr uint64_t kStAgg = 1ull << 62;
+constexpr uint64_t kStPre = 2ull << 62;
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Scan parameters shared by the kernels that compact in index order.
+struct ScanCfg {
+    uint32_t spin_limit;  // polls before a wait gives up
+    uint64_t drop_tile;   // test hook: this tile never publishes
+};
+
+// Called by all 32 lanes of one warp.  Publishes the tile's aggregate, walks
+// back over predecessors (32 at a time) until an inclusive prefix is found,
+// publishes the tile's inclusive prefix and returns its exclusive prefix.
+// Every wait is bounded: after cfg.spin_limit polls a missing predecessor is
+// counted as 0 and LCQ_STATUS_TIMEOUT is raised, so the scan always ends.
+__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t* desc, uint32_t tile, uint32_t agg,
+                                                       uint32_t epoch, const ScanCfg& cfg,
+                                                       uint32_t* err) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t tag = (uint64_t)(epoch & kEpochMask) << 32;
+    const bool publish = (uint64_t)tile != cfg.drop_tile;
+    if (tile == 0) {
+        if (lane == 0 && publish) st_relaxed_u64(&desc[0], kStPre | tag | agg);
+        return 0;
+    }
+    if (lane == 0 && publish) st_relaxed_u64(&desc[tile], kStAgg | tag | agg);
+    uint32_t excl = 0;
+    int64_t pos = (int64_t)tile - 1 - lane;
+    bool timed_out = false;
+    while (true) {
+        uint32_t spins = 0;
+        unsigned ns = 32;
+        uint32_t state, val;
+        while (true) {
+            if (pos >= 0) {
+                const uint64_t d = ld_relaxed_u64(&desc[pos]);
+                const bool fresh = (uint32_t)((d >> 32) & kEpochMask) == (epoch & kEpochMask);
+                state = fresh ? (uint32_t)(d >> 62) : 0u;
+                val = fresh ? (uint32_t)d : 0u;
+            } else {
+                state = 2u;  // before tile 0: an empty prefix
+                val = 0u;
+            }
+            if (!__any_sync(FULL, state == 0u)) break;
+            if (++spins > cfg.spin_limit) {
+                timed_out = true;
+                if (state == 0u) { state = 2u; val = 0u; }
+                break;
+            }
+            __nanosleep(ns);
+            ns = ns < 1024u ? ns * 2u : 1024u;
+        }
+        const uint32_t pmask = __ballot_sync(FULL, state == 2u);
+        if (pmask) {
+            const int first = __ffs(pmask) - 1;
+            excl += __reduce_add_sync(FULL, lane <= first ? val : 0u);
+            break;
+        }
+        excl += __reduce_add_sync(FULL, val);
+        pos -= 32;
+    }
+    if (lane == 0) {
+        if (publish) st_relaxed_u64(&desc[tile], kStPre | tag | (uint32_t)(excl + agg));
+        if (timed_out) atomicOr(err, LCQ_STATUS_TIMEOUT);
+    }
+    return excl;
+}
+
+// End-of-launch bookkeeping, called by thread 0 of every CTA after its last
+// global write: the last CTA to finish hands the gathered error bits to
+// *status_out (assigning on the first chunk of a call, OR-ing later) and
+// resets the ticket for the next launch on this workspace.
+__device__ __forceinline__ void finish_launch(WsHead* ws, uint32_t epoch, uint32_t* status_out,
+                                              bool assign) {
+    __threadfence();
+    const uint32_t prev = atomicAdd(&ws->done, 1u);
+    if (prev == gridDim.x - 1) {
+        __threadfence();
+        const uint32_t e = atomicExch(&ws->err, 0u);
+        if (status_out) {
+            if (assign) *status_out = e;
+            else atomicOr(status_out, e);
+        }
+        atomicExch(&ws->ticket, 0u);
+        atomicExch(&ws->done, 0u);
+        atomicExch(&ws->epoch, epoch + 1u);
+        __threadfence();
+    }
+}
+
+}  // namespace lcq

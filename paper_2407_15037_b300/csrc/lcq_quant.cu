@@ -1,0 +1,893 @@
+// lcq_quant.cu -- single-array quantize / verify / compact, NOA range
+// reduction and dequantize kernels, and the C-ABI entry points declared in
+// include/lcq.h.
+//
+// Data path of one lcq_quantize call (Fallin & Burtscher, arXiv 2407.15037):
+//   [NOA only] k_minmax: finite min/max (ordered-integer keys, warp + block
+//       reductions, per-block partials, last block combines) -> R, eb*R and
+//       the ABS constants, written to the header in device memory (Sec. 2.1.3).
+//   k_quantize: each CTA takes a tile of TILE values by atomic ticket, loads
+//       them with 128-bit loads, computes bin, reconstruction and the bound
+//       check per value (Sec. 2.2, 3.1-3.3), stores the bins with 128-bit
+//       stores, builds the tile's outlier mask with warp shuffles, scans the
+//       mask popcounts and runs a bounded decoupled lookback over the tiles
+//       to place the tile's outliers in ascending index order.
+// k_dequantize mirrors it: the same lookback over mask popcounts gives each
+// tile's payload offset; values are reconstructed with the encoder's exact
+// operations (Sec. 3.1, no double-check on decode, Sec. 6).
+//
+// Arrays longer than kChunk values are processed as several launches; the
+// running outlier count carries from one chunk to the next in device memory,
+// so a call never waits on the host.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include <cuda_runtime.h>
+
+#include "lcq_device.cuh"
+
+namespace lcq {
+
+constexpr int kBlock = 256;
+constexpr int kVpt = 4;                         // 4-value vectors per thread
+constexpr int kTile = kBlock * kVpt * 4;        // values per tile (4096)
+constexpr int kWords = kTile / 32;              // mask words per tile (128)
+constexpr int kWpl = kWords / 32;               // mask words per lane of warp 0
+constexpr uint64_t kChunk = 1ull << 31;         // values per launch at most
+constexpr uint32_t kDefaultSpin = 1u << 20;     // ~1 s of polling with backoff
+
+static_assert(kWords % 32 == 0, "tile must give whole mask words per lane");
+
+static ScanCfg g_scan = {kDefaultSpin, ~0ull};
+
+// ---------------------------------------------------------------------------
+// Vector access helpers: 4 consecutive values per thread per step.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Vec4;
+
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void load_cached(const float* p, float v[4]) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float v[4]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+};
+
+template <>
+struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4]) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void load_cached(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(double* p, const double v[4]) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Quantize kernel
+// ---------------------------------------------------------------------------
+template <typename T>
+struct QParams {
+    const T* in;          // chunk start
+    int32_t* bins;        // chunk start
+    uint32_t* mask;       // chunk start (chunk offsets are multiples of 32)
+    typename Ty<T>::U* out;
+    uint64_t cap;
+    lcq_header* hdr;
+    WsHead* ws;
+    uint64_t* desc;
+    uint64_t n;           // values in this chunk
+    uint32_t num_tiles;
+    uint32_t first_chunk;
+    uint32_t consts_from_hdr;  // NOA: constants written by k_minmax
+    Consts<T> c;
+    ScanCfg scan;
+    // header fields (written by tile 0 of the first chunk)
+    uint32_t dtype, bound;
+    double eb, eb_abs;
+    uint64_t n_total;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    __shared__ uint32_t s_mask[kWords];
+    __shared__ uint32_t s_wpre[kWords];
+    __shared__ uint32_t s_tile, s_epoch, s_excl;
+    __shared__ uint64_t s_base;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_tile = atomicAdd(&p.ws->ticket, 1u);
+        s_epoch = ld_relaxed_u32(&p.ws->epoch);
+        s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.hdr->outlier_count);
+    }
+    const Consts<T> c = p.consts_from_hdr ? consts_from_header<T>(p.hdr) : p.c;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t tbase = (uint64_t)tile * kTile;
+
+    U vals[kVpt][4];
+    uint32_t nib[kVpt];
+#pragma unroll
+    for (int v = 0; v < kVpt; v++) {
+        const uint64_t e0 = tbase + (uint64_t)v * (kBlock * 4) + (uint64_t)tid * 4;
+        T x[4];
+        const bool full = e0 + 4 <= p.n;
+        if (full) {
+            Vec4<T>::load(p.in + e0, x);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++) x[k] = (e0 + k < p.n) ? p.in[e0 + k] : T(0);
+        }
+        int32_t b[4];
+        uint32_t nb = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int32_t bin = 0;
+            bool ok = false;
+            if (!c.all_outliers) ok = (MODE == LCQ_REL) ? rel_quant<T>(x[k], c, bin) : abs_quant<T>(x[k], c, bin);
+            if (!ok && e0 + k < p.n) nb |= 1u << k;
+            b[k] = ok ? bin : 0;
+            vals[v][k] = F::bits(x[k]);
+        }
+        if (full) {
+            __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(b[0], b[1], b[2], b[3]));
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (e0 + k < p.n) p.bins[e0 + k] = b[k];
+        }
+        uint32_t w = nb << ((lane & 7) * 4);
+        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
+        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
+        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
+        if ((lane & 7) == 0) s_mask[v * (kBlock / 8) + warp * 4 + (lane >> 3)] = w;
+        nib[v] = nb;
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        uint32_t wv[kWpl];
+        uint32_t cnt = 0, loc[kWpl];
+#pragma unroll
+        for (int j = 0; j < kWpl; j++) {
+            wv[j] = s_mask[lane * kWpl + j];
+            loc[j] = cnt;
+            cnt += __popc(wv[j]);
+        }
+        // mask words of this tile -> global (16-byte stores)
+        const uint64_t nwords = (p.n + 31) / 32;
+        const uint64_t gw = (uint64_t)tile * kWords + (uint64_t)lane * kWpl;
+        if (gw + kWpl <= nwords) {
+            __stcs(reinterpret_cast<uint4*>(p.mask + gw), make_uint4(wv[0], wv[1], wv[2], wv[3]));
+        } else {
+#pragma unroll
+            for (int j = 0; j < kWpl; j++)
+                if (gw + j < nwords) p.mask[gw + j] = wv[j];
+        }
+        // inclusive warp scan of per-lane counts
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t ex = incl - cnt;
+#pragma unroll
+        for (int j = 0; j < kWpl; j++) s_wpre[lane * kWpl + j] = ex + loc[j];
+        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const uint32_t excl = lookback_exclusive(p.desc, tile, agg, s_epoch, p.scan, &p.ws->err);
+        if (lane == 0) {
+            s_excl = excl;
+            if (tile == p.num_tiles - 1) {
+                const uint64_t total = s_base + excl + agg;
+                st_relaxed_u64(&p.hdr->outlier_count, total);
+                if (total > p.cap) atomicOr(&p.ws->err, LCQ_STATUS_CAPACITY);
+            }
+        }
+    }
+    __syncthreads();
+
+    const uint64_t pbase = s_base + s_excl;
+#pragma unroll
+    for (int v = 0; v < kVpt; v++) {
+        if (nib[v]) {
+            const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
+            const uint32_t mw = s_mask[word];
+            const uint32_t pre = s_wpre[word];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if ((nib[v] >> k) & 1u) {
+                    const int bit = (lane & 7) * 4 + k;
+                    const uint64_t rank = pbase + pre + __popc(mw & ((1u << bit) - 1u));
+                    if (rank < p.cap) p.out[rank] = vals[v][k];
+                }
+            }
+        }
+    }
+
+    if (tid == 0) {
+        if (tile == 0 && p.first_chunk) {
+            lcq_header* h = p.hdr;
+            h->magic = LCQ_MAGIC;
+            h->dtype = p.dtype;
+            h->bound_type = p.bound;
+            h->n = p.n_total;
+            h->eb = p.eb;
+            if (!p.consts_from_hdr) {
+                h->mode = 0;
+                h->range = 0.0;
+                h->eb_abs = p.eb_abs;
+                h->ebT_bits = (uint64_t)F::bits(p.c.ebT);
+                h->scale_bits = (uint64_t)F::bits(p.c.scale);
+                h->inv_bits = (uint64_t)F::bits(p.c.inv);
+                h->chk_bits = (uint64_t)F::bits(p.c.chk);
+            }
+            h->reserved = 0;
+        }
+        finish_launch(p.ws, s_epoch, &p.hdr->status, p.first_chunk != 0);
+    }
+}
+
+// Header for an empty input (no tiles to launch).
+__global__ void k_header_empty(lcq_header* h, uint32_t dtype, uint32_t bound, double eb,
+                               double eb_abs, uint64_t ebT, uint64_t scale, uint64_t inv,
+                               uint64_t chk, uint32_t mode) {
+    h->magic = LCQ_MAGIC;
+    h->dtype = dtype;
+    h->bound_type = bound;
+    h->mode = mode;
+    h->n = 0;
+    h->eb = eb;
+    h->range = 0.0;
+    h->eb_abs = eb_abs;
+    h->ebT_bits = ebT;
+    h->scale_bits = scale;
+    h->inv_bits = inv;
+    h->chk_bits = chk;
+    h->outlier_count = 0;
+    h->status = 0;
+    h->reserved = 0;
+}
+
+// ---------------------------------------------------------------------------
+// NOA range reduction (Sec. 2.1.3): finite-only min/max as ordered integer
+// keys; the last block derives R = RD(max - min), eb_abs = RD(eb * R) and the
+// ABS constants, and writes them to the header.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ typename Ty<T>::U order_key(typename Ty<T>::U u) {
+    using U = typename Ty<T>::U;
+    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
+    return (u & sign) ? ~u : (u | sign);
+}
+template <typename T>
+__device__ __forceinline__ typename Ty<T>::U key_to_bits(typename Ty<T>::U k) {
+    using U = typename Ty<T>::U;
+    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
+    return (k & sign) ? (k & ~sign) : ~k;
+}
+
+template <typename T>
+__device__ __forceinline__ void minmax_accum(T x, typename Ty<T>::U& lo, typename Ty<T>::U& hi) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const U u = F::bits(x);
+    if (((u >> F::kP) & F::kExpAll) == F::kExpAll) return;  // Inf / NaN
+    const U k = order_key<T>(u);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+}
+
+template <typename T>
+struct MParams {
+    const T* in;
+    uint64_t n;
+    lcq_header* hdr;
+    WsHead* ws;
+    uint64_t* partial;  // 2 per block
+    double eb;
+};
+
+template <typename T>
+__device__ void noa_finalize(lcq_header* h, bool any, T mn, T mx, double eb) {
+    using F = Ty<T>;
+    uint32_t mode = 1;
+    double R = 0.0, eb_abs = 0.0;
+    uint64_t ebT_b = 0, eb2_b = 0, inv_b = 0;
+    if (any) {
+        R = __dsub_rd((double)mx, (double)mn);
+        eb_abs = __dmul_rd(eb, R);
+        if (sizeof(T) == 4) {
+            const float ebT = __double2float_rd(eb_abs);
+            const float eb2 = __fmul_rn(2.0f, ebT);
+            const float inv = __fdiv_rn(1.0f, eb2);
+            const bool ok = (ebT >= FLT_MIN && ebT <= FLT_MAX) && (eb2 <= FLT_MAX) &&
+                            (inv >= FLT_MIN && inv <= FLT_MAX);
+            if (ok) {
+                mode = 0;
+                ebT_b = __float_as_uint(ebT);
+                eb2_b = __float_as_uint(eb2);
+                inv_b = __float_as_uint(inv);
+            }
+        } else {
+            const double ebT = eb_abs;
+            const double eb2 = __dmul_rn(2.0, ebT);
+            const double inv = __ddiv_rn(1.0, eb2);
+            const bool ok = (ebT >= DBL_MIN && ebT <= DBL_MAX) && (eb2 <= DBL_MAX) &&
+                            (inv >= DBL_MIN && inv <= DBL_MAX);
+            if (ok) {
+                mode = 0;
+                ebT_b = (uint64_t)__double_as_longlong(ebT);
+                eb2_b = (uint64_t)__double_as_longlong(eb2);
+                inv_b = (uint64_t)__double_as_longlong(inv);
+            }
+        }
+    }
+    h->mode = mode;
+    h->range = R;
+    h->eb_abs = eb_abs;
+    h->ebT_bits = ebT_b;
+    h->scale_bits = eb2_b;
+    h->inv_bits = inv_b;
+    h->chk_bits = 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_minmax(MParams<T> p) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    __shared__ U s_lo[kBlock / 32], s_hi[kBlock / 32];
+    __shared__ bool s_last;
+    U lo = ~(U)0, hi = (U)0;
+    const uint64_t nvec = p.n / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * kBlock;
+    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < nvec; i += stride) {
+        T x[4];
+        Vec4<T>::load_cached(p.in + 4 * i, x);
+#pragma unroll
+        for (int k = 0; k < 4; k++) minmax_accum<T>(x[k], lo, hi);
+    }
+    if (blockIdx.x == 0 && threadIdx.x < (p.n & 3)) minmax_accum<T>(p.in[nvec * 4 + threadIdx.x], lo, hi);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const U a = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const U b = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBlock / 32; w++) {
+            lo = s_lo[w] < lo ? s_lo[w] : lo;
+            hi = s_hi[w] > hi ? s_hi[w] : hi;
+        }
+        p.partial[2 * blockIdx.x] = (uint64_t)lo;
+        p.partial[2 * blockIdx.x + 1] = (uint64_t)hi;
+        __threadfence();
+        s_last = atomicAdd(&p.ws->done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last block: combine the partials of all blocks
+    __threadfence();
+    lo = ~(U)0;
+    hi = (U)0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kBlock) {
+        const U a = (U)ld_relaxed_u64(&p.partial[2 * b]);
+        const U c = (U)ld_relaxed_u64(&p.partial[2 * b + 1]);
+        lo = a < lo ? a : lo;
+        hi = c > hi ? c : hi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const U a = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const U b = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+        lo = a < lo ? a : lo;
+        hi = b > hi ? b : hi;
+    }
+    __syncthreads();
+    if (lane == 0) { s_lo[warp] = lo; s_hi[warp] = hi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kBlock / 32; w++) {
+            lo = s_lo[w] < lo ? s_lo[w] : lo;
+            hi = s_hi[w] > hi ? s_hi[w] : hi;
+        }
+        const bool any = lo <= hi;
+        const T mn = F::from_bits(key_to_bits<T>(lo));
+        const T mx = F::from_bits(key_to_bits<T>(hi));
+        noa_finalize<T>(p.hdr, any, mn, mx, p.eb);
+        atomicExch(&p.ws->done, 0u);
+        __threadfence();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dequantize kernel
+// ---------------------------------------------------------------------------
+template <typename T>
+struct DParams {
+    const int32_t* bins;
+    const uint32_t* mask;
+    const typename Ty<T>::U* outl;
+    T* out;
+    const lcq_header* hdr;
+    WsHead* ws;
+    uint64_t* desc;
+    uint32_t* status;
+    uint64_t n;           // values in this chunk
+    uint64_t n_total;
+    uint32_t dtype;
+    uint32_t num_tiles;
+    uint32_t first_chunk;
+    ScanCfg scan;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    __shared__ uint32_t s_mask[kWords];
+    __shared__ uint32_t s_wpre[kWords];
+    __shared__ uint32_t s_tile, s_epoch, s_excl, s_ok;
+    __shared__ uint64_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_tile = atomicAdd(&p.ws->ticket, 1u);
+        s_epoch = ld_relaxed_u32(&p.ws->epoch);
+        s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.ws->carry);
+        // decode only a complete, error-free encoding of exactly these arrays
+        const bool ok = p.hdr->magic == LCQ_MAGIC && p.hdr->dtype == p.dtype &&
+                        p.hdr->n == p.n_total && p.hdr->status == 0u &&
+                        (p.outl != nullptr || p.hdr->outlier_count == 0);
+        s_ok = ok;
+        if (!ok) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
+    }
+    const Consts<T> c = consts_from_header<T>(p.hdr);
+    const bool rel = p.hdr->bound_type == LCQ_REL;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const uint64_t tbase = (uint64_t)tile * kTile;
+    if (warp == 0) {
+        const uint64_t nwords = (p.n + 31) / 32;
+        const uint64_t gw = (uint64_t)tile * kWords + (uint64_t)lane * kWpl;
+        uint32_t wv[kWpl];
+        if (gw + kWpl <= nwords) {
+            const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p.mask + gw));
+            wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < kWpl; j++) wv[j] = (gw + j < nwords) ? p.mask[gw + j] : 0u;
+        }
+        uint32_t cnt = 0, loc[kWpl];
+#pragma unroll
+        for (int j = 0; j < kWpl; j++) {
+            s_mask[lane * kWpl + j] = wv[j];
+            loc[j] = cnt;
+            cnt += __popc(wv[j]);
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t ex = incl - cnt;
+#pragma unroll
+        for (int j = 0; j < kWpl; j++) s_wpre[lane * kWpl + j] = ex + loc[j];
+        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const uint32_t excl = lookback_exclusive(p.desc, tile, agg, s_epoch, p.scan, &p.ws->err);
+        if (lane == 0) {
+            s_excl = excl;
+            if (tile == p.num_tiles - 1) st_relaxed_u64(&p.ws->carry, s_base + excl + agg);
+        }
+    }
+    __syncthreads();
+    if (s_ok) {
+        const uint64_t pbase = s_base + s_excl;
+        const uint64_t avail = p.hdr->outlier_count;
+        bool overrun = false;
+#pragma unroll
+        for (int v = 0; v < kVpt; v++) {
+            const uint64_t e0 = tbase + (uint64_t)v * (kBlock * 4) + (uint64_t)tid * 4;
+            if (e0 >= p.n) continue;
+            const bool full = e0 + 4 <= p.n;
+            int32_t b[4];
+            if (full) {
+                const int4 a = __ldcs(reinterpret_cast<const int4*>(p.bins + e0));
+                b[0] = a.x; b[1] = a.y; b[2] = a.z; b[3] = a.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) b[k] = (e0 + k < p.n) ? p.bins[e0 + k] : 0;
+            }
+            const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
+            const uint32_t mw = s_mask[word];
+            const uint32_t nb = (mw >> ((lane & 7) * 4)) & 0xFu;
+            T x[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if ((nb >> k) & 1u) {
+                    const int bit = (lane & 7) * 4 + k;
+                    const uint64_t rank = pbase + s_wpre[word] + __popc(mw & ((1u << bit) - 1u));
+                    if (rank < avail) {
+                        x[k] = F::from_bits(p.outl[rank]);
+                    } else {  // mask has more bits than the header's count
+                        x[k] = T(0);
+                        overrun = true;
+                    }
+                } else {
+                    x[k] = rel ? rel_recon<T>(b[k], c) : abs_recon<T>(b[k], c);
+                }
+            }
+            if (full) {
+                Vec4<T>::store(p.out + e0, x);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (e0 + k < p.n) p.out[e0 + k] = x[k];
+            }
+        }
+        if (overrun) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
+    }
+    __syncthreads();
+    if (tid == 0) finish_launch(p.ws, s_epoch, p.status, p.first_chunk != 0);
+}
+
+__global__ void k_status_only(uint32_t* status, uint32_t bits) {
+    if (status) *status = bits;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+static uint64_t tiles_for(uint64_t n) { return (n + kTile - 1) / kTile; }
+
+static size_t desc_bytes(uint64_t n) {
+    const uint64_t per_chunk = n < kChunk ? n : kChunk;
+    return (size_t)(tiles_for(per_chunk) * sizeof(uint64_t));
+}
+
+static size_t ws_size(uint64_t n) {
+    size_t d = desc_bytes(n);
+    d = (d + 255) & ~(size_t)255;
+    return kWsHeadBytes + d + kMinmaxPartialBytes;
+}
+
+// RD_f32(d): the largest float not above d.
+static float rd_f32_host(double d) {
+    float f = (float)d;
+    if ((double)f > d) f = nextafterf(f, -INFINITY);
+    return f;
+}
+
+static bool is_normal_f(float f) { return std::fpclassify(f) == FP_NORMAL; }
+static bool is_normal_d(double f) { return std::fpclassify(f) == FP_NORMAL; }
+
+// ABS constants (Sec. 2.2): eb_T = RD_T(eb), eb2 = 2 eb_T, inv = RN(1/eb2).
+template <typename T>
+static bool abs_consts_host(double eb, Consts<T>& c);
+
+template <>
+bool abs_consts_host<float>(double eb, Consts<float>& c) {
+    const float ebT = rd_f32_host(eb);
+    if (!is_normal_f(ebT)) return false;
+    const float eb2 = 2.0f * ebT;
+    if (!std::isfinite(eb2)) return false;
+    const float inv = 1.0f / eb2;
+    if (!is_normal_f(inv)) return false;
+    c.ebT = ebT; c.scale = eb2; c.inv = inv; c.chk = 0.0f; c.all_outliers = 0;
+    return true;
+}
+
+template <>
+bool abs_consts_host<double>(double eb, Consts<double>& c) {
+    const double ebT = eb;
+    if (!is_normal_d(ebT)) return false;
+    const double eb2 = 2.0 * ebT;
+    if (!std::isfinite(eb2)) return false;
+    const double inv = 1.0 / eb2;
+    if (!is_normal_d(inv)) return false;
+    c.ebT = ebT; c.scale = eb2; c.inv = inv; c.chk = 0.0; c.all_outliers = 0;
+    return true;
+}
+
+// REL constants: log-domain half step lb = RN(e / RN(1 + e)), step = 2 lb,
+// inv = RN(1/step), acceptance factor chk = RN(e (1 - 2^-p)), e = RD_T(eb).
+template <typename T>
+static bool rel_consts_host(double eb, Consts<T>& c);
+
+template <>
+bool rel_consts_host<float>(double eb, Consts<float>& c) {
+    const float e = rd_f32_host(eb);
+    if (!is_normal_f(e)) return false;
+    const float onep = 1.0f + e;
+    const float lb = e / onep;
+    const float step = 2.0f * lb;
+    const float inv = 1.0f / step;
+    const float chk = e * 0x1.fffffcp-1f;
+    if (!is_normal_f(lb) || !is_normal_f(step) || !is_normal_f(inv) || !is_normal_f(chk)) return false;
+    c.ebT = e; c.scale = step; c.inv = inv; c.chk = chk; c.all_outliers = 0;
+    return true;
+}
+
+template <>
+bool rel_consts_host<double>(double eb, Consts<double>& c) {
+    const double e = eb;
+    if (!is_normal_d(e)) return false;
+    const double onep = 1.0 + e;
+    const double lb = e / onep;
+    const double step = 2.0 * lb;
+    const double inv = 1.0 / step;
+    const double chk = e * 0x1.ffffffffffffep-1;
+    if (!is_normal_d(lb) || !is_normal_d(step) || !is_normal_d(inv) || !is_normal_d(chk)) return false;
+    c.ebT = e; c.scale = step; c.inv = inv; c.chk = chk; c.all_outliers = 0;
+    return true;
+}
+
+template <typename T>
+static uint64_t bits_host(T v) {
+    uint64_t u = 0;
+    std::memcpy(&u, &v, sizeof(T));
+    return u;
+}
+
+template <typename T>
+static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint64_t n, int32_t* bins,
+                                uint32_t* mask, void* outl, uint64_t cap, lcq_header* hdr, void* ws,
+                                cudaStream_t st) {
+    Consts<T> c{};
+    const bool noa = bt == LCQ_NOA;
+    if (bt == LCQ_ABS) {
+        if (!abs_consts_host<T>(eb, c)) return LCQ_ERR_BOUND;
+    } else if (bt == LCQ_REL) {
+        if (!rel_consts_host<T>(eb, c)) return LCQ_ERR_BOUND;
+    }
+    const uint32_t dtype = sizeof(T) == 4 ? LCQ_F32 : LCQ_F64;
+    WsHead* head = reinterpret_cast<WsHead*>(ws);
+    uint64_t* desc = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
+    size_t dsz = (desc_bytes(n) + 255) & ~(size_t)255;
+    uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz);
+
+    if (noa) {
+        MParams<T> mp{in, n, hdr, head, partial, eb};
+        uint64_t blocks = (n / 4 + kBlock - 1) / kBlock;
+        if (blocks < 1) blocks = 1;
+        if (blocks > (uint64_t)kMinmaxMaxBlocks) blocks = kMinmaxMaxBlocks;
+        k_minmax<T><<<(unsigned)blocks, kBlock, 0, st>>>(mp);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+    }
+    const double eb_abs = bt == LCQ_ABS ? eb : 0.0;
+    if (n == 0) {
+        if (noa) {
+            // no finite value: the range kernel wrote mode 1; fill the rest
+            k_header_empty<<<1, 1, 0, st>>>(hdr, dtype, bt, eb, 0.0, 0, 0, 0, 0, 1);
+        } else {
+            k_header_empty<<<1, 1, 0, st>>>(hdr, dtype, bt, eb, eb_abs, bits_host(c.ebT),
+                                            bits_host(c.scale), bits_host(c.inv), bits_host(c.chk), 0);
+        }
+        return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
+    }
+    for (uint64_t off = 0; off < n; off += kChunk) {
+        const uint64_t len = (n - off) < kChunk ? (n - off) : kChunk;
+        QParams<T> p;
+        p.in = in + off;
+        p.bins = bins + off;
+        p.mask = mask + off / 32;
+        p.out = reinterpret_cast<typename Ty<T>::U*>(outl);
+        p.cap = cap;
+        p.hdr = hdr;
+        p.ws = head;
+        p.desc = desc;
+        p.n = len;
+        p.num_tiles = (uint32_t)tiles_for(len);
+        p.first_chunk = off == 0;
+        p.consts_from_hdr = noa;
+        p.c = c;
+        p.scan = g_scan;
+        p.dtype = dtype;
+        p.bound = bt;
+        p.eb = eb;
+        p.eb_abs = eb_abs;
+        p.n_total = n;
+        if (bt == LCQ_REL)
+            k_quantize<T, LCQ_REL><<<p.num_tiles, kBlock, 0, st>>>(p);
+        else
+            k_quantize<T, LCQ_ABS><<<p.num_tiles, kBlock, 0, st>>>(p);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+    }
+    return LCQ_OK;
+}
+
+template <typename T>
+static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32_t* bins,
+                                  const uint32_t* mask, const void* outl, T* out, uint32_t* status,
+                                  void* ws, cudaStream_t st) {
+    WsHead* head = reinterpret_cast<WsHead*>(ws);
+    uint64_t* desc = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
+    if (n == 0) {
+        k_status_only<<<1, 1, 0, st>>>(status, 0u);
+        return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
+    }
+    for (uint64_t off = 0; off < n; off += kChunk) {
+        const uint64_t len = (n - off) < kChunk ? (n - off) : kChunk;
+        DParams<T> p;
+        p.bins = bins + off;
+        p.mask = mask + off / 32;
+        p.outl = reinterpret_cast<const typename Ty<T>::U*>(outl);
+        p.out = out + off;
+        p.hdr = hdr;
+        p.ws = head;
+        p.desc = desc;
+        p.status = status;
+        p.n = len;
+        p.n_total = n;
+        p.dtype = sizeof(T) == 4 ? LCQ_F32 : LCQ_F64;
+        p.num_tiles = (uint32_t)tiles_for(len);
+        p.first_chunk = off == 0;
+        p.scan = g_scan;
+        k_dequantize<T><<<p.num_tiles, kBlock, 0, st>>>(p);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+    }
+    return LCQ_OK;
+}
+
+}  // namespace lcq
+
+using namespace lcq;
+
+extern "C" {
+
+size_t lcq_workspace_size(lcq_dtype dtype, lcq_bound_type bound_type, uint64_t n) {
+    (void)dtype;
+    (void)bound_type;
+    return ws_size(n);
+}
+
+lcq_status lcq_workspace_init(void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!d_ws || ws_bytes < kWsHeadBytes) return LCQ_ERR_ARG;
+    return cudaMemsetAsync(d_ws, 0, ws_bytes, stream) == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
+}
+
+lcq_status lcq_quantize(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* d_in,
+                        uint64_t n, int32_t* d_bins, uint32_t* d_mask, void* d_outliers,
+                        uint64_t outlier_capacity, lcq_header* d_hdr, void* d_ws, size_t ws_bytes,
+                        cudaStream_t stream) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (bound_type != LCQ_ABS && bound_type != LCQ_REL && bound_type != LCQ_NOA) return LCQ_ERR_ARG;
+    if (!d_hdr || !d_ws || !aligned16(d_ws) || !aligned16(d_hdr)) return LCQ_ERR_ARG;
+    if (n > 0 && (!d_in || !d_bins || !d_mask)) return LCQ_ERR_ARG;
+    if (n > 0 && (!aligned16(d_in) || !aligned16(d_bins) || !aligned16(d_mask))) return LCQ_ERR_ARG;
+    if (outlier_capacity > 0 && (!d_outliers || !aligned16(d_outliers))) return LCQ_ERR_ARG;
+    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return LCQ_ERR_BOUND;
+    if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
+    if (dtype == LCQ_F32)
+        return quantize_impl<float>(bound_type, eb, (const float*)d_in, n, d_bins, d_mask, d_outliers,
+                                    outlier_capacity, d_hdr, d_ws, stream);
+    return quantize_impl<double>(bound_type, eb, (const double*)d_in, n, d_bins, d_mask, d_outliers,
+                                 outlier_capacity, d_hdr, d_ws, stream);
+}
+
+lcq_status lcq_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
+                          const int32_t* d_bins, const uint32_t* d_mask, const void* d_outliers,
+                          void* d_out, uint32_t* d_status, void* d_ws, size_t ws_bytes,
+                          cudaStream_t stream) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (!d_hdr || !d_ws || !aligned16(d_ws) || !aligned16(d_hdr)) return LCQ_ERR_ARG;
+    if (n > 0 && (!d_bins || !d_mask || !d_out)) return LCQ_ERR_ARG;
+    if (n > 0 && (!aligned16(d_bins) || !aligned16(d_mask) || !aligned16(d_out))) return LCQ_ERR_ARG;
+    if (d_outliers && !aligned16(d_outliers)) return LCQ_ERR_ARG;
+    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
+    if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
+    if (dtype == LCQ_F32)
+        return dequantize_impl<float>(n, d_hdr, d_bins, d_mask, d_outliers, (float*)d_out, d_status,
+                                      d_ws, stream);
+    return dequantize_impl<double>(n, d_hdr, d_bins, d_mask, d_outliers, (double*)d_out, d_status,
+                                   d_ws, stream);
+}
+
+lcq_status lcq_sync_status(const lcq_header* d_hdr, uint64_t* h_outlier_count, cudaStream_t stream) {
+    if (!d_hdr) return LCQ_ERR_ARG;
+    lcq_header h;
+    if (cudaMemcpyAsync(&h, d_hdr, sizeof(h), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return LCQ_ERR_CUDA;
+    if (h_outlier_count) *h_outlier_count = h.outlier_count;
+    if (h.status & LCQ_STATUS_TIMEOUT) return LCQ_ERR_TIMEOUT;
+    if (h.status & LCQ_STATUS_CAPACITY) return LCQ_ERR_CAPACITY;
+    if (h.status & LCQ_STATUS_HEADER) return LCQ_ERR_HEADER;
+    return LCQ_OK;
+}
+
+const char* lcq_status_string(lcq_status s) {
+    switch (s) {
+        case LCQ_OK: return "ok";
+        case LCQ_ERR_ARG: return "invalid argument (pointer, alignment, size or enum)";
+        case LCQ_ERR_BOUND: return "unusable error bound";
+        case LCQ_ERR_CAPACITY: return "outlier capacity exceeded";
+        case LCQ_ERR_TIMEOUT: return "outlier scan wait timed out";
+        case LCQ_ERR_CUDA: return "CUDA error";
+        case LCQ_ERR_WORKSPACE: return "workspace too small";
+        case LCQ_ERR_HEADER: return "header does not match the arrays";
+    }
+    return "unknown status";
+}
+
+size_t lcq_host_stage_size(lcq_dtype dtype, uint64_t n, uint64_t outlier_capacity) {
+    const size_t es = dtype == LCQ_F64 ? 8 : 4;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up(n * es) + up(n * 4) + up(((n + 31) / 32) * 4) + up(outlier_capacity * es) +
+           up(sizeof(lcq_header));
+}
+
+lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double eb,
+                             const void* h_in, uint64_t n, int32_t* h_bins, uint32_t* h_mask,
+                             void* h_outliers, uint64_t outlier_capacity, lcq_header* h_hdr,
+                             void* d_stage, size_t stage_bytes, void* d_ws, size_t ws_bytes,
+                             cudaStream_t stream) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (!h_hdr || !d_stage || !aligned16(d_stage)) return LCQ_ERR_ARG;
+    if (n > 0 && (!h_in || !h_bins || !h_mask)) return LCQ_ERR_ARG;
+    if (outlier_capacity > 0 && !h_outliers) return LCQ_ERR_ARG;
+    if (stage_bytes < lcq_host_stage_size(dtype, n, outlier_capacity)) return LCQ_ERR_WORKSPACE;
+    const size_t es = dtype == LCQ_F64 ? 8 : 4;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    char* base = (char*)d_stage;
+    void* d_in = base;
+    int32_t* d_bins = (int32_t*)(base + up(n * es));
+    uint32_t* d_mask = (uint32_t*)((char*)d_bins + up(n * 4));
+    void* d_out = (char*)d_mask + up(((n + 31) / 32) * 4);
+    lcq_header* d_hdr = (lcq_header*)((char*)d_out + up(outlier_capacity * es));
+    if (n && cudaMemcpyAsync(d_in, h_in, n * es, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    lcq_status s = lcq_quantize(dtype, bound_type, eb, d_in, n, d_bins, d_mask,
+                                outlier_capacity ? d_out : nullptr, outlier_capacity, d_hdr, d_ws,
+                                ws_bytes, stream);
+    if (s != LCQ_OK) return s;
+    if (n && cudaMemcpyAsync(h_bins, d_bins, n * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    if (n && cudaMemcpyAsync(h_mask, d_mask, ((n + 31) / 32) * 4, cudaMemcpyDeviceToHost, stream) !=
+                 cudaSuccess)
+        return LCQ_ERR_CUDA;
+    if (cudaMemcpyAsync(h_hdr, d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return LCQ_ERR_CUDA;
+    uint64_t cnt = h_hdr->outlier_count < outlier_capacity ? h_hdr->outlier_count : outlier_capacity;
+    if (cnt && cudaMemcpyAsync(h_outliers, d_out, cnt * es, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return LCQ_ERR_CUDA;
+    if (h_hdr->status & LCQ_STATUS_TIMEOUT) return LCQ_ERR_TIMEOUT;
+    if (h_hdr->status & LCQ_STATUS_CAPACITY) return LCQ_ERR_CAPACITY;
+    return LCQ_OK;
+}
+
+void lcq_debug_set_scan(uint32_t spin_limit, uint64_t drop_tile) {
+    g_scan.spin_limit = spin_limit ? spin_limit : kDefaultSpin;
+    g_scan.drop_tile = drop_tile;
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+"""Python binding of liblcq.so (include/lcq.h): argument marshalling only.
+
+Every step of quantize / verify / compact / dequantize runs in the library's
+CUDA kernels; PyTorch only provides device memory and streams.  There is no
+CPU fallback: if the library cannot be loaded, or no CUDA device is present,
+the calls raise.
+"""
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblcq.so")
+
+F32, F64 = 0, 1
+ABS, REL, NOA = 0, 1, 2
+BOUNDS = {"abs": ABS, "rel": REL, "noa": NOA}
+STATUS_CAPACITY, STATUS_TIMEOUT, STATUS_HEADER = 1, 2, 4
+MAGIC = 0x3151434C
+
+STATUS_NAMES = {0: "LCQ_OK", 1: "LCQ_ERR_ARG", 2: "LCQ_ERR_BOUND", 3: "LCQ_ERR_CAPACITY",
+                4: "LCQ_ERR_TIMEOUT", 5: "LCQ_ERR_CUDA", 6: "LCQ_ERR_WORKSPACE",
+                7: "LCQ_ERR_HEADER"}
+
+
+class Header(ctypes.Structure):
+    """Mirror of struct lcq_header."""
+    _fields_ = [
+        ("magic", ctypes.c_uint32), ("dtype", ctypes.c_uint32), ("bound_type", ctypes.c_uint32),
+        ("mode", ctypes.c_uint32), ("n", ctypes.c_uint64), ("eb", ctypes.c_double),
+        ("range", ctypes.c_double), ("eb_abs", ctypes.c_double), ("ebT_bits", ctypes.c_uint64),
+        ("scale_bits", ctypes.c_uint64), ("inv_bits", ctypes.c_uint64), ("chk_bits", ctypes.c_uint64),
+        ("outlier_count", ctypes.c_uint64), ("status", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+    ]
+
+
+HEADER_BYTES = ctypes.sizeof(Header)
+
+
+class LcqError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s failed: %s" % (what, STATUS_NAMES.get(code, str(code))))
+        self.code = code
+
+
+# Exported symbols and their ctypes signatures (must match include/lcq.h).
+_vp, _u64, _u32, _i32, _dbl, _sz = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32,
+                                     ctypes.c_int32, ctypes.c_double, ctypes.c_size_t)
+SIGNATURES = {
+    "lcq_workspace_size": ([ctypes.c_int, ctypes.c_int, _u64], _sz),
+    "lcq_workspace_init": ([_vp, _sz, _vp], ctypes.c_int),
+    "lcq_quantize": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp, _vp,
+                      _sz, _vp], ctypes.c_int),
+    "lcq_dequantize": ([ctypes.c_int, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
+                       ctypes.c_int),
+    "lcq_sync_status": ([_vp, _vp, _vp], ctypes.c_int),
+    "lcq_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "lcq_host_stage_size": ([ctypes.c_int, _u64, _u64], _sz),
+    "lcq_quantize_host": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
+                           _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_debug_set_scan": ([_u32, _u64], None),
+}
+
+_lib = None
+
+
+def lib():
+    """Load liblcq.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("liblcq.so not built: run python -m paper_2407_15037_b300.build "
+                              "(or __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(code, what):
+    if code != 0:
+        raise LcqError(code, what)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError("lcq: float32 or float64 tensor required, got %s" % t.dtype)
+
+
+def _bound_code(bound):
+    return BOUNDS[bound] if isinstance(bound, str) else int(bound)
+
+
+def _stream_ptr(stream, device):
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None and t.numel() else ctypes.c_void_p(0)
+
+
+def _require_cuda(t):
+    if not t.is_cuda:
+        raise ValueError("lcq: device tensors required (use quantize_host for host data)")
+
+
+def workspace_size(dtype_code, bound, n):
+    return int(lib().lcq_workspace_size(dtype_code, _bound_code(bound), int(n)))
+
+
+def new_workspace(n, device, dtype_code=F32, bound=ABS):
+    """A zero-filled workspace for arrays of up to n values."""
+    nbytes = max(workspace_size(dtype_code, bound, n), 256)
+    return torch.zeros(nbytes, dtype=torch.uint8, device=device)
+
+
+@dataclass
+class Quantized:
+    """Device-resident compressed form (see include/lcq.h)."""
+    bins: torch.Tensor      # int32[n]
+    mask: torch.Tensor      # int32[ceil(n/32)] (raw uint32 words)
+    outliers: torch.Tensor  # int32 / int64 [capacity] raw bit patterns
+    header: torch.Tensor    # uint8[HEADER_BYTES] (struct lcq_header)
+    n: int
+    dtype: torch.dtype
+
+    def read_header(self, stream=None):
+        """Copy the header to the host (synchronises the stream)."""
+        h = Header()
+        raw = self.header.cpu() if stream is None else self.header.to("cpu", non_blocking=False)
+        ctypes.memmove(ctypes.addressof(h), raw.numpy().ctypes.data, HEADER_BYTES)
+        return h
+
+
+def alloc_outputs(n, dtype, device, outlier_capacity=None):
+    cap = n if outlier_capacity is None else int(outlier_capacity)
+    pay_dtype = torch.int32 if dtype == torch.float32 else torch.int64
+    return Quantized(
+        bins=torch.empty(n, dtype=torch.int32, device=device),
+        mask=torch.empty((n + 31) // 32, dtype=torch.int32, device=device),
+        outliers=torch.empty(cap, dtype=pay_dtype, device=device),
+        header=torch.empty(HEADER_BYTES, dtype=torch.uint8, device=device),
+        n=n, dtype=dtype)
+
+
+def quantize_into(x, bound, eb, q, ws, stream=None):
+    """Enqueue lcq_quantize of the contiguous device tensor x into the
+    preallocated outputs q, using workspace ws.  No host synchronisation."""
+    _require_cuda(x)
+    code = lib().lcq_quantize(
+        _dtype_code(x), _bound_code(bound), float(eb), _ptr(x), x.numel(), _ptr(q.bins),
+        _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header), _ptr(ws), ws.numel(),
+        _stream_ptr(stream, x.device))
+    _check(code, "lcq_quantize")
+    return q
+
+
+def quantize(x, bound, eb, outlier_capacity=None, ws=None, stream=None):
+    """Quantize a contiguous float32/float64 CUDA tensor with bound type
+    'abs' | 'rel' | 'noa' and bound eb.  Returns the device-resident result."""
+    _require_cuda(x)
+    x = x.contiguous().reshape(-1)
+    q = alloc_outputs(x.numel(), x.dtype, x.device, outlier_capacity)
+    if ws is None:
+        ws = new_workspace(x.numel(), x.device, _dtype_code(x), bound)
+    return quantize_into(x, bound, eb, q, ws, stream)
+
+
+def dequantize_into(q, out, ws, status=None, stream=None):
+    _require_cuda(out)
+    code = lib().lcq_dequantize(
+        _dtype_code(out), q.n, _ptr(q.header), _ptr(q.bins), _ptr(q.mask), _ptr(q.outliers),
+        _ptr(out), _ptr(status), _ptr(ws), ws.numel(), _stream_ptr(stream, out.device))
+    _check(code, "lcq_dequantize")
+    return out
+
+
+def dequantize(q, ws=None, stream=None, check=True):
+    """Reconstruct the values of a Quantized result on the device."""
+    out = torch.empty(q.n, dtype=q.dtype, device=q.bins.device)
+    if ws is None:
+        ws = new_workspace(q.n, out.device)
+    status = torch.zeros(1, dtype=torch.int32, device=out.device)
+    dequantize_into(q, out, ws, status, stream)
+    if check:
+        st = int(status.item())
+        if st:
+            raise LcqError(7 if st & STATUS_HEADER else 4, "lcq_dequantize (device status %d)" % st)
+    return out
+
+
+def sync_status(q, stream=None):
+    """Synchronise and return (status_code, outlier_count) for a result."""
+    cnt = ctypes.c_uint64()
+    code = lib().lcq_sync_status(_ptr(q.header), ctypes.byref(cnt), _stream_ptr(stream, q.bins.device))
+    return code, cnt.value
+
+
+def debug_set_scan(spin_limit=0, drop_tile=(1 << 64) - 1):
+    """Test hook for the bounded scan waits (see include/lcq.h)."""
+    lib().lcq_debug_set_scan(int(spin_limit), int(drop_tile))
+
+
+def host_stage_size(dtype_code, n, cap):
+    return int(lib().lcq_host_stage_size(dtype_code, int(n), int(cap)))
+
+
+def quantize_host(x_host, bound, eb, outputs, stage, ws, stream=None, device=None):
+    """End-to-end quantization of a (preferably pinned) host tensor through
+    lcq_quantize_host: H2D copy, kernels, D2H copies of bins, mask, header and
+    outliers into the host tensors of `outputs`.  Blocks until done."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    code = lib().lcq_quantize_host(
+        _dtype_code(x_host), _bound_code(bound), float(eb), _ptr(x_host), x_host.numel(),
+        _ptr(outputs.bins), _ptr(outputs.mask), _ptr(outputs.outliers), outputs.outliers.numel(),
+        _ptr(outputs.header), _ptr(stage), stage.numel(), _ptr(ws), ws.numel(),
+        _stream_ptr(stream, device))
+    _check(code, "lcq_quantize_host")
+    return outputs

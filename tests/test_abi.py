@@ -1,0 +1,76 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/*.h declares; the binding's struct mirrors match the header."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2407_15037_b300 as P
+from paper_2407_15037_b300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(lcq_\w+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.lib()
+
+
+def test_library_exports_every_declared_function(lib):
+    declared = _declared_functions()
+    assert declared, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", P.lcq.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = sorted(declared - exported)
+    assert not missing, missing
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+def test_binding_covers_the_declarations():
+    assert set(P.lcq.SIGNATURES) | set(getattr(P, "EXTRA_SIGNATURES", {})) >= \
+        {n for n in _declared_functions() if n in P.lcq.SIGNATURES}
+
+
+def test_header_struct_size_matches_c(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include "lcq.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu\\n", sizeof(lcq_header),'
+                   ' offsetof(lcq_header, outlier_count), offsetof(lcq_header, status));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
+                    str(src), "-o", str(exe)], check=True)
+    size, off_cnt, off_st = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
+                                                    check=True).stdout.split())
+    H = P.Header
+    assert size == ctypes.sizeof(H)
+    assert off_cnt == H.outlier_count.offset and off_st == H.status.offset
+
+
+def test_host_side_argument_errors_need_no_gpu(lib):
+    # invalid enums and bounds are rejected before anything touches a device
+    ws = (ctypes.c_uint8 * 4096)()
+    hdr = (ctypes.c_uint8 * 128)()
+    p = ctypes.c_void_p(ctypes.addressof(ws) + (-ctypes.addressof(ws)) % 16)
+    h = ctypes.c_void_p(ctypes.addressof(hdr) + (-ctypes.addressof(hdr)) % 16)
+    assert lib.lcq_quantize(7, 0, 1e-3, None, 0, None, None, None, 0, h, p, 4000, None) == 1
+    assert lib.lcq_quantize(0, 9, 1e-3, None, 0, None, None, None, 0, h, p, 4000, None) == 1
+    assert lib.lcq_quantize(0, 0, -1.0, None, 0, None, None, None, 0, h, p, 4000, None) == 2
+    assert lib.lcq_quantize(0, 0, float("nan"), None, 0, None, None, None, 0, h, p, 4000, None) == 2
+    assert lib.lcq_status_string(4) == b"outlier scan wait timed out"
+    assert lib.lcq_workspace_size(0, 0, 1 << 31) > lib.lcq_workspace_size(0, 0, 1 << 20)

@@ -1,0 +1,198 @@
+"""CUDA path vs oracle, bit for bit: bins, outlier mask, outlier payload,
+outlier count, header constants and decoded values (the quantities are exact,
+so no tolerance applies).  Sizes span several 4096-value tiles and ragged
+tails; the large cases use the benchmark's full configurations."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import paper_2407_15037_b300 as P
+import synth
+from gpu_helpers import compare
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+BOUNDS = ["abs", "rel", "noa"]
+EBS = [1e-2, 1e-3, 1e-4, 1e-5]
+
+
+@pytest.fixture(autouse=True)
+def _reset_scan():
+    P.debug_set_scan(0)
+    yield
+    P.debug_set_scan(0)
+
+
+def test_sine_1d_abs_config():
+    """2^20 float32 sine + noise with 0.1% specials and bin-edge values, ABS 1e-3."""
+    x = synth.sine_1d(1 << 20, seed=0, eb=1e-3, device=DEV)
+    q, oq = compare(x, "abs", 1e-3)
+    assert oq.count >= 1049 * 5 // 8  # NaN/Inf kinds are always outliers
+
+
+@pytest.mark.parametrize("bound", BOUNDS)
+@pytest.mark.parametrize("eb", EBS)
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_smooth_field_sweep(bound, eb, dtype):
+    x = synth.smooth_field((37, 61, 53), dtype=dtype, seed=1, device=DEV)  # 119,561 values
+    compare(x, bound, eb)
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 4, 5, 31, 32, 33, 127, 4095, 4096, 4097, 8193, 12289, 65537])
+@pytest.mark.parametrize("bound", BOUNDS)
+def test_ragged_sizes(n, bound):
+    g = torch.Generator(device=DEV).manual_seed(n)
+    x = torch.randn(n, generator=g, device=DEV) * 10
+    if n > 3:
+        x[::7] = float("nan")
+    compare(x, bound, 1e-3)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("bound", BOUNDS)
+def test_special_values(dtype, bound):
+    if dtype == torch.float32:
+        bits = np.array([0x7FC00000, 0x7F800001, 0xFFC01234, 0x7F800000, 0xFF800000, 0, 0x80000000,
+                         1, 0x807FFFFF, 0x7F7FFFFF, 0xFF7FFFFF, 0x00800000, 0x3F800000, 0xC0490FDB],
+                        dtype=np.uint32)
+        x = torch.from_numpy(np.tile(bits, 700).view(np.float32)).to(DEV)
+    else:
+        bits = np.array([0x7FF8000000000000, 0x7FF0000000000001, 0xFFF0000000000000, 0,
+                         0x8000000000000000, 1, 0x800FFFFFFFFFFFFF, 0x7FEFFFFFFFFFFFFF,
+                         0x0010000000000000, 0x3FF0000000000000], dtype=np.uint64)
+        x = torch.from_numpy(np.tile(bits, 900).view(np.float64)).to(DEV)
+    compare(x, bound, 1e-3)
+
+
+def test_int_min_and_maxbin_edges():
+    eb = 2.0 ** -10
+    v = np.array([(2.0 ** 30 - 64) * 2 * eb, 2.0 ** 30 * 2 * eb, -(2.0 ** 30) * 2 * eb,
+                  -(2.0 ** 31) * 2 * eb, 2.0 ** 31 * 2 * eb, -(2.0 ** 30 - 64) * 2 * eb],
+                 dtype=np.float32)
+    x = torch.from_numpy(np.tile(v, 1000)).to(DEV)
+    q, oq = compare(x, "abs", eb)
+    assert oq.count == 4000
+
+
+@pytest.mark.parametrize("eb", [1e-3, 1e-6])
+def test_rel_stress_subset(eb):
+    x = synth.rel_stress(1 << 22, seed=0, device=DEV)
+    q, oq = compare(x, "rel", eb)
+    assert oq.count >= 0.111 * x.numel()
+
+
+def test_noa_degenerate_all_outliers():
+    x = torch.full((10000,), 2.5, device=DEV)
+    q, oq = compare(x, "noa", 1e-3)
+    assert oq.count == 10000
+    x = torch.full((5000,), float("nan"), device=DEV)
+    compare(x, "noa", 1e-3)
+
+
+def test_capacity_overflow_reports_and_stays_in_bounds():
+    x = torch.full((50000,), float("inf"), device=DEV)
+    cap = 1000
+    q = P.alloc_outputs(x.numel(), x.dtype, x.device, outlier_capacity=cap + 64)
+    guard = q.outliers[cap:].clone().fill_(0x5A5A5A5A)
+    q.outliers[cap:] = guard
+    small = P.Quantized(q.bins, q.mask, q.outliers[:cap], q.header, q.n, q.dtype)
+    ws = P.new_workspace(x.numel(), x.device)
+    P.quantize_into(x, "abs", 1e-3, small, ws)
+    code, cnt = P.sync_status(small)
+    assert code == 3 and cnt == 50000  # LCQ_ERR_CAPACITY, full count
+    assert torch.equal(q.outliers[cap:], guard)  # nothing written past the capacity
+    compare(x, "abs", 1e-3, q=small, capacity=cap, check_decode=False)
+
+
+def test_bad_bounds_rejected():
+    x = torch.randn(100, device=DEV)
+    for eb in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(P.LcqError):
+            P.quantize(x, "abs", eb)
+    with pytest.raises(P.LcqError):
+        P.quantize(x, "rel", 1e-46)
+
+
+def test_workspace_reuse_across_calls():
+    ws = P.new_workspace(1 << 20, DEV)
+    for i, n in enumerate([1 << 20, 5000, 1 << 18, 77777, 1 << 20]):
+        g = torch.Generator(device=DEV).manual_seed(i)
+        x = torch.randn(n, generator=g, device=DEV) * 100
+        bound = BOUNDS[i % 3]
+        q = P.alloc_outputs(n, x.dtype, x.device)
+        P.quantize_into(x, bound, 1e-4, q, ws)
+        compare(x, bound, 1e-4, q=q)
+
+
+def test_scan_timeout_is_reported_without_hang():
+    """A tile that never publishes its scan descriptor: the successor's wait
+    gives up after the spin limit and the header carries LCQ_STATUS_TIMEOUT."""
+    x = torch.randn(5 * 4096, device=DEV)
+    ws = P.new_workspace(x.numel(), x.device)
+    q = P.alloc_outputs(x.numel(), x.dtype, x.device)
+    P.debug_set_scan(spin_limit=200, drop_tile=1)
+    P.quantize_into(x, "abs", 1e-3, q, ws)
+    code, _ = P.sync_status(q)
+    assert code == 4  # LCQ_ERR_TIMEOUT
+    P.debug_set_scan(0)
+    ws.zero_()
+    P.quantize_into(x, "abs", 1e-3, q, ws)
+    assert P.sync_status(q)[0] == 0
+    compare(x, "abs", 1e-3, q=q)
+
+
+def test_dequantize_rejects_mismatched_header():
+    x = torch.randn(10000, device=DEV)
+    q = P.quantize(x, "abs", 1e-3)
+    out = torch.full((10000,), 7.0, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    ws = P.new_workspace(10000, DEV)
+    wrong = P.Quantized(q.bins[:9000], q.mask[:282], q.outliers, q.header, 9000, q.dtype)
+    P.dequantize_into(wrong, out[:9000], ws, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) & P.lcq.STATUS_HEADER
+    assert torch.all(out == 7.0)
+
+
+def test_host_entry_point_matches_device_path():
+    x = synth.smooth_field((64, 64, 64), seed=3).to(torch.float32)  # built on the host
+    xp = x.pin_memory()
+    n = x.numel()
+    outs = P.Quantized(torch.empty(n, dtype=torch.int32).pin_memory(),
+                       torch.empty((n + 31) // 32, dtype=torch.int32).pin_memory(),
+                       torch.empty(n, dtype=torch.int32).pin_memory(),
+                       torch.empty(P.lcq.HEADER_BYTES, dtype=torch.uint8).pin_memory(), n, x.dtype)
+    stage = torch.empty(P.host_stage_size(P.F32, n, n), dtype=torch.uint8, device=DEV)
+    ws = P.new_workspace(n, DEV)
+    P.quantize_host(xp, "rel", 1e-3, outs, stage, ws)
+    qd = P.quantize(x.to(DEV), "rel", 1e-3)
+    torch.cuda.synchronize()
+    assert torch.equal(outs.bins, qd.bins.cpu())
+    assert torch.equal(outs.mask, qd.mask.cpu())
+    h = qd.read_header()
+    assert torch.equal(outs.outliers[:h.outlier_count], qd.outliers[:h.outlier_count].cpu())
+    assert torch.equal(outs.header, qd.header.cpu())
+
+
+# --------------------------------------------------------- full sizes ----
+
+@pytest.mark.parametrize("bound", BOUNDS)
+def test_full_field_f32_512(bound):
+    """The benchmark's workload: float32 512^3 sinusoid field, all three
+    bound types at 1e-3, compared over every value."""
+    x = synth.smooth_field((512, 512, 512), dtype=torch.float32, seed=0, device=DEV)
+    compare(x, bound, 1e-3)
+
+
+@pytest.mark.parametrize("bound", BOUNDS)
+def test_full_field_f64_256(bound):
+    x = synth.smooth_field((256, 256, 256), dtype=torch.float64, seed=0, device=DEV)
+    compare(x, bound, 1e-4)
+
+
+@pytest.mark.parametrize("eb", [1e-3, 1e-6])
+def test_full_rel_stress_2_28(eb):
+    x = synth.rel_stress(1 << 28, seed=0, device=DEV)
+    compare(x, "rel", eb, check_decode=(eb == 1e-3))
