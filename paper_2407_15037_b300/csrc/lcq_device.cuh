@@ -272,7 +272,10 @@ __device__ __forceinline__ uint32_t lookback_exclusive(uint64_t* desc, uint32_t 
                 state = 2u;  // before tile 0: an empty prefix
                 val = 0u;
             }
-            if (!__any_sync(FULL, state == 0u)) break;
+            // only the lanes closer than the nearest inclusive prefix matter
+            const uint32_t pm = __ballot_sync(FULL, state == 2u);
+            const uint32_t need = pm ? ((pm & (0u - pm)) - 1u) : FULL;
+            if ((__ballot_sync(FULL, state == 0u) & need) == 0u) break;
             if (++spins > cfg.spin_limit) {
                 timed_out = true;
                 if (state == 0u) { state = 2u; val = 0u; }
