@@ -238,23 +238,25 @@ struct ScanCfg {
     uint64_t drop_tile;   // test hook: this tile never publishes
 };
 
-// Called by all 32 lanes of one warp.  Publishes the tile's aggregate, walks
-// back over predecessors (32 at a time) until an inclusive prefix is found,
+// Publish a tile's aggregate (or, for tile 0, its inclusive prefix).  Lane 0.
+__device__ __forceinline__ void lookback_publish(uint64_t* desc, uint32_t tile, uint32_t agg,
+                                                 uint32_t epoch, const ScanCfg& cfg) {
+    if ((uint64_t)tile == cfg.drop_tile) return;
+    const uint64_t tag = (uint64_t)(epoch & kEpochMask) << 32;
+    st_relaxed_u64(&desc[tile], (tile == 0 ? kStPre : kStAgg) | tag | agg);
+}
+
+// Called by all 32 lanes of one warp after lookback_publish.  Walks back over
+// the predecessors (32 at a time) until an inclusive prefix is found,
 // publishes the tile's inclusive prefix and returns its exclusive prefix.
 // Every wait is bounded: after cfg.spin_limit polls a missing predecessor is
 // counted as 0 and LCQ_STATUS_TIMEOUT is raised, so the scan always ends.
-__device__ __forceinline__ uint32_t lookback_exclusive(uint64_t* desc, uint32_t tile, uint32_t agg,
-                                                       uint32_t epoch, const ScanCfg& cfg,
-                                                       uint32_t* err) {
+__device__ __forceinline__ uint32_t lookback_walk(uint64_t* desc, uint32_t tile, uint32_t agg,
+                                                  uint32_t epoch, const ScanCfg& cfg, uint32_t* err) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
+    if (tile == 0) return 0;
     const uint64_t tag = (uint64_t)(epoch & kEpochMask) << 32;
-    const bool publish = (uint64_t)tile != cfg.drop_tile;
-    if (tile == 0) {
-        if (lane == 0 && publish) st_relaxed_u64(&desc[0], kStPre | tag | agg);
-        return 0;
-    }
-    if (lane == 0 && publish) st_relaxed_u64(&desc[tile], kStAgg | tag | agg);
     uint32_t excl = 0;
     int64_t pos = (int64_t)tile - 1 - lane;
     bool timed_out = false;
@@ -282,7 +284,7 @@ __device__ __forceinline__ uint32_t lookback_exclusive(uint64_t* desc, uint32_t 
                 break;
             }
             __nanosleep(ns);
-            ns = ns < 1024u ? ns * 2u : 1024u;
+            ns = ns < 256u ? ns * 2u : 256u;
         }
         const uint32_t pmask = __ballot_sync(FULL, state == 2u);
         if (pmask) {
@@ -294,7 +296,7 @@ __device__ __forceinline__ uint32_t lookback_exclusive(uint64_t* desc, uint32_t 
         pos -= 32;
     }
     if (lane == 0) {
-        if (publish) st_relaxed_u64(&desc[tile], kStPre | tag | (uint32_t)(excl + agg));
+        if ((uint64_t)tile != cfg.drop_tile) st_relaxed_u64(&desc[tile], kStPre | tag | (uint32_t)(excl + agg));
         if (timed_out) atomicOr(err, LCQ_STATUS_TIMEOUT);
     }
     return excl;

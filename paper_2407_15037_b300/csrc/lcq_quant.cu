@@ -26,18 +26,20 @@
 #include <cuda_runtime.h>
 
 #include "lcq_device.cuh"
+#include "lcq_pipe.cuh"
 
 namespace lcq {
 
 constexpr int kBlock = 256;
-constexpr int kVpt = 4;                         // 4-value vectors per thread
-constexpr int kTile = kBlock * kVpt * 4;        // values per tile (4096)
-constexpr int kWords = kTile / 32;              // mask words per tile (128)
-constexpr int kWpl = kWords / 32;               // mask words per lane of warp 0
+constexpr int kTileMin = 4096;                  // smallest tile; sizes the scan workspace
 constexpr uint64_t kChunk = 1ull << 31;         // values per launch at most
-constexpr uint32_t kDefaultSpin = 1u << 20;     // ~1 s of polling with backoff
+constexpr uint32_t kDefaultSpin = 1u << 20;     // lookback polls (~1 s with backoff)
+constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (seconds)
 
-static_assert(kWords % 32 == 0, "tile must give whole mask words per lane");
+// Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
+// the depth of the shared-memory stage ring.
+constexpr int kVptF32 = 8, kStagesF32 = 3;      // 8192-value tiles, 32 KB stages
+constexpr int kVptF64 = 4, kStagesF64 = 3;      // 4096-value tiles, 32 KB stages
 
 static ScanCfg g_scan = {kDefaultSpin, ~0ull};
 
@@ -51,6 +53,10 @@ template <>
 struct Vec4<float> {
     static __device__ __forceinline__ void load(const float* p, float v[4]) {
         const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void load_shared(const float* p, float v[4]) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
         v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
     }
     static __device__ __forceinline__ void load_cached(const float* p, float v[4]) {
@@ -69,6 +75,11 @@ struct Vec4<double> {
         const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
     }
+    static __device__ __forceinline__ void load_shared(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
     static __device__ __forceinline__ void load_cached(const double* p, double v[4]) {
         const double2 a = reinterpret_cast<const double2*>(p)[0];
         const double2 b = reinterpret_cast<const double2*>(p)[1];
@@ -81,7 +92,10 @@ struct Vec4<double> {
 };
 
 // ---------------------------------------------------------------------------
-// Quantize kernel
+// Quantize kernel: persistent CTAs; input tiles stream into a ring of
+// shared-memory stages by bulk asynchronous copies, so that the next tiles
+// are in flight while the current tile is quantized and its outliers are
+// placed by the lookback scan.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct QParams {
@@ -99,134 +113,194 @@ struct QParams {
     uint32_t consts_from_hdr;  // NOA: constants written by k_minmax
     Consts<T> c;
     ScanCfg scan;
-    // header fields (written by tile 0 of the first chunk)
+    // header fields (written by the CTA that owns tile 0 of the first chunk)
     uint32_t dtype, bound;
     double eb, eb_abs;
     uint64_t n_total;
 };
 
-template <typename T, int MODE>
+template <typename T, int VPT>
+__device__ __forceinline__ void load4(const T* sbuf_tile, const T* gin, bool from_smem, int off,
+                                      uint64_t e0, uint64_t n, T x[4]) {
+    if (from_smem) {
+        Vec4<T>::load_shared(sbuf_tile + off, x);
+    } else if (e0 + 4 <= n) {
+        Vec4<T>::load(gin + e0, x);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) x[k] = (e0 + k < n) ? gin[e0 + k] : T(0);
+    }
+}
+
+// Mask words of one tile -> global, 16-byte stores where the tile is whole.
+template <int WPL>
+__device__ __forceinline__ void store_mask_words(uint32_t* gmask, uint64_t gw, uint64_t nwords,
+                                                 const uint32_t* wv) {
+#pragma unroll
+    for (int j = 0; j < WPL; j += 4) {
+        if (gw + j + 4 <= nwords) {
+            __stcs(reinterpret_cast<uint4*>(gmask + gw + j), make_uint4(wv[j], wv[j + 1], wv[j + 2], wv[j + 3]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (gw + j + i < nwords) gmask[gw + j + i] = wv[j + i];
+        }
+    }
+}
+
+// Warp 0: exclusive prefix popcounts of the tile's mask words into s_wpre;
+// returns the tile's outlier count.  Also stores the words to global memory.
+template <int WPL>
+__device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uint32_t* s_wpre,
+                                                    uint32_t* gmask, uint64_t gw, uint64_t nwords,
+                                                    bool store) {
+    const int lane = threadIdx.x & 31;
+    uint32_t wv[WPL], loc[WPL], cnt = 0;
+#pragma unroll
+    for (int j = 0; j < WPL; j++) {
+        wv[j] = s_words[lane * WPL + j];
+        loc[j] = cnt;
+        cnt += __popc(wv[j]);
+    }
+    if (store) store_mask_words<WPL>(gmask, gw, nwords, wv);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t ex = incl - cnt;
+#pragma unroll
+    for (int j = 0; j < WPL; j++) s_wpre[lane * WPL + j] = ex + loc[j];
+    return __shfl_sync(0xFFFFFFFFu, incl, 31);
+}
+
+template <typename T, int MODE, int VPT, int STAGES>
 __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
     using F = Ty<T>;
     using U = typename F::U;
-    __shared__ uint32_t s_mask[kWords];
-    __shared__ uint32_t s_wpre[kWords];
-    __shared__ uint32_t s_tile, s_epoch, s_excl;
+    constexpr int TILE = kBlock * 4 * VPT;
+    constexpr int WORDS = TILE / 32;
+    constexpr int WPL = WORDS / 32;
+    static_assert(WPL % 4 == 0, "whole uint4 mask stores per lane");
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    T* sbuf = reinterpret_cast<T*>(dsmem);
+    __shared__ __align__(8) uint64_t s_bar[STAGES];
+    __shared__ uint32_t s_stile[STAGES];
+    __shared__ uint32_t s_mask[WORDS];
+    __shared__ uint32_t s_wpre[WORDS];
+    __shared__ uint32_t s_epoch, s_excl, s_abort;
     __shared__ uint64_t s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t full_tiles = (uint32_t)(p.n / TILE);
+
+    auto issue = [&](int s) {  // thread 0: next ticket into stage s
+        const uint32_t t = atomicAdd(&p.ws->ticket, 1u);
+        s_stile[s] = t;
+        if (t < full_tiles) {
+            mbar_arrive_expect_tx(&s_bar[s], TILE * sizeof(T));
+            bulk_g2s(sbuf + (size_t)s * TILE, p.in + (uint64_t)t * TILE, TILE * sizeof(T), &s_bar[s]);
+        } else if (t < p.num_tiles) {
+            mbar_arrive(&s_bar[s]);  // ragged last tile: read straight from global memory
+        }
+    };
+
     if (tid == 0) {
-        s_tile = atomicAdd(&p.ws->ticket, 1u);
+        for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
+        mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
         s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.hdr->outlier_count);
+        s_abort = 0;
+        for (int s = 0; s < STAGES; s++) issue(s);
     }
     const Consts<T> c = p.consts_from_hdr ? consts_from_header<T>(p.hdr) : p.c;
     __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t tbase = (uint64_t)tile * kTile;
 
-    U vals[kVpt][4];
-    uint32_t nib[kVpt];
-#pragma unroll
-    for (int v = 0; v < kVpt; v++) {
-        const uint64_t e0 = tbase + (uint64_t)v * (kBlock * 4) + (uint64_t)tid * 4;
-        T x[4];
-        const bool full = e0 + 4 <= p.n;
-        if (full) {
-            Vec4<T>::load(p.in + e0, x);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; k++) x[k] = (e0 + k < p.n) ? p.in[e0 + k] : T(0);
+    for (uint32_t k = 0;; k++) {
+        const int s = (int)(k % STAGES);
+        const uint32_t tile = s_stile[s];
+        if (tile >= p.num_tiles) break;
+        const bool from_smem = tile < full_tiles;
+        if (from_smem && !mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit)) {
+            atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
+            s_abort = 1;
+        } else if (!from_smem) {
+            mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit);
         }
-        int32_t b[4];
-        uint32_t nb = 0;
+        const T* st = sbuf + (size_t)s * TILE;
+        const uint64_t tbase = (uint64_t)tile * TILE;
+        uint32_t nib[VPT];
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            int32_t bin = 0;
-            bool ok = false;
-            if (!c.all_outliers) ok = (MODE == LCQ_REL) ? rel_quant<T>(x[k], c, bin) : abs_quant<T>(x[k], c, bin);
-            if (!ok && e0 + k < p.n) nb |= 1u << k;
-            b[k] = ok ? bin : 0;
-            vals[v][k] = F::bits(x[k]);
-        }
-        if (full) {
-            __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(b[0], b[1], b[2], b[3]));
-        } else {
+        for (int v = 0; v < VPT; v++) {
+            const int off = v * (kBlock * 4) + tid * 4;
+            const uint64_t e0 = tbase + off;
+            T x[4];
+            load4<T, VPT>(st, p.in, from_smem, off, e0, p.n, x);
+            int32_t b[4];
+            uint32_t nb = 0;
 #pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (e0 + k < p.n) p.bins[e0 + k] = b[k];
-        }
-        uint32_t w = nb << ((lane & 7) * 4);
-        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
-        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
-        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
-        if ((lane & 7) == 0) s_mask[v * (kBlock / 8) + warp * 4 + (lane >> 3)] = w;
-        nib[v] = nb;
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-        uint32_t wv[kWpl];
-        uint32_t cnt = 0, loc[kWpl];
-#pragma unroll
-        for (int j = 0; j < kWpl; j++) {
-            wv[j] = s_mask[lane * kWpl + j];
-            loc[j] = cnt;
-            cnt += __popc(wv[j]);
-        }
-        // mask words of this tile -> global (16-byte stores)
-        const uint64_t nwords = (p.n + 31) / 32;
-        const uint64_t gw = (uint64_t)tile * kWords + (uint64_t)lane * kWpl;
-        if (gw + kWpl <= nwords) {
-            __stcs(reinterpret_cast<uint4*>(p.mask + gw), make_uint4(wv[0], wv[1], wv[2], wv[3]));
-        } else {
-#pragma unroll
-            for (int j = 0; j < kWpl; j++)
-                if (gw + j < nwords) p.mask[gw + j] = wv[j];
-        }
-        // inclusive warp scan of per-lane counts
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t ex = incl - cnt;
-#pragma unroll
-        for (int j = 0; j < kWpl; j++) s_wpre[lane * kWpl + j] = ex + loc[j];
-        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const uint32_t excl = lookback_exclusive(p.desc, tile, agg, s_epoch, p.scan, &p.ws->err);
-        if (lane == 0) {
-            s_excl = excl;
-            if (tile == p.num_tiles - 1) {
-                const uint64_t total = s_base + excl + agg;
-                st_relaxed_u64(&p.hdr->outlier_count, total);
-                if (total > p.cap) atomicOr(&p.ws->err, LCQ_STATUS_CAPACITY);
+            for (int q = 0; q < 4; q++) {
+                int32_t bin = 0;
+                bool ok = false;
+                if (!c.all_outliers)
+                    ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
+                if (!ok && e0 + q < p.n) nb |= 1u << q;
+                b[q] = ok ? bin : 0;
             }
+            if (e0 + 4 <= p.n) {
+                __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(b[0], b[1], b[2], b[3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (e0 + q < p.n) p.bins[e0 + q] = b[q];
+            }
+            uint32_t w = nb << ((lane & 7) * 4);
+            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
+            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
+            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
+            if ((lane & 7) == 0) s_mask[v * (kBlock / 8) + warp * 4 + (lane >> 3)] = w;
+            nib[v] = nb;
         }
-    }
-    __syncthreads();
-
-    const uint64_t pbase = s_base + s_excl;
-#pragma unroll
-    for (int v = 0; v < kVpt; v++) {
-        if (nib[v]) {
-            const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-            const uint32_t mw = s_mask[word];
-            const uint32_t pre = s_wpre[word];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if ((nib[v] >> k) & 1u) {
-                    const int bit = (lane & 7) * 4 + k;
-                    const uint64_t rank = pbase + pre + __popc(mw & ((1u << bit) - 1u));
-                    if (rank < p.cap) p.out[rank] = vals[v][k];
+        __syncthreads();
+        if (s_abort) break;
+        if (warp == 0) {
+            const uint64_t nwords = (p.n + 31) / 32;
+            const uint32_t agg = scan_mask_words<WPL>(s_mask, s_wpre, p.mask,
+                                                      (uint64_t)tile * WORDS + (uint64_t)lane * WPL,
+                                                      nwords, true);
+            if (lane == 0) lookback_publish(p.desc, tile, agg, s_epoch, p.scan);
+            const uint32_t excl = lookback_walk(p.desc, tile, agg, s_epoch, p.scan, &p.ws->err);
+            if (lane == 0) {
+                s_excl = excl;
+                if (tile == p.num_tiles - 1) {
+                    const uint64_t total = s_base + excl + agg;
+                    st_relaxed_u64(&p.hdr->outlier_count, total);
+                    if (total > p.cap) atomicOr(&p.ws->err, LCQ_STATUS_CAPACITY);
                 }
             }
         }
-    }
-
-    if (tid == 0) {
-        if (tile == 0 && p.first_chunk) {
+        __syncthreads();
+        const uint64_t pbase = s_base + s_excl;
+#pragma unroll
+        for (int v = 0; v < VPT; v++) {
+            if (nib[v]) {
+                const int off = v * (kBlock * 4) + tid * 4;
+                const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
+                const uint32_t mw = s_mask[word];
+                const uint32_t pre = s_wpre[word];
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    if ((nib[v] >> q) & 1u) {
+                        const int bit = (lane & 7) * 4 + q;
+                        const uint64_t rank = pbase + pre + __popc(mw & ((1u << bit) - 1u));
+                        const T xv = from_smem ? st[off + q] : p.in[tbase + off + q];
+                        if (rank < p.cap) p.out[rank] = F::bits(xv);
+                    }
+                }
+            }
+        }
+        if (tid == 0 && tile == 0 && p.first_chunk) {
             lcq_header* h = p.hdr;
             h->magic = LCQ_MAGIC;
             h->dtype = p.dtype;
@@ -244,8 +318,11 @@ __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
             }
             h->reserved = 0;
         }
-        finish_launch(p.ws, s_epoch, &p.hdr->status, p.first_chunk != 0);
+        fence_proxy_async_smem();
+        __syncthreads();  // stage s, s_mask and s_wpre are free again
+        if (tid == 0) issue(s);
     }
+    if (tid == 0) finish_launch(p.ws, s_epoch, &p.hdr->status, p.first_chunk != 0);
 }
 
 // Header for an empty input (no tiles to launch).
@@ -425,7 +502,10 @@ __global__ void __launch_bounds__(kBlock) k_minmax(MParams<T> p) {
 }
 
 // ---------------------------------------------------------------------------
-// Dequantize kernel
+// Dequantize kernel: persistent CTAs; bins and mask words of each tile stream
+// into shared-memory stages.  A tile publishes its outlier count before it
+// reconstructs its values, writes the reconstructions of the quantized values
+// at once, and patches the outliers after the lookback walk.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct DParams {
@@ -445,17 +525,40 @@ struct DParams {
     ScanCfg scan;
 };
 
-template <typename T>
+template <typename T, int VPT, int STAGES>
 __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
     using F = Ty<T>;
-    using U = typename F::U;
-    __shared__ uint32_t s_mask[kWords];
-    __shared__ uint32_t s_wpre[kWords];
-    __shared__ uint32_t s_tile, s_epoch, s_excl, s_ok;
+    constexpr int TILE = kBlock * 4 * VPT;
+    constexpr int WORDS = TILE / 32;
+    constexpr int WPL = WORDS / 32;
+    constexpr int STAGE_WORDS = TILE + WORDS;  // bins then mask words
+    extern __shared__ __align__(128) unsigned char dsmem[];
+    uint32_t* sbuf = reinterpret_cast<uint32_t*>(dsmem);
+    __shared__ __align__(8) uint64_t s_bar[STAGES];
+    __shared__ uint32_t s_stile[STAGES];
+    __shared__ uint32_t s_gmask[WORDS];  // mask words of a ragged tile
+    __shared__ uint32_t s_wpre[WORDS];
+    __shared__ uint32_t s_epoch, s_excl, s_ok, s_abort, s_agg;
     __shared__ uint64_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t full_tiles = (uint32_t)(p.n / TILE);
+
+    auto issue = [&](int s) {
+        const uint32_t t = atomicAdd(&p.ws->ticket, 1u);
+        s_stile[s] = t;
+        if (t < full_tiles) {
+            uint32_t* st = sbuf + (size_t)s * STAGE_WORDS;
+            mbar_arrive_expect_tx(&s_bar[s], (TILE + WORDS) * 4);
+            bulk_g2s(st, p.bins + (uint64_t)t * TILE, TILE * 4, &s_bar[s]);
+            bulk_g2s(st + TILE, p.mask + (uint64_t)t * WORDS, WORDS * 4, &s_bar[s]);
+        } else if (t < p.num_tiles) {
+            mbar_arrive(&s_bar[s]);
+        }
+    };
+
     if (tid == 0) {
-        s_tile = atomicAdd(&p.ws->ticket, 1u);
+        for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
+        mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
         s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.ws->carry);
         // decode only a complete, error-free encoding of exactly these arrays
@@ -463,91 +566,106 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                         p.hdr->n == p.n_total && p.hdr->status == 0u &&
                         (p.outl != nullptr || p.hdr->outlier_count == 0);
         s_ok = ok;
+        s_abort = 0;
         if (!ok) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
-    }
-    const Consts<T> c = consts_from_header<T>(p.hdr);
-    const bool rel = p.hdr->bound_type == LCQ_REL;
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    const uint64_t tbase = (uint64_t)tile * kTile;
-    if (warp == 0) {
-        const uint64_t nwords = (p.n + 31) / 32;
-        const uint64_t gw = (uint64_t)tile * kWords + (uint64_t)lane * kWpl;
-        uint32_t wv[kWpl];
-        if (gw + kWpl <= nwords) {
-            const uint4 a = __ldcs(reinterpret_cast<const uint4*>(p.mask + gw));
-            wv[0] = a.x; wv[1] = a.y; wv[2] = a.z; wv[3] = a.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < kWpl; j++) wv[j] = (gw + j < nwords) ? p.mask[gw + j] : 0u;
-        }
-        uint32_t cnt = 0, loc[kWpl];
-#pragma unroll
-        for (int j = 0; j < kWpl; j++) {
-            s_mask[lane * kWpl + j] = wv[j];
-            loc[j] = cnt;
-            cnt += __popc(wv[j]);
-        }
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t ex = incl - cnt;
-#pragma unroll
-        for (int j = 0; j < kWpl; j++) s_wpre[lane * kWpl + j] = ex + loc[j];
-        const uint32_t agg = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const uint32_t excl = lookback_exclusive(p.desc, tile, agg, s_epoch, p.scan, &p.ws->err);
-        if (lane == 0) {
-            s_excl = excl;
-            if (tile == p.num_tiles - 1) st_relaxed_u64(&p.ws->carry, s_base + excl + agg);
-        }
+        else
+            for (int s = 0; s < STAGES; s++) issue(s);
     }
     __syncthreads();
     if (s_ok) {
-        const uint64_t pbase = s_base + s_excl;
+        const Consts<T> c = consts_from_header<T>(p.hdr);
+        const bool rel = p.hdr->bound_type == LCQ_REL;
         const uint64_t avail = p.hdr->outlier_count;
         bool overrun = false;
-#pragma unroll
-        for (int v = 0; v < kVpt; v++) {
-            const uint64_t e0 = tbase + (uint64_t)v * (kBlock * 4) + (uint64_t)tid * 4;
-            if (e0 >= p.n) continue;
-            const bool full = e0 + 4 <= p.n;
-            int32_t b[4];
-            if (full) {
-                const int4 a = __ldcs(reinterpret_cast<const int4*>(p.bins + e0));
-                b[0] = a.x; b[1] = a.y; b[2] = a.z; b[3] = a.w;
-            } else {
-#pragma unroll
-                for (int k = 0; k < 4; k++) b[k] = (e0 + k < p.n) ? p.bins[e0 + k] : 0;
+        for (uint32_t k = 0;; k++) {
+            const int s = (int)(k % STAGES);
+            const uint32_t tile = s_stile[s];
+            if (tile >= p.num_tiles) break;
+            const bool from_smem = tile < full_tiles;
+            if (!mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit)) {
+                atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
+                s_abort = 1;
             }
-            const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-            const uint32_t mw = s_mask[word];
-            const uint32_t nb = (mw >> ((lane & 7) * 4)) & 0xFu;
-            T x[4];
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if ((nb >> k) & 1u) {
-                    const int bit = (lane & 7) * 4 + k;
-                    const uint64_t rank = pbase + s_wpre[word] + __popc(mw & ((1u << bit) - 1u));
-                    if (rank < avail) {
-                        x[k] = F::from_bits(p.outl[rank]);
-                    } else {  // mask has more bits than the header's count
-                        x[k] = T(0);
-                        overrun = true;
-                    }
-                } else {
-                    x[k] = rel ? rel_recon<T>(b[k], c) : abs_recon<T>(b[k], c);
+            const uint32_t* sb = sbuf + (size_t)s * STAGE_WORDS;
+            const uint64_t tbase = (uint64_t)tile * TILE;
+            const uint64_t nwords = (p.n + 31) / 32;
+            if (!from_smem) {  // ragged last tile: mask words from global memory
+                for (int w = tid; w < WORDS; w += kBlock) {
+                    const uint64_t gw = (uint64_t)tile * WORDS + w;
+                    s_gmask[w] = gw < nwords ? p.mask[gw] : 0u;
+                }
+                __syncthreads();
+            }
+            const uint32_t* words = from_smem ? sb + TILE : s_gmask;
+            if (warp == 0) {
+                const uint32_t agg = scan_mask_words<WPL>(words, s_wpre, nullptr, 0, 0, false);
+                if (lane == 0) {
+                    s_agg = agg;
+                    lookback_publish(p.desc, tile, agg, s_epoch, p.scan);
                 }
             }
-            if (full) {
-                Vec4<T>::store(p.out + e0, x);
-            } else {
+            uint32_t nib[VPT];
 #pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (e0 + k < p.n) p.out[e0 + k] = x[k];
+            for (int v = 0; v < VPT; v++) {
+                const int off = v * (kBlock * 4) + tid * 4;
+                const uint64_t e0 = tbase + off;
+                const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
+                const uint32_t nb = (words[word] >> ((lane & 7) * 4)) & 0xFu;
+                nib[v] = nb;
+                int32_t b[4];
+                if (from_smem) {
+                    const int4 a = *reinterpret_cast<const int4*>(sb + off);
+                    b[0] = a.x; b[1] = a.y; b[2] = a.z; b[3] = a.w;
+                } else if (e0 + 4 <= p.n) {
+                    const int4 a = __ldcs(reinterpret_cast<const int4*>(p.bins + e0));
+                    b[0] = a.x; b[1] = a.y; b[2] = a.z; b[3] = a.w;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++) b[q] = (e0 + q < p.n) ? p.bins[e0 + q] : 0;
+                }
+                T x[4];
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    x[q] = ((nb >> q) & 1u) ? T(0) : (rel ? rel_recon<T>(b[q], c) : abs_recon<T>(b[q], c));
+                if (e0 + 4 <= p.n) {
+                    Vec4<T>::store(p.out + e0, x);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (e0 + q < p.n) p.out[e0 + q] = x[q];
+                }
             }
+            __syncthreads();
+            if (s_abort) break;
+            if (warp == 0) {
+                const uint32_t excl = lookback_walk(p.desc, tile, s_agg, s_epoch, p.scan, &p.ws->err);
+                if (lane == 0) {
+                    s_excl = excl;
+                    if (tile == p.num_tiles - 1) st_relaxed_u64(&p.ws->carry, s_base + excl + s_agg);
+                }
+            }
+            __syncthreads();
+            const uint64_t pbase = s_base + s_excl;
+#pragma unroll
+            for (int v = 0; v < VPT; v++) {
+                if (nib[v]) {
+                    const int off = v * (kBlock * 4) + tid * 4;
+                    const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
+                    const uint32_t mw = words[word];
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        if ((nib[v] >> q) & 1u) {
+                            const int bit = (lane & 7) * 4 + q;
+                            const uint64_t rank = pbase + s_wpre[word] + __popc(mw & ((1u << bit) - 1u));
+                            if (rank < avail) p.out[tbase + off + q] = F::from_bits(p.outl[rank]);
+                            else overrun = true;
+                        }
+                    }
+                }
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) issue(s);
         }
         if (overrun) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
     }
@@ -564,7 +682,65 @@ __global__ void k_status_only(uint32_t* status, uint32_t bits) {
 // ---------------------------------------------------------------------------
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-static uint64_t tiles_for(uint64_t n) { return (n + kTile - 1) / kTile; }
+static uint64_t tiles_for(uint64_t n) { return (n + kTileMin - 1) / kTileMin; }
+static uint64_t tiles_of(uint64_t n, int tile) { return (n + tile - 1) / tile; }
+
+// Persistent grid: as many CTAs as fit on the device at once (cached per
+// kernel instantiation and device), never more than there are tiles.
+struct GridCache {
+    int blocks_per_sm[16];
+    bool set[16];
+};
+
+static int device_sms(int dev) {
+    static int sms[16] = {0};
+    if (dev < 0 || dev >= 16) return 148;
+    if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+    return sms[dev] ? sms[dev] : 148;
+}
+
+template <typename K>
+static int persistent_blocks(K kernel, size_t dyn_smem, GridCache& cache) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int slot = (dev >= 0 && dev < 16) ? dev : 0;
+    if (!cache.set[slot]) {
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, dyn_smem);
+        cache.blocks_per_sm[slot] = b > 0 ? b : 1;
+        cache.set[slot] = true;
+    }
+    return cache.blocks_per_sm[slot] * device_sms(dev);
+}
+
+template <typename T, int MODE, int VPT, int STAGES>
+static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
+    static GridCache cache{};
+    constexpr int TILE = kBlock * 4 * VPT;
+    const size_t smem = (size_t)STAGES * TILE * sizeof(T);
+    auto kern = k_quantize<T, MODE, VPT, STAGES>;
+    QParams<T> q = p;
+    q.num_tiles = (uint32_t)tiles_of(p.n, TILE);
+    uint64_t grid = (uint64_t)persistent_blocks(kern, smem, cache);
+    if (grid > q.num_tiles) grid = q.num_tiles;
+    kern<<<(unsigned)grid, kBlock, smem, st>>>(q);
+    return cudaPeekAtLastError();
+}
+
+template <typename T, int VPT, int STAGES>
+static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
+    static GridCache cache{};
+    constexpr int TILE = kBlock * 4 * VPT;
+    const size_t smem = (size_t)STAGES * (TILE + TILE / 32) * 4;
+    auto kern = k_dequantize<T, VPT, STAGES>;
+    DParams<T> q = p;
+    q.num_tiles = (uint32_t)tiles_of(p.n, TILE);
+    uint64_t grid = (uint64_t)persistent_blocks(kern, smem, cache);
+    if (grid > q.num_tiles) grid = q.num_tiles;
+    kern<<<(unsigned)grid, kBlock, smem, st>>>(q);
+    return cudaPeekAtLastError();
+}
 
 static size_t desc_bytes(uint64_t n) {
     const uint64_t per_chunk = n < kChunk ? n : kChunk;
@@ -703,7 +879,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.ws = head;
         p.desc = desc;
         p.n = len;
-        p.num_tiles = (uint32_t)tiles_for(len);
+        p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
         p.consts_from_hdr = noa;
         p.c = c;
@@ -713,11 +889,15 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.eb = eb;
         p.eb_abs = eb_abs;
         p.n_total = n;
-        if (bt == LCQ_REL)
-            k_quantize<T, LCQ_REL><<<p.num_tiles, kBlock, 0, st>>>(p);
-        else
-            k_quantize<T, LCQ_ABS><<<p.num_tiles, kBlock, 0, st>>>(p);
-        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+        cudaError_t e;
+        if (sizeof(T) == 4) {
+            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF32, kStagesF32>(p, st)
+                              : launch_quantize<T, LCQ_ABS, kVptF32, kStagesF32>(p, st);
+        } else {
+            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF64, kStagesF64>(p, st)
+                              : launch_quantize<T, LCQ_ABS, kVptF64, kStagesF64>(p, st);
+        }
+        if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
 }
@@ -746,11 +926,12 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         p.n = len;
         p.n_total = n;
         p.dtype = sizeof(T) == 4 ? LCQ_F32 : LCQ_F64;
-        p.num_tiles = (uint32_t)tiles_for(len);
+        p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
         p.scan = g_scan;
-        k_dequantize<T><<<p.num_tiles, kBlock, 0, st>>>(p);
-        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+        const cudaError_t e = sizeof(T) == 4 ? launch_dequantize<T, kVptF32, kStagesF32>(p, st)
+                                             : launch_dequantize<T, kVptF64, kStagesF64>(p, st);
+        if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
 }
