@@ -247,53 +247,70 @@ __device__ __forceinline__ void lookback_publish(uint64_t* desc, uint32_t tile, 
 }
 
 // Called by all 32 lanes of one warp after lookback_publish.  Walks back over
-// the predecessors (32 at a time) until an inclusive prefix is found,
-// publishes the tile's inclusive prefix and returns its exclusive prefix.
-// Every wait is bounded: after cfg.spin_limit polls a missing predecessor is
-// counted as 0 and LCQ_STATUS_TIMEOUT is raised, so the scan always ends.
+// the predecessors, kLbPerLane x 32 descriptors per round trip (lane j reads
+// the descriptors j*kLbPerLane .. j*kLbPerLane+kLbPerLane-1 places back,
+// closest first), until an inclusive prefix is found; publishes the tile's
+// inclusive prefix and returns its exclusive prefix.  Every wait is bounded:
+// after cfg.spin_limit polls a missing predecessor is counted as 0 and
+// LCQ_STATUS_TIMEOUT is raised, so the scan always ends.
+constexpr int kLbPerLane = 4;
+
 __device__ __forceinline__ uint32_t lookback_walk(uint64_t* desc, uint32_t tile, uint32_t agg,
                                                   uint32_t epoch, const ScanCfg& cfg, uint32_t* err) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     if (tile == 0) return 0;
-    const uint64_t tag = (uint64_t)(epoch & kEpochMask) << 32;
+    const uint32_t ep = epoch & kEpochMask;
+    const uint64_t tag = (uint64_t)ep << 32;
     uint32_t excl = 0;
-    int64_t pos = (int64_t)tile - 1 - lane;
+    int64_t pos0 = (int64_t)tile - 1 - (int64_t)lane * kLbPerLane;  // closest descriptor of this lane
     bool timed_out = false;
     while (true) {
         uint32_t spins = 0;
         unsigned ns = 32;
-        uint32_t state, val;
+        uint32_t lane_sum, first_p, invalid_before;
         while (true) {
-            if (pos >= 0) {
-                const uint64_t d = ld_relaxed_u64(&desc[pos]);
-                const bool fresh = (uint32_t)((d >> 32) & kEpochMask) == (epoch & kEpochMask);
-                state = fresh ? (uint32_t)(d >> 62) : 0u;
-                val = fresh ? (uint32_t)d : 0u;
-            } else {
-                state = 2u;  // before tile 0: an empty prefix
-                val = 0u;
+            uint64_t d[kLbPerLane];
+#pragma unroll
+            for (int i = 0; i < kLbPerLane; i++) {
+                const int64_t pos = pos0 - i;
+                d[i] = pos >= 0 ? ld_relaxed_u64(&desc[pos]) : (kStPre | tag);  // before tile 0: empty prefix
             }
-            // only the lanes closer than the nearest inclusive prefix matter
-            const uint32_t pm = __ballot_sync(FULL, state == 2u);
-            const uint32_t need = pm ? ((pm & (0u - pm)) - 1u) : FULL;
-            if ((__ballot_sync(FULL, state == 0u) & need) == 0u) break;
+            lane_sum = 0;
+            first_p = kLbPerLane;
+            invalid_before = 0;
+#pragma unroll
+            for (int i = 0; i < kLbPerLane; i++) {
+                const bool fresh = (uint32_t)((d[i] >> 32) & kEpochMask) == ep;
+                const uint32_t st = fresh ? (uint32_t)(d[i] >> 62) : 0u;
+                if (first_p == kLbPerLane) {
+                    if (st == 0u) {
+                        if (timed_out) first_p = i;  // give up on it: count 0, stop here
+                        else invalid_before = 1;
+                    } else {
+                        lane_sum += (uint32_t)d[i];
+                        if (st == 2u) first_p = i;
+                    }
+                }
+            }
+            const uint32_t pm = __ballot_sync(FULL, first_p < kLbPerLane);
+            const uint32_t need = pm ? ((pm & (0u - pm)) << 1) - 1u : FULL;  // lanes up to the first prefix
+            if ((__ballot_sync(FULL, invalid_before != 0u) & need) == 0u) break;
             if (++spins > cfg.spin_limit) {
                 timed_out = true;
-                if (state == 0u) { state = 2u; val = 0u; }
-                break;
+                continue;  // re-evaluate once with missing predecessors counted as 0
             }
             __nanosleep(ns);
             ns = ns < 256u ? ns * 2u : 256u;
         }
-        const uint32_t pmask = __ballot_sync(FULL, state == 2u);
+        const uint32_t pmask = __ballot_sync(FULL, first_p < kLbPerLane);
         if (pmask) {
             const int first = __ffs(pmask) - 1;
-            excl += __reduce_add_sync(FULL, lane <= first ? val : 0u);
+            excl += __reduce_add_sync(FULL, lane <= first ? lane_sum : 0u);
             break;
         }
-        excl += __reduce_add_sync(FULL, val);
-        pos -= 32;
+        excl += __reduce_add_sync(FULL, lane_sum);
+        pos0 -= 32 * kLbPerLane;
     }
     if (lane == 0) {
         if ((uint64_t)tile != cfg.drop_tile) st_relaxed_u64(&desc[tile], kStPre | tag | (uint32_t)(excl + agg));

@@ -175,10 +175,16 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
+// Ring protocol shared by the streaming kernels: the k-th tile a CTA handles
+// sits in stage k % STAGES.  Tiles are requested one at a time (one at the
+// start of an iteration while the ring fills, one after each compute phase),
+// so that the global ticket order follows the order in which CTAs reach their
+// tiles; each CTA processes its tiles in ticket order, which the lookback
+// needs for progress.  A stage is released as soon as its tile is computed,
+// before the lookback walk, so the walk overlaps the copies in flight.
 template <typename T, int MODE, int VPT, int STAGES>
 __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
     using F = Ty<T>;
-    using U = typename F::U;
     constexpr int TILE = kBlock * 4 * VPT;
     constexpr int WORDS = TILE / 32;
     constexpr int WPL = WORDS / 32;
@@ -187,17 +193,19 @@ __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
     T* sbuf = reinterpret_cast<T*>(dsmem);
     __shared__ __align__(8) uint64_t s_bar[STAGES];
     __shared__ uint32_t s_stile[STAGES];
-    __shared__ uint32_t s_mask[WORDS];
-    __shared__ uint32_t s_wpre[WORDS];
-    __shared__ uint32_t s_epoch, s_excl, s_abort;
+    __shared__ uint32_t s_mask[2][WORDS];
+    __shared__ uint32_t s_wpre[2][WORDS];
+    __shared__ uint32_t s_epoch, s_excl, s_abort, s_filled;
     __shared__ uint64_t s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t full_tiles = (uint32_t)(p.n / TILE);
 
-    auto issue = [&](int s) {  // thread 0: next ticket into stage s
+    auto issue = [&]() {  // thread 0: request the next tile into the next stage
+        const int s = (int)(s_filled % STAGES);
         const uint32_t t = atomicAdd(&p.ws->ticket, 1u);
         s_stile[s] = t;
+        s_filled++;
         if (t < full_tiles) {
             mbar_arrive_expect_tx(&s_bar[s], TILE * sizeof(T));
             bulk_g2s(sbuf + (size_t)s * TILE, p.in + (uint64_t)t * TILE, TILE * sizeof(T), &s_bar[s]);
@@ -212,21 +220,22 @@ __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
         s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.hdr->outlier_count);
         s_abort = 0;
-        for (int s = 0; s < STAGES; s++) issue(s);
+        s_filled = 0;
+        issue();
     }
     const Consts<T> c = p.consts_from_hdr ? consts_from_header<T>(p.hdr) : p.c;
     __syncthreads();
 
     for (uint32_t k = 0;; k++) {
         const int s = (int)(k % STAGES);
+        const int mb = (int)(k & 1u);
+        if (tid == 0 && s_filled < k + STAGES) issue();  // ring fill, one tile per step
         const uint32_t tile = s_stile[s];
         if (tile >= p.num_tiles) break;
         const bool from_smem = tile < full_tiles;
-        if (from_smem && !mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit)) {
+        if (!mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit)) {
             atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
             s_abort = 1;
-        } else if (!from_smem) {
-            mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit);
         }
         const T* st = sbuf + (size_t)s * TILE;
         const uint64_t tbase = (uint64_t)tile * TILE;
@@ -259,14 +268,16 @@ __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
             w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
             w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
             w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
-            if ((lane & 7) == 0) s_mask[v * (kBlock / 8) + warp * 4 + (lane >> 3)] = w;
+            if ((lane & 7) == 0) s_mask[mb][v * (kBlock / 8) + warp * 4 + (lane >> 3)] = w;
             nib[v] = nb;
         }
-        __syncthreads();
+        fence_proxy_async_smem();
+        __syncthreads();  // stage s consumed; the tile's mask words are complete
         if (s_abort) break;
+        if (tid == 0 && s_filled < k + 1 + STAGES) issue();  // refill stage s
         if (warp == 0) {
             const uint64_t nwords = (p.n + 31) / 32;
-            const uint32_t agg = scan_mask_words<WPL>(s_mask, s_wpre, p.mask,
+            const uint32_t agg = scan_mask_words<WPL>(s_mask[mb], s_wpre[mb], p.mask,
                                                       (uint64_t)tile * WORDS + (uint64_t)lane * WPL,
                                                       nwords, true);
             if (lane == 0) lookback_publish(p.desc, tile, agg, s_epoch, p.scan);
@@ -281,21 +292,22 @@ __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
             }
         }
         __syncthreads();
+        // outliers: the raw input bits, re-read from global memory (the tile
+        // was read moments ago, so these reads hit L2)
         const uint64_t pbase = s_base + s_excl;
 #pragma unroll
         for (int v = 0; v < VPT; v++) {
             if (nib[v]) {
                 const int off = v * (kBlock * 4) + tid * 4;
                 const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-                const uint32_t mw = s_mask[word];
-                const uint32_t pre = s_wpre[word];
+                const uint32_t mw = s_mask[mb][word];
+                const uint32_t pre = s_wpre[mb][word];
 #pragma unroll
                 for (int q = 0; q < 4; q++) {
                     if ((nib[v] >> q) & 1u) {
                         const int bit = (lane & 7) * 4 + q;
                         const uint64_t rank = pbase + pre + __popc(mw & ((1u << bit) - 1u));
-                        const T xv = from_smem ? st[off + q] : p.in[tbase + off + q];
-                        if (rank < p.cap) p.out[rank] = F::bits(xv);
+                        if (rank < p.cap) p.out[rank] = F::bits(p.in[tbase + off + q]);
                     }
                 }
             }
@@ -318,10 +330,8 @@ __global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
             }
             h->reserved = 0;
         }
-        fence_proxy_async_smem();
-        __syncthreads();  // stage s, s_mask and s_wpre are free again
-        if (tid == 0) issue(s);
     }
+    __syncthreads();
     if (tid == 0) finish_launch(p.ws, s_epoch, &p.hdr->status, p.first_chunk != 0);
 }
 
@@ -536,16 +546,18 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
     uint32_t* sbuf = reinterpret_cast<uint32_t*>(dsmem);
     __shared__ __align__(8) uint64_t s_bar[STAGES];
     __shared__ uint32_t s_stile[STAGES];
-    __shared__ uint32_t s_gmask[WORDS];  // mask words of a ragged tile
-    __shared__ uint32_t s_wpre[WORDS];
-    __shared__ uint32_t s_epoch, s_excl, s_ok, s_abort, s_agg;
+    __shared__ uint32_t s_words[2][WORDS];  // the tile's mask words, kept past the stage's release
+    __shared__ uint32_t s_wpre[2][WORDS];
+    __shared__ uint32_t s_epoch, s_excl, s_ok, s_abort, s_agg, s_filled;
     __shared__ uint64_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t full_tiles = (uint32_t)(p.n / TILE);
 
-    auto issue = [&](int s) {
+    auto issue = [&]() {
+        const int s = (int)(s_filled % STAGES);
         const uint32_t t = atomicAdd(&p.ws->ticket, 1u);
         s_stile[s] = t;
+        s_filled++;
         if (t < full_tiles) {
             uint32_t* st = sbuf + (size_t)s * STAGE_WORDS;
             mbar_arrive_expect_tx(&s_bar[s], (TILE + WORDS) * 4);
@@ -567,18 +579,21 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                         (p.outl != nullptr || p.hdr->outlier_count == 0);
         s_ok = ok;
         s_abort = 0;
+        s_filled = 0;
         if (!ok) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
-        else
-            for (int s = 0; s < STAGES; s++) issue(s);
+        else issue();
     }
     __syncthreads();
     if (s_ok) {
         const Consts<T> c = consts_from_header<T>(p.hdr);
         const bool rel = p.hdr->bound_type == LCQ_REL;
         const uint64_t avail = p.hdr->outlier_count;
+        const uint64_t nwords = (p.n + 31) / 32;
         bool overrun = false;
         for (uint32_t k = 0;; k++) {
             const int s = (int)(k % STAGES);
+            const int mb = (int)(k & 1u);
+            if (tid == 0 && s_filled < k + STAGES) issue();
             const uint32_t tile = s_stile[s];
             if (tile >= p.num_tiles) break;
             const bool from_smem = tile < full_tiles;
@@ -588,17 +603,21 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
             }
             const uint32_t* sb = sbuf + (size_t)s * STAGE_WORDS;
             const uint64_t tbase = (uint64_t)tile * TILE;
-            const uint64_t nwords = (p.n + 31) / 32;
-            if (!from_smem) {  // ragged last tile: mask words from global memory
-                for (int w = tid; w < WORDS; w += kBlock) {
+            // the tile's mask words -> s_words[mb] (from the stage, or from
+            // global memory for the ragged last tile)
+            for (int w = tid; w < WORDS; w += kBlock) {
+                uint32_t word;
+                if (from_smem) {
+                    word = sb[TILE + w];
+                } else {
                     const uint64_t gw = (uint64_t)tile * WORDS + w;
-                    s_gmask[w] = gw < nwords ? p.mask[gw] : 0u;
+                    word = gw < nwords ? p.mask[gw] : 0u;
                 }
-                __syncthreads();
+                s_words[mb][w] = word;
             }
-            const uint32_t* words = from_smem ? sb + TILE : s_gmask;
+            __syncthreads();
             if (warp == 0) {
-                const uint32_t agg = scan_mask_words<WPL>(words, s_wpre, nullptr, 0, 0, false);
+                const uint32_t agg = scan_mask_words<WPL>(s_words[mb], s_wpre[mb], nullptr, 0, 0, false);
                 if (lane == 0) {
                     s_agg = agg;
                     lookback_publish(p.desc, tile, agg, s_epoch, p.scan);
@@ -610,7 +629,7 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                 const int off = v * (kBlock * 4) + tid * 4;
                 const uint64_t e0 = tbase + off;
                 const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-                const uint32_t nb = (words[word] >> ((lane & 7) * 4)) & 0xFu;
+                const uint32_t nb = (s_words[mb][word] >> ((lane & 7) * 4)) & 0xFu;
                 nib[v] = nb;
                 int32_t b[4];
                 if (from_smem) {
@@ -635,8 +654,10 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                         if (e0 + q < p.n) p.out[e0 + q] = x[q];
                 }
             }
-            __syncthreads();
+            fence_proxy_async_smem();
+            __syncthreads();  // stage s consumed
             if (s_abort) break;
+            if (tid == 0 && s_filled < k + 1 + STAGES) issue();
             if (warp == 0) {
                 const uint32_t excl = lookback_walk(p.desc, tile, s_agg, s_epoch, p.scan, &p.ws->err);
                 if (lane == 0) {
@@ -651,21 +672,18 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                 if (nib[v]) {
                     const int off = v * (kBlock * 4) + tid * 4;
                     const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-                    const uint32_t mw = words[word];
+                    const uint32_t mw = s_words[mb][word];
 #pragma unroll
                     for (int q = 0; q < 4; q++) {
                         if ((nib[v] >> q) & 1u) {
                             const int bit = (lane & 7) * 4 + q;
-                            const uint64_t rank = pbase + s_wpre[word] + __popc(mw & ((1u << bit) - 1u));
+                            const uint64_t rank = pbase + s_wpre[mb][word] + __popc(mw & ((1u << bit) - 1u));
                             if (rank < avail) p.out[tbase + off + q] = F::from_bits(p.outl[rank]);
                             else overrun = true;
                         }
                     }
                 }
             }
-            fence_proxy_async_smem();
-            __syncthreads();
-            if (tid == 0) issue(s);
         }
         if (overrun) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
     }
