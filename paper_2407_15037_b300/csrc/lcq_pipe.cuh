@@ -67,3 +67,45 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 }
 
 }  // namespace lcq
+
+namespace lcq {
+
+// Named barrier over the first `nthreads` threads of the CTA (the compute
+// warps of a warp-specialised kernel); id 0 is reserved for __syncthreads.
+__device__ __forceinline__ void named_barrier_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Bounded wait that also gives up when another thread of the CTA raised the
+// abort flag (so that every warp leaves the kernel after one timeout).
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                                   volatile uint32_t* abort_flag) {
+    for (uint32_t i = 0; i < limit; i++) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((i & 63u) == 63u && *abort_flag) return false;
+    }
+    return false;
+}
+
+}  // namespace lcq
+
+namespace lcq {
+
+// Named barrier that also ORs a predicate over its participants: every
+// participant gets the same answer, so a decision taken from it (such as
+// leaving the loop after a timeout) is uniform and no thread is left waiting
+// at a later barrier.
+__device__ __forceinline__ bool named_barrier_or(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+}  // namespace lcq

@@ -38,8 +38,8 @@ constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (s
 
 // Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
 // the depth of the shared-memory stage ring.
-constexpr int kVptF32 = 8, kStagesF32 = 3;      // 8192-value tiles, 32 KB stages
-constexpr int kVptF64 = 4, kStagesF64 = 3;      // 4096-value tiles, 32 KB stages
+constexpr int kVptF32 = 8, kStagesF32 = 3, kSubF32 = 4;  // 8192-value stages (32 KB), 32K-value scan tiles
+constexpr int kVptF64 = 4, kStagesF64 = 3, kSubF64 = 4;  // 4096-value stages (32 KB), 16K-value scan tiles
 
 static ScanCfg g_scan = {kDefaultSpin, ~0ull};
 
@@ -175,160 +175,225 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
-// Ring protocol shared by the streaming kernels: the k-th tile a CTA handles
-// sits in stage k % STAGES.  Tiles are requested one at a time (one at the
-// start of an iteration while the ring fills, one after each compute phase),
-// so that the global ticket order follows the order in which CTAs reach their
-// tiles; each CTA processes its tiles in ticket order, which the lookback
-// needs for progress.  A stage is released as soon as its tile is computed,
-// before the lookback walk, so the walk overlaps the copies in flight.
-template <typename T, int MODE, int VPT, int STAGES>
-__global__ void __launch_bounds__(kBlock) k_quantize(QParams<T> p) {
+// Warp-specialised streaming kernels.  A CTA has 8 compute warps and one
+// scan warp.  The compute warps stream the CTA's tiles through a ring of
+// shared-memory stages (bulk asynchronous copies, one sub-tile per stage) and
+// never wait on the cross-CTA scan: when a scan tile (SUB sub-tiles) is done
+// they hand its mask words to the scan warp and go on.  The scan warp scans
+// the words, publishes the tile's count, walks back over the predecessors
+// (bounded decoupled lookback) and posts the tile's payload offset; the
+// compute warps write that tile's outliers one scan tile later.
+//
+// Tickets are taken one scan tile at a time as the ring fills, so the global
+// ticket order follows the order in which CTAs reach their tiles, and every
+// CTA handles its tiles in ticket order (needed for the lookback to progress).
+constexpr int kComputeThreads = 256;
+constexpr int kSpecThreads = kComputeThreads + 32;
+constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
+template <typename T, int MODE, int VPT, int STAGES, int SUB>
+__global__ void __launch_bounds__(kSpecThreads) k_quantize(QParams<T> p) {
     using F = Ty<T>;
-    constexpr int TILE = kBlock * 4 * VPT;
+    constexpr int STILE = kComputeThreads * 4 * VPT;  // values per stage (sub-tile)
+    constexpr int TILE = STILE * SUB;                  // values per scan tile
+    constexpr int SWORDS = STILE / 32;
     constexpr int WORDS = TILE / 32;
     constexpr int WPL = WORDS / 32;
     static_assert(WPL % 4 == 0, "whole uint4 mask stores per lane");
     extern __shared__ __align__(128) unsigned char dsmem[];
     T* sbuf = reinterpret_cast<T*>(dsmem);
-    __shared__ __align__(8) uint64_t s_bar[STAGES];
-    __shared__ uint32_t s_stile[STAGES];
+    __shared__ __align__(8) uint64_t s_stage_bar[STAGES];
+    __shared__ __align__(8) uint64_t s_full[2];
+    __shared__ __align__(8) uint64_t s_done[2];
+    __shared__ uint32_t s_stage_ticket[STAGES];
     __shared__ uint32_t s_mask[2][WORDS];
     __shared__ uint32_t s_wpre[2][WORDS];
-    __shared__ uint32_t s_epoch, s_excl, s_abort, s_filled;
+    __shared__ uint32_t s_jt[2];
+    __shared__ uint64_t s_pbase[2];
+    __shared__ uint32_t s_epoch, s_filled;
+    __shared__ volatile uint32_t s_abort;
     __shared__ uint64_t s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t full_tiles = (uint32_t)(p.n / TILE);
-
-    auto issue = [&]() {  // thread 0: request the next tile into the next stage
-        const int s = (int)(s_filled % STAGES);
-        const uint32_t t = atomicAdd(&p.ws->ticket, 1u);
-        s_stile[s] = t;
-        s_filled++;
-        if (t < full_tiles) {
-            mbar_arrive_expect_tx(&s_bar[s], TILE * sizeof(T));
-            bulk_g2s(sbuf + (size_t)s * TILE, p.in + (uint64_t)t * TILE, TILE * sizeof(T), &s_bar[s]);
-        } else if (t < p.num_tiles) {
-            mbar_arrive(&s_bar[s]);  // ragged last tile: read straight from global memory
-        }
-    };
+    const uint64_t full_sub = p.n / STILE;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
+        for (int s = 0; s < STAGES; s++) mbar_init(&s_stage_bar[s], 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&s_done[b], 1);
+        }
         mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
         s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.hdr->outlier_count);
         s_abort = 0;
         s_filled = 0;
-        issue();
     }
     const Consts<T> c = p.consts_from_hdr ? consts_from_header<T>(p.hdr) : p.c;
     __syncthreads();
 
-    for (uint32_t k = 0;; k++) {
-        const int s = (int)(k % STAGES);
-        const int mb = (int)(k & 1u);
-        if (tid == 0 && s_filled < k + STAGES) issue();  // ring fill, one tile per step
-        const uint32_t tile = s_stile[s];
-        if (tile >= p.num_tiles) break;
-        const bool from_smem = tile < full_tiles;
-        if (!mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit)) {
-            atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
-            s_abort = 1;
-        }
-        const T* st = sbuf + (size_t)s * TILE;
-        const uint64_t tbase = (uint64_t)tile * TILE;
-        uint32_t nib[VPT];
-#pragma unroll
-        for (int v = 0; v < VPT; v++) {
-            const int off = v * (kBlock * 4) + tid * 4;
-            const uint64_t e0 = tbase + off;
-            T x[4];
-            load4<T, VPT>(st, p.in, from_smem, off, e0, p.n, x);
-            int32_t b[4];
-            uint32_t nb = 0;
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                int32_t bin = 0;
-                bool ok = false;
-                if (!c.all_outliers)
-                    ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
-                if (!ok && e0 + q < p.n) nb |= 1u << q;
-                b[q] = ok ? bin : 0;
+    if (warp < kComputeThreads / 32) {
+        // ------------------------------------------------ compute warps --
+        auto issue = [&]() {  // thread 0: the next sub-tile of this CTA into the next stage
+            const uint32_t f = s_filled;
+            const int s = (int)(f % STAGES);
+            const uint32_t sub = f % SUB;
+            const uint32_t t = sub == 0 ? atomicAdd(&p.ws->ticket, 1u) : s_stage_ticket[(f - 1) % STAGES];
+            s_stage_ticket[s] = t;
+            s_filled = f + 1;
+            if (t < p.num_tiles) {
+                const uint64_t g = (uint64_t)t * SUB + sub;
+                if (g < full_sub) {
+                    mbar_arrive_expect_tx(&s_stage_bar[s], STILE * sizeof(T));
+                    bulk_g2s(sbuf + (size_t)s * STILE, p.in + g * STILE, STILE * sizeof(T), &s_stage_bar[s]);
+                } else {
+                    mbar_arrive(&s_stage_bar[s]);  // ragged or empty sub-tile: global reads
+                }
             }
-            if (e0 + 4 <= p.n) {
-                __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(b[0], b[1], b[2], b[3]));
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; q++)
-                    if (e0 + q < p.n) p.bins[e0 + q] = b[q];
+        };
+        // Returns true if the kernel must stop (uniform over the compute warps).
+        auto write_payload = [&](uint32_t jj) -> bool {  // all compute threads
+            const int bb = (int)(jj & 1u);
+            bool ok = mbar_wait_or_abort(&s_done[bb], (jj >> 1) & 1u, kMbarLimit, &s_abort);
+            if (!ok && !s_abort) {
+                atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
+                s_abort = 1;
             }
-            uint32_t w = nb << ((lane & 7) * 4);
-            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
-            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
-            w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
-            if ((lane & 7) == 0) s_mask[mb][v * (kBlock / 8) + warp * 4 + (lane >> 3)] = w;
-            nib[v] = nb;
+            if (named_barrier_or(1, kComputeThreads, !ok)) return true;
+            const uint64_t tb = (uint64_t)s_jt[bb] * TILE;
+            const uint64_t pbase = s_pbase[bb];
+            for (int w = tid; w < WORDS; w += kComputeThreads) {
+                uint32_t mw = s_mask[bb][w];
+                if (!mw) continue;
+                const uint32_t pre = s_wpre[bb][w];
+                uint32_t below = 0;
+                while (mw) {
+                    const int bit = __ffs(mw) - 1;
+                    mw &= mw - 1u;
+                    const uint64_t rank = pbase + pre + below++;
+                    // the tile was read moments ago, so this hits L2
+                    if (rank < p.cap) p.out[rank] = F::bits(p.in[tb + (uint64_t)w * 32 + bit]);
+                }
+            }
+            named_barrier_sync(1, kComputeThreads);  // buffer bb may be reused
+            return false;
+        };
+
+        if (tid == 0) issue();
+        named_barrier_sync(1, kComputeThreads);
+        uint32_t k = 0;
+        for (;; k++) {
+            const int s = (int)(k % STAGES);
+            const uint32_t sub = k % SUB;
+            const uint32_t j = k / SUB;
+            const int b = (int)(j & 1u);
+            if (tid == 0 && s_filled < k + STAGES) issue();  // ring fill
+            const uint32_t t = s_stage_ticket[s];
+            if (t >= p.num_tiles) break;
+            const uint64_t g = (uint64_t)t * SUB + sub;
+            const bool from_smem = g < full_sub;
+            if (!mbar_wait_or_abort(&s_stage_bar[s], (k / STAGES) & 1u, kMbarLimit, &s_abort)) {
+                if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
+            }
+            const T* st = sbuf + (size_t)s * STILE;
+            const uint64_t sbase = g * STILE;
+#pragma unroll
+            for (int v = 0; v < VPT; v++) {
+                const int off = v * (kComputeThreads * 4) + tid * 4;
+                const uint64_t e0 = sbase + off;
+                T x[4];
+                load4<T, VPT>(st, p.in, from_smem, off, e0, p.n, x);
+                int32_t bn[4];
+                uint32_t nb = 0;
+#pragma unroll
+                for (int q = 0; q < 4; q++) {
+                    int32_t bin = 0;
+                    bool ok = false;
+                    if (!c.all_outliers)
+                        ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
+                    if (!ok && e0 + q < p.n) nb |= 1u << q;
+                    bn[q] = ok ? bin : 0;
+                }
+                if (e0 + 4 <= p.n) {
+                    __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(bn[0], bn[1], bn[2], bn[3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        if (e0 + q < p.n) p.bins[e0 + q] = bn[q];
+                }
+                uint32_t w = nb << ((lane & 7) * 4);
+                w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
+                w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
+                w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
+                if ((lane & 7) == 0) s_mask[b][sub * SWORDS + v * (kComputeThreads / 8) + warp * 4 + (lane >> 3)] = w;
+            }
+            fence_proxy_async_smem();
+            bool stop = named_barrier_or(1, kComputeThreads, s_abort != 0);  // stage s consumed
+            if (stop) break;
+            if (tid == 0 && s_filled < k + 1 + STAGES) issue();  // refill stage s
+            if (sub == SUB - 1) {
+                if (tid == 0) {
+                    s_jt[b] = t;
+                    mbar_arrive(&s_full[b]);  // hand the scan tile to the scan warp
+                }
+                if (j >= 1 && write_payload(j - 1)) {
+                    stop = true;
+                    break;
+                }
+            }
         }
-        fence_proxy_async_smem();
-        __syncthreads();  // stage s consumed; the tile's mask words are complete
-        if (s_abort) break;
-        if (tid == 0 && s_filled < k + 1 + STAGES) issue();  // refill stage s
-        if (warp == 0) {
-            const uint64_t nwords = (p.n + 31) / 32;
-            const uint32_t agg = scan_mask_words<WPL>(s_mask[mb], s_wpre[mb], p.mask,
-                                                      (uint64_t)tile * WORDS + (uint64_t)lane * WPL,
-                                                      nwords, true);
-            if (lane == 0) lookback_publish(p.desc, tile, agg, s_epoch, p.scan);
-            const uint32_t excl = lookback_walk(p.desc, tile, agg, s_epoch, p.scan, &p.ws->err);
+        // k is uniform here; an aborted loop leaves the scan warp to notice
+        // the abort flag by itself
+        if (!named_barrier_or(1, kComputeThreads, s_abort != 0)) {
+            const uint32_t J = k / SUB;  // scan tiles handled by this CTA
+            if (!(J >= 1 && write_payload(J - 1)) && tid == 0) {
+                s_jt[J & 1u] = kNoTile;
+                mbar_arrive(&s_full[J & 1u]);
+            }
+        }
+    } else {
+        // --------------------------------------------------- scan warp --
+        const uint64_t nwords = (p.n + 31) / 32;
+        for (uint32_t j = 0;; j++) {
+            const int b = (int)(j & 1u);
+            if (!mbar_wait_or_abort(&s_full[b], (j >> 1) & 1u, kMbarLimit, &s_abort)) {
+                if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
+                break;
+            }
+            const uint32_t t = s_jt[b];
+            if (t == kNoTile) break;
+            const uint32_t agg = scan_mask_words<WPL>(s_mask[b], s_wpre[b], p.mask,
+                                                      (uint64_t)t * WORDS + (uint64_t)lane * WPL, nwords, true);
+            if (lane == 0) lookback_publish(p.desc, t, agg, s_epoch, p.scan);
+            const uint32_t excl = lookback_walk(p.desc, t, agg, s_epoch, p.scan, &p.ws->err);
             if (lane == 0) {
-                s_excl = excl;
-                if (tile == p.num_tiles - 1) {
+                s_pbase[b] = s_base + excl;
+                if (t == p.num_tiles - 1) {
                     const uint64_t total = s_base + excl + agg;
                     st_relaxed_u64(&p.hdr->outlier_count, total);
                     if (total > p.cap) atomicOr(&p.ws->err, LCQ_STATUS_CAPACITY);
                 }
-            }
-        }
-        __syncthreads();
-        // outliers: the raw input bits, re-read from global memory (the tile
-        // was read moments ago, so these reads hit L2)
-        const uint64_t pbase = s_base + s_excl;
-#pragma unroll
-        for (int v = 0; v < VPT; v++) {
-            if (nib[v]) {
-                const int off = v * (kBlock * 4) + tid * 4;
-                const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-                const uint32_t mw = s_mask[mb][word];
-                const uint32_t pre = s_wpre[mb][word];
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    if ((nib[v] >> q) & 1u) {
-                        const int bit = (lane & 7) * 4 + q;
-                        const uint64_t rank = pbase + pre + __popc(mw & ((1u << bit) - 1u));
-                        if (rank < p.cap) p.out[rank] = F::bits(p.in[tbase + off + q]);
+                if (t == 0 && p.first_chunk) {
+                    lcq_header* h = p.hdr;
+                    h->magic = LCQ_MAGIC;
+                    h->dtype = p.dtype;
+                    h->bound_type = p.bound;
+                    h->n = p.n_total;
+                    h->eb = p.eb;
+                    if (!p.consts_from_hdr) {
+                        h->mode = 0;
+                        h->range = 0.0;
+                        h->eb_abs = p.eb_abs;
+                        h->ebT_bits = (uint64_t)F::bits(p.c.ebT);
+                        h->scale_bits = (uint64_t)F::bits(p.c.scale);
+                        h->inv_bits = (uint64_t)F::bits(p.c.inv);
+                        h->chk_bits = (uint64_t)F::bits(p.c.chk);
                     }
+                    h->reserved = 0;
                 }
             }
-        }
-        if (tid == 0 && tile == 0 && p.first_chunk) {
-            lcq_header* h = p.hdr;
-            h->magic = LCQ_MAGIC;
-            h->dtype = p.dtype;
-            h->bound_type = p.bound;
-            h->n = p.n_total;
-            h->eb = p.eb;
-            if (!p.consts_from_hdr) {
-                h->mode = 0;
-                h->range = 0.0;
-                h->eb_abs = p.eb_abs;
-                h->ebT_bits = (uint64_t)F::bits(p.c.ebT);
-                h->scale_bits = (uint64_t)F::bits(p.c.scale);
-                h->inv_bits = (uint64_t)F::bits(p.c.inv);
-                h->chk_bits = (uint64_t)F::bits(p.c.chk);
-            }
-            h->reserved = 0;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_done[b]);
         }
     }
     __syncthreads();
@@ -535,41 +600,38 @@ struct DParams {
     ScanCfg scan;
 };
 
-template <typename T, int VPT, int STAGES>
-__global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
+template <typename T, int VPT, int STAGES, int SUB>
+__global__ void __launch_bounds__(kSpecThreads) k_dequantize(DParams<T> p) {
     using F = Ty<T>;
-    constexpr int TILE = kBlock * 4 * VPT;
+    constexpr int STILE = kComputeThreads * 4 * VPT;
+    constexpr int TILE = STILE * SUB;
+    constexpr int SWORDS = STILE / 32;
     constexpr int WORDS = TILE / 32;
     constexpr int WPL = WORDS / 32;
-    constexpr int STAGE_WORDS = TILE + WORDS;  // bins then mask words
+    constexpr int STAGE_WORDS = STILE + SWORDS;  // bins, then the sub-tile's mask words
     extern __shared__ __align__(128) unsigned char dsmem[];
     uint32_t* sbuf = reinterpret_cast<uint32_t*>(dsmem);
-    __shared__ __align__(8) uint64_t s_bar[STAGES];
-    __shared__ uint32_t s_stile[STAGES];
-    __shared__ uint32_t s_words[2][WORDS];  // the tile's mask words, kept past the stage's release
+    __shared__ __align__(8) uint64_t s_stage_bar[STAGES];
+    __shared__ __align__(8) uint64_t s_full[2];
+    __shared__ __align__(8) uint64_t s_done[2];
+    __shared__ uint32_t s_stage_ticket[STAGES];
+    __shared__ uint32_t s_mask[2][WORDS];
     __shared__ uint32_t s_wpre[2][WORDS];
-    __shared__ uint32_t s_epoch, s_excl, s_ok, s_abort, s_agg, s_filled;
+    __shared__ uint32_t s_jt[2];
+    __shared__ uint64_t s_pbase[2];
+    __shared__ uint32_t s_epoch, s_filled, s_ok;
+    __shared__ volatile uint32_t s_abort;
     __shared__ uint64_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t full_tiles = (uint32_t)(p.n / TILE);
-
-    auto issue = [&]() {
-        const int s = (int)(s_filled % STAGES);
-        const uint32_t t = atomicAdd(&p.ws->ticket, 1u);
-        s_stile[s] = t;
-        s_filled++;
-        if (t < full_tiles) {
-            uint32_t* st = sbuf + (size_t)s * STAGE_WORDS;
-            mbar_arrive_expect_tx(&s_bar[s], (TILE + WORDS) * 4);
-            bulk_g2s(st, p.bins + (uint64_t)t * TILE, TILE * 4, &s_bar[s]);
-            bulk_g2s(st + TILE, p.mask + (uint64_t)t * WORDS, WORDS * 4, &s_bar[s]);
-        } else if (t < p.num_tiles) {
-            mbar_arrive(&s_bar[s]);
-        }
-    };
+    const uint64_t full_sub = p.n / STILE;
+    const uint64_t nwords = (p.n + 31) / 32;
 
     if (tid == 0) {
-        for (int s = 0; s < STAGES; s++) mbar_init(&s_bar[s], 1);
+        for (int s = 0; s < STAGES; s++) mbar_init(&s_stage_bar[s], 1);
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&s_full[b], 1);
+            mbar_init(&s_done[b], 1);
+        }
         mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
         s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.ws->carry);
@@ -578,74 +640,109 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                         p.hdr->n == p.n_total && p.hdr->status == 0u &&
                         (p.outl != nullptr || p.hdr->outlier_count == 0);
         s_ok = ok;
+        if (!ok) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
         s_abort = 0;
         s_filled = 0;
-        if (!ok) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
-        else issue();
     }
     __syncthreads();
-    if (s_ok) {
+    if (s_ok && warp < kComputeThreads / 32) {
+        // ------------------------------------------------ compute warps --
         const Consts<T> c = consts_from_header<T>(p.hdr);
         const bool rel = p.hdr->bound_type == LCQ_REL;
         const uint64_t avail = p.hdr->outlier_count;
-        const uint64_t nwords = (p.n + 31) / 32;
         bool overrun = false;
-        for (uint32_t k = 0;; k++) {
-            const int s = (int)(k % STAGES);
-            const int mb = (int)(k & 1u);
-            if (tid == 0 && s_filled < k + STAGES) issue();
-            const uint32_t tile = s_stile[s];
-            if (tile >= p.num_tiles) break;
-            const bool from_smem = tile < full_tiles;
-            if (!mbar_wait(&s_bar[s], (k / STAGES) & 1u, kMbarLimit)) {
+        auto issue = [&]() {
+            const uint32_t f = s_filled;
+            const int s = (int)(f % STAGES);
+            const uint32_t sub = f % SUB;
+            const uint32_t t = sub == 0 ? atomicAdd(&p.ws->ticket, 1u) : s_stage_ticket[(f - 1) % STAGES];
+            s_stage_ticket[s] = t;
+            s_filled = f + 1;
+            if (t < p.num_tiles) {
+                const uint64_t g = (uint64_t)t * SUB + sub;
+                if (g < full_sub) {
+                    uint32_t* st = sbuf + (size_t)s * STAGE_WORDS;
+                    mbar_arrive_expect_tx(&s_stage_bar[s], STAGE_WORDS * 4);
+                    bulk_g2s(st, p.bins + g * STILE, STILE * 4, &s_stage_bar[s]);
+                    bulk_g2s(st + STILE, p.mask + g * SWORDS, SWORDS * 4, &s_stage_bar[s]);
+                } else {
+                    mbar_arrive(&s_stage_bar[s]);
+                }
+            }
+        };
+        // Patch the outliers of local scan tile jj; true if the kernel must stop.
+        auto patch_outliers = [&](uint32_t jj) -> bool {
+            const int bb = (int)(jj & 1u);
+            bool ok = mbar_wait_or_abort(&s_done[bb], (jj >> 1) & 1u, kMbarLimit, &s_abort);
+            if (!ok && !s_abort) {
                 atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
                 s_abort = 1;
             }
+            if (named_barrier_or(1, kComputeThreads, !ok)) return true;
+            const uint64_t tb = (uint64_t)s_jt[bb] * TILE;
+            const uint64_t pbase = s_pbase[bb];
+            for (int w = tid; w < WORDS; w += kComputeThreads) {
+                uint32_t mw = s_mask[bb][w];
+                if (!mw) continue;
+                const uint32_t pre = s_wpre[bb][w];
+                uint32_t below = 0;
+                while (mw) {
+                    const int bit = __ffs(mw) - 1;
+                    mw &= mw - 1u;
+                    const uint64_t rank = pbase + pre + below++;
+                    if (rank < avail) p.out[tb + (uint64_t)w * 32 + bit] = F::from_bits(p.outl[rank]);
+                    else overrun = true;
+                }
+            }
+            named_barrier_sync(1, kComputeThreads);
+            return false;
+        };
+
+        if (tid == 0) issue();
+        named_barrier_sync(1, kComputeThreads);
+        uint32_t k = 0;
+        for (;; k++) {
+            const int s = (int)(k % STAGES);
+            const uint32_t sub = k % SUB;
+            const uint32_t j = k / SUB;
+            const int b = (int)(j & 1u);
+            if (tid == 0 && s_filled < k + STAGES) issue();
+            const uint32_t t = s_stage_ticket[s];
+            if (t >= p.num_tiles) break;
+            const uint64_t g = (uint64_t)t * SUB + sub;
+            const bool from_smem = g < full_sub;
+            if (!mbar_wait_or_abort(&s_stage_bar[s], (k / STAGES) & 1u, kMbarLimit, &s_abort)) {
+                if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
+            }
             const uint32_t* sb = sbuf + (size_t)s * STAGE_WORDS;
-            const uint64_t tbase = (uint64_t)tile * TILE;
-            // the tile's mask words -> s_words[mb] (from the stage, or from
-            // global memory for the ragged last tile)
-            for (int w = tid; w < WORDS; w += kBlock) {
-                uint32_t word;
-                if (from_smem) {
-                    word = sb[TILE + w];
-                } else {
-                    const uint64_t gw = (uint64_t)tile * WORDS + w;
-                    word = gw < nwords ? p.mask[gw] : 0u;
-                }
-                s_words[mb][w] = word;
+            const uint64_t sbase = g * STILE;
+            for (int w = tid; w < SWORDS; w += kComputeThreads) {
+                const uint64_t gw = g * SWORDS + w;
+                s_mask[b][sub * SWORDS + w] = from_smem ? sb[STILE + w] : (gw < nwords ? p.mask[gw] : 0u);
             }
-            __syncthreads();
-            if (warp == 0) {
-                const uint32_t agg = scan_mask_words<WPL>(s_words[mb], s_wpre[mb], nullptr, 0, 0, false);
-                if (lane == 0) {
-                    s_agg = agg;
-                    lookback_publish(p.desc, tile, agg, s_epoch, p.scan);
-                }
-            }
-            uint32_t nib[VPT];
 #pragma unroll
             for (int v = 0; v < VPT; v++) {
-                const int off = v * (kBlock * 4) + tid * 4;
-                const uint64_t e0 = tbase + off;
-                const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-                const uint32_t nb = (s_words[mb][word] >> ((lane & 7) * 4)) & 0xFu;
-                nib[v] = nb;
-                int32_t b[4];
+                const int off = v * (kComputeThreads * 4) + tid * 4;
+                const uint64_t e0 = sbase + off;
+                const int word = v * (kComputeThreads / 8) + warp * 4 + (lane >> 3);
+                const uint64_t gw = g * SWORDS + word;
+                const uint32_t mw = from_smem ? sb[STILE + word] : (gw < nwords ? p.mask[gw] : 0u);
+                const uint32_t nb = (mw >> ((lane & 7) * 4)) & 0xFu;
+                int32_t bn[4];
                 if (from_smem) {
                     const int4 a = *reinterpret_cast<const int4*>(sb + off);
-                    b[0] = a.x; b[1] = a.y; b[2] = a.z; b[3] = a.w;
+                    bn[0] = a.x; bn[1] = a.y; bn[2] = a.z; bn[3] = a.w;
                 } else if (e0 + 4 <= p.n) {
                     const int4 a = __ldcs(reinterpret_cast<const int4*>(p.bins + e0));
-                    b[0] = a.x; b[1] = a.y; b[2] = a.z; b[3] = a.w;
+                    bn[0] = a.x; bn[1] = a.y; bn[2] = a.z; bn[3] = a.w;
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; q++) b[q] = (e0 + q < p.n) ? p.bins[e0 + q] : 0;
+                    for (int q = 0; q < 4; q++) bn[q] = (e0 + q < p.n) ? p.bins[e0 + q] : 0;
                 }
                 T x[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++)
-                    x[q] = ((nb >> q) & 1u) ? T(0) : (rel ? rel_recon<T>(b[q], c) : abs_recon<T>(b[q], c));
+                    x[q] = ((nb >> q) & 1u) ? T(0) : (rel ? rel_recon<T>(bn[q], c) : abs_recon<T>(bn[q], c));
                 if (e0 + 4 <= p.n) {
                     Vec4<T>::store(p.out + e0, x);
                 } else {
@@ -655,37 +752,44 @@ __global__ void __launch_bounds__(kBlock) k_dequantize(DParams<T> p) {
                 }
             }
             fence_proxy_async_smem();
-            __syncthreads();  // stage s consumed
-            if (s_abort) break;
+            if (named_barrier_or(1, kComputeThreads, s_abort != 0)) break;  // stage s consumed
             if (tid == 0 && s_filled < k + 1 + STAGES) issue();
-            if (warp == 0) {
-                const uint32_t excl = lookback_walk(p.desc, tile, s_agg, s_epoch, p.scan, &p.ws->err);
-                if (lane == 0) {
-                    s_excl = excl;
-                    if (tile == p.num_tiles - 1) st_relaxed_u64(&p.ws->carry, s_base + excl + s_agg);
+            if (sub == SUB - 1) {
+                if (tid == 0) {
+                    s_jt[b] = t;
+                    mbar_arrive(&s_full[b]);
                 }
+                if (j >= 1 && patch_outliers(j - 1)) break;
             }
-            __syncthreads();
-            const uint64_t pbase = s_base + s_excl;
-#pragma unroll
-            for (int v = 0; v < VPT; v++) {
-                if (nib[v]) {
-                    const int off = v * (kBlock * 4) + tid * 4;
-                    const int word = v * (kBlock / 8) + warp * 4 + (lane >> 3);
-                    const uint32_t mw = s_words[mb][word];
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        if ((nib[v] >> q) & 1u) {
-                            const int bit = (lane & 7) * 4 + q;
-                            const uint64_t rank = pbase + s_wpre[mb][word] + __popc(mw & ((1u << bit) - 1u));
-                            if (rank < avail) p.out[tbase + off + q] = F::from_bits(p.outl[rank]);
-                            else overrun = true;
-                        }
-                    }
-                }
+        }
+        if (!named_barrier_or(1, kComputeThreads, s_abort != 0)) {
+            const uint32_t J = k / SUB;
+            if (!(J >= 1 && patch_outliers(J - 1)) && tid == 0) {
+                s_jt[J & 1u] = kNoTile;
+                mbar_arrive(&s_full[J & 1u]);
             }
         }
         if (overrun) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
+    } else if (s_ok) {
+        // --------------------------------------------------- scan warp --
+        for (uint32_t j = 0;; j++) {
+            const int b = (int)(j & 1u);
+            if (!mbar_wait_or_abort(&s_full[b], (j >> 1) & 1u, kMbarLimit, &s_abort)) {
+                if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
+                break;
+            }
+            const uint32_t t = s_jt[b];
+            if (t == kNoTile) break;
+            const uint32_t agg = scan_mask_words<WPL>(s_mask[b], s_wpre[b], nullptr, 0, 0, false);
+            if (lane == 0) lookback_publish(p.desc, t, agg, s_epoch, p.scan);
+            const uint32_t excl = lookback_walk(p.desc, t, agg, s_epoch, p.scan, &p.ws->err);
+            if (lane == 0) {
+                s_pbase[b] = s_base + excl;
+                if (t == p.num_tiles - 1) st_relaxed_u64(&p.ws->carry, s_base + excl + agg);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_done[b]);
+        }
     }
     __syncthreads();
     if (tid == 0) finish_launch(p.ws, s_epoch, p.status, p.first_chunk != 0);
@@ -703,6 +807,17 @@ static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 static uint64_t tiles_for(uint64_t n) { return (n + kTileMin - 1) / kTileMin; }
 static uint64_t tiles_of(uint64_t n, int tile) { return (n + tile - 1) / tile; }
 
+static size_t desc_bytes(uint64_t n) {
+    const uint64_t per_chunk = n < kChunk ? n : kChunk;
+    return (size_t)(tiles_for(per_chunk) * sizeof(uint64_t));
+}
+
+static size_t ws_size(uint64_t n) {
+    size_t d = desc_bytes(n);
+    d = (d + 255) & ~(size_t)255;
+    return kWsHeadBytes + d + kMinmaxPartialBytes;
+}
+
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // kernel instantiation and device), never more than there are tiles.
 struct GridCache {
@@ -718,57 +833,46 @@ static int device_sms(int dev) {
 }
 
 template <typename K>
-static int persistent_blocks(K kernel, size_t dyn_smem, GridCache& cache) {
+static int persistent_blocks(K kernel, size_t dyn_smem, int threads, GridCache& cache) {
     int dev = 0;
     cudaGetDevice(&dev);
     const int slot = (dev >= 0 && dev < 16) ? dev : 0;
     if (!cache.set[slot]) {
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
         int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kBlock, dyn_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, dyn_smem);
         cache.blocks_per_sm[slot] = b > 0 ? b : 1;
         cache.set[slot] = true;
     }
     return cache.blocks_per_sm[slot] * device_sms(dev);
 }
 
-template <typename T, int MODE, int VPT, int STAGES>
+template <typename T, int MODE, int VPT, int STAGES, int SUB>
 static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
     static GridCache cache{};
-    constexpr int TILE = kBlock * 4 * VPT;
-    const size_t smem = (size_t)STAGES * TILE * sizeof(T);
-    auto kern = k_quantize<T, MODE, VPT, STAGES>;
+    constexpr int STILE = kComputeThreads * 4 * VPT;
+    const size_t smem = (size_t)STAGES * STILE * sizeof(T);
+    auto kern = k_quantize<T, MODE, VPT, STAGES, SUB>;
     QParams<T> q = p;
-    q.num_tiles = (uint32_t)tiles_of(p.n, TILE);
-    uint64_t grid = (uint64_t)persistent_blocks(kern, smem, cache);
+    q.num_tiles = (uint32_t)tiles_of(p.n, STILE * SUB);
+    uint64_t grid = (uint64_t)persistent_blocks(kern, smem, kSpecThreads, cache);
     if (grid > q.num_tiles) grid = q.num_tiles;
-    kern<<<(unsigned)grid, kBlock, smem, st>>>(q);
+    kern<<<(unsigned)grid, kSpecThreads, smem, st>>>(q);
     return cudaPeekAtLastError();
 }
 
-template <typename T, int VPT, int STAGES>
+template <typename T, int VPT, int STAGES, int SUB>
 static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
     static GridCache cache{};
-    constexpr int TILE = kBlock * 4 * VPT;
-    const size_t smem = (size_t)STAGES * (TILE + TILE / 32) * 4;
-    auto kern = k_dequantize<T, VPT, STAGES>;
+    constexpr int STILE = kComputeThreads * 4 * VPT;
+    const size_t smem = (size_t)STAGES * (STILE + STILE / 32) * 4;
+    auto kern = k_dequantize<T, VPT, STAGES, SUB>;
     DParams<T> q = p;
-    q.num_tiles = (uint32_t)tiles_of(p.n, TILE);
-    uint64_t grid = (uint64_t)persistent_blocks(kern, smem, cache);
+    q.num_tiles = (uint32_t)tiles_of(p.n, STILE * SUB);
+    uint64_t grid = (uint64_t)persistent_blocks(kern, smem, kSpecThreads, cache);
     if (grid > q.num_tiles) grid = q.num_tiles;
-    kern<<<(unsigned)grid, kBlock, smem, st>>>(q);
+    kern<<<(unsigned)grid, kSpecThreads, smem, st>>>(q);
     return cudaPeekAtLastError();
-}
-
-static size_t desc_bytes(uint64_t n) {
-    const uint64_t per_chunk = n < kChunk ? n : kChunk;
-    return (size_t)(tiles_for(per_chunk) * sizeof(uint64_t));
-}
-
-static size_t ws_size(uint64_t n) {
-    size_t d = desc_bytes(n);
-    d = (d + 255) & ~(size_t)255;
-    return kWsHeadBytes + d + kMinmaxPartialBytes;
 }
 
 // RD_f32(d): the largest float not above d.
@@ -908,12 +1012,12 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.eb_abs = eb_abs;
         p.n_total = n;
         cudaError_t e;
-        if (sizeof(T) == 4) {
-            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF32, kStagesF32>(p, st)
-                              : launch_quantize<T, LCQ_ABS, kVptF32, kStagesF32>(p, st);
+        if constexpr (sizeof(T) == 4) {
+            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF32, kStagesF32, kSubF32>(p, st)
+                              : launch_quantize<T, LCQ_ABS, kVptF32, kStagesF32, kSubF32>(p, st);
         } else {
-            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF64, kStagesF64>(p, st)
-                              : launch_quantize<T, LCQ_ABS, kVptF64, kStagesF64>(p, st);
+            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF64, kStagesF64, kSubF64>(p, st)
+                              : launch_quantize<T, LCQ_ABS, kVptF64, kStagesF64, kSubF64>(p, st);
         }
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
@@ -947,8 +1051,9 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
         p.scan = g_scan;
-        const cudaError_t e = sizeof(T) == 4 ? launch_dequantize<T, kVptF32, kStagesF32>(p, st)
-                                             : launch_dequantize<T, kVptF64, kStagesF64>(p, st);
+        cudaError_t e;
+        if constexpr (sizeof(T) == 4) e = launch_dequantize<T, kVptF32, kStagesF32, kSubF32>(p, st);
+        else e = launch_dequantize<T, kVptF64, kStagesF64, kSubF64>(p, st);
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
