@@ -129,7 +129,7 @@ def test_workspace_reuse_across_calls():
 def test_scan_timeout_is_reported_without_hang():
     """A tile that never publishes its scan descriptor: the successor's wait
     gives up after the spin limit and the header carries LCQ_STATUS_TIMEOUT."""
-    x = torch.randn(5 * 4096, device=DEV)
+    x = torch.randn(1 << 19, device=DEV)  # several scan tiles of every tile shape
     ws = P.new_workspace(x.numel(), x.device)
     q = P.alloc_outputs(x.numel(), x.dtype, x.device)
     P.debug_set_scan(spin_limit=200, drop_tile=1)
