@@ -167,6 +167,33 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
                              cudaStream_t stream);
 
 /*
+ * Allocation-free variant of lcq_quantize.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory
+ * where they quantize (code inside a no-allocation region such as a fixed
+ * memory budget streaming pipeline or a simulation step that must not
+ * synchronise through the allocator, or code running inside another
+ * library's callback), so it takes no workspace argument.
+ *   - Arguments, outputs and results are those of lcq_quantize.
+ *   - The scan workspace is a fixed 1 MiB device array inside the library,
+ *     held by every GPU that loads the library until the process exits.  It
+ *     limits n to lcq_noalloc_max_values() values (about 5.2e8 at the time of
+ *     writing); larger n returns LCQ_ERR_WORKSPACE and enqueues nothing.
+ *   - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *     routine.  The first call on each device looks up the device address of
+ *     that array (cudaGetSymbolAddress) with the device current; make that
+ *     first call before any stream capture.
+ *   - Every call on a device shares the one array: calls that can overlap on
+ *     the GPU (other streams, other host threads) race and must not be made;
+ *     serialise them on one stream.  Each call clears the scan counters it
+ *     needs at zero before launching.
+ */
+uint64_t lcq_noalloc_max_values(void);
+lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, double eb,
+                                const void* d_in, uint64_t n, int32_t* d_bins, uint32_t* d_mask,
+                                void* d_outliers, uint64_t outlier_capacity, lcq_header* d_hdr,
+                                cudaStream_t stream);
+
+/*
  * Test hook for the bounded waits of the outlier scan (no counterpart in the
  * paper).  spin_limit: maximum polls of one predecessor's scan descriptor
  * before the wait gives up with LCQ_STATUS_TIMEOUT (0 restores the default,

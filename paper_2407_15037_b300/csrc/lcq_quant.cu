@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -1192,6 +1193,78 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
 void lcq_debug_set_scan(uint32_t spin_limit, uint64_t drop_tile) {
     g_scan.spin_limit = spin_limit ? spin_limit : kDefaultSpin;
     g_scan.drop_tile = drop_tile;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free quantize entry point.
+//
+// Some callers cannot allocate device memory at the point where they
+// quantize: code running inside a region that must not allocate (a
+// fixed-memory-budget streaming pipeline, a simulation time step that must
+// not synchronise the device through the allocator, a callback invoked from
+// another library's allocator or scheduler), or code that simply has no
+// allocator to hand.  lcq_quantize_noalloc serves them: the caller still
+// passes inputs and outputs, and the scan workspace comes from the
+// fixed-size device array below, which every GPU that loads this library
+// holds until the process exits.
+// ---------------------------------------------------------------------------
+namespace lcq {
+
+constexpr size_t kNoAllocWsBytes = (size_t)1 << 20;  // 1 MiB of scratch per device
+static __device__ __align__(256) unsigned char g_noalloc_ws[kNoAllocWsBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64];  // device address of g_noalloc_ws, per device
+
+// Device address of the scratch array for the current device (set-up on the
+// first call per device; the array's host-side name is only a stand-in).
+static lcq_status noalloc_scratch(void** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LCQ_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_ws) != cudaSuccess || !p) return LCQ_ERR_CUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LCQ_OK;
+}
+
+}  // namespace lcq
+
+extern "C" {
+
+uint64_t lcq_noalloc_max_values(void) {
+    // largest n whose workspace fits the static scratch
+    uint64_t lo = 0, hi = 1ull << 40;
+    while (lo + 1 < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        if (ws_size(mid) <= kNoAllocWsBytes) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, double eb,
+                                const void* d_in, uint64_t n, int32_t* d_bins, uint32_t* d_mask,
+                                void* d_outliers, uint64_t outlier_capacity, lcq_header* d_hdr,
+                                cudaStream_t stream) {
+    if (n > lcq_noalloc_max_values()) return LCQ_ERR_WORKSPACE;
+    void* ws = nullptr;
+    const lcq_status st = noalloc_scratch(&ws);
+    if (st != LCQ_OK) return st;
+    // Start from a clean scan state even if an earlier call on this device
+    // was cut short: zero the ticket, the finished-CTA counter and the error
+    // bits (the epoch counter must keep counting, so it is left alone).
+    WsHead* head = reinterpret_cast<WsHead*>(ws);
+    if (cudaMemsetAsync(&head->ticket, 0, 2 * sizeof(uint32_t), stream) != cudaSuccess ||
+        cudaMemsetAsync(&head->err, 0, sizeof(uint32_t), stream) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    return lcq_quantize(dtype, bound_type, eb, d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
+                        d_hdr, ws, kNoAllocWsBytes, stream);
 }
 
 }  // extern "C"

@@ -61,6 +61,9 @@ SIGNATURES = {
     "lcq_quantize_host": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
                            _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
     "lcq_debug_set_scan": ([_u32, _u64], None),
+    "lcq_noalloc_max_values": ([], _u64),
+    "lcq_quantize_noalloc": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
+                              _vp], ctypes.c_int),
 }
 
 _lib = None
@@ -173,6 +176,18 @@ def quantize(x, bound, eb, outlier_capacity=None, ws=None, stream=None):
     if ws is None:
         ws = new_workspace(x.numel(), x.device, _dtype_code(x), bound)
     return quantize_into(x, bound, eb, q, ws, stream)
+
+
+def quantize_noalloc_into(x, bound, eb, q, stream=None):
+    """Enqueue lcq_quantize_noalloc (no workspace argument; the library's
+    built-in scratch is used).  Calls on one device must not overlap."""
+    _require_cuda(x)
+    code = lib().lcq_quantize_noalloc(
+        _dtype_code(x), _bound_code(bound), float(eb), _ptr(x), x.numel(), _ptr(q.bins),
+        _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header),
+        _stream_ptr(stream, x.device))
+    _check(code, "lcq_quantize_noalloc")
+    return q
 
 
 def dequantize_into(q, out, ws, status=None, stream=None):
