@@ -266,6 +266,37 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize(dev)
     t_deq = a.elapsed_time(b) / reps / 1e3
 
+    # ---- other configurations of the same path (timed per call) ----
+    extra = {}
+
+    def time_calls(xx, bound, eb, reps=5):
+        qq = P.alloc_outputs(xx.numel(), xx.dtype, dev)
+        ww = P.new_workspace(xx.numel(), dev)
+        P.quantize_into(xx, bound, eb, qq, ww, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            P.quantize_into(xx, bound, eb, qq, ww, stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        t = a.elapsed_time(b) / reps / 1e3
+        h = qq.read_header()
+        es = xx.element_size()
+        alg = xx.numel() * (es + 4) + (xx.numel() + 31) // 32 * 4 + es * h.outlier_count + \
+            (xx.numel() * es if bound == "noa" else 0)
+        return {"ms": t * 1e3, "in_GBps": xx.numel() * es / t / 1e9, "hbm_GBps": alg / t / 1e9,
+                "outliers": int(h.outlier_count)}
+
+    if args.extras:
+        x64 = synth.smooth_field((256, 256, 256), dtype=torch.float64, seed=0, device=dev)
+        for bound in BOUNDS:
+            extra["f64_256_%s_1e-3" % bound] = time_calls(x64, bound, 1e-3)
+        del x64
+        xs = synth.rel_stress(1 << 28, seed=0, device=dev)
+        for eb in (1e-3, 1e-6):
+            extra["rel_stress_2^28_%g" % eb] = time_calls(xs, "rel", eb)
+        del xs
+
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if args.e2e_steps > 0:
@@ -327,7 +358,9 @@ def run_ours(args, world, rank, local):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "per_call": per,
-            "dequantize_f32_abs_1e-3": {"ms": t_deq * 1e3, "out_GBps": n * 4 / t_deq / 1e9},
+            "dequantize_f32_abs_1e-3": {"ms": t_deq * 1e3, "out_GBps": n * 4 / t_deq / 1e9,
+                                        "hbm_GBps": n * 8.125 / t_deq / 1e9},
+            "other_configs": extra,
         }
         print(json.dumps(line), flush=True)
 
@@ -366,6 +399,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -86,6 +86,53 @@ struct Ty<double> {
     static __device__ __forceinline__ double bias_f() { return 1023.0; }
 };
 
+// ---------------------------------------------------------------------------
+// Exact replacements for conversions (the float<->int conversions run on a
+// slow pipe).  Each returns exactly what the conversion it replaces returns:
+//   round_small(q): for |q| < 2^22 (float) / 2^51 (double), t = RN(q + 1.5 2^p)
+//     lies in one binade with unit spacing, so t - 1.5 2^p = rint(q) (ties to
+//     even, as 1.5 2^p is even) exactly, and the bit difference of t and
+//     1.5 2^p is that integer;
+//   floor_bb(bb): for 0 <= bb < 2^p, RZ(bb + 2^p) = 2^p + floor(bb), exactly;
+//   int_to_float_small(i): for |i| < 2^22, the float with bits
+//     bits(1.5 2^23) + i is 1.5 2^23 + i, so subtracting 1.5 2^23 gives i.
+// ---------------------------------------------------------------------------
+struct Rounded {
+    int32_t i;  // the integer
+    float f32;  // the same integer as a float (float path)
+};
+
+__device__ __forceinline__ bool round_small_f32(float q, int32_t& i, float& f) {
+    if (!(fabsf(q) < 0x1p22f)) return false;
+    const float t = __fadd_rn(q, 0x1.8p23f);
+    i = __float_as_int(t) - 0x4B400000;
+    f = __fsub_rn(t, 0x1.8p23f);
+    return true;
+}
+
+__device__ __forceinline__ void round_any_f32(float q, int32_t& i, float& f) {
+    if (!round_small_f32(q, i, f)) {
+        i = __float2int_rn(q);
+        f = __int2float_rn(i);
+    }
+}
+
+__device__ __forceinline__ void round_any_f64(double q, int32_t& i, double& f) {
+    // |q| < 2^30 < 2^51 always holds here
+    const double t = __dadd_rn(q, 0x1.8p52);
+    i = (int32_t)(__double_as_longlong(t) - 0x4338000000000000ll);
+    f = __dsub_rn(t, 0x1.8p52);
+}
+
+__device__ __forceinline__ float int_to_float_f32(int32_t i) {
+    if (i > -(1 << 22) && i < (1 << 22)) return __fsub_rn(__int_as_float(0x4B400000 + i), 0x1.8p23f);
+    return __int2float_rn(i);
+}
+
+__device__ __forceinline__ double int_to_float_f64(int32_t i) {
+    return __dsub_rn(__longlong_as_double(0x4338000000000000ll + i), 0x1.8p52);
+}
+
 // Constants of one quantization, in the data type.
 template <typename T>
 struct Consts {
@@ -112,6 +159,39 @@ __device__ __forceinline__ Consts<T> consts_from_header(const lcq_header* h) {
 // Per-value recipes
 // ---------------------------------------------------------------------------
 
+// Per-type rounding / conversion helpers used by the recipes below.
+template <typename T>
+struct Cv;
+template <>
+struct Cv<float> {
+    static __device__ __forceinline__ void round(float q, int32_t& i, float& f) { round_any_f32(q, i, f); }
+    static __device__ __forceinline__ float from_int(int32_t i) { return int_to_float_f32(i); }
+    // floor(bb) for 1 <= bb < 255, as integer and as float: RZ(bb + 2^23)
+    static __device__ __forceinline__ void floor_bb(float bb, int32_t& k, float& kf) {
+        const float t = __fadd_rz(bb, 0x1p23f);
+        k = __float_as_int(t) - 0x4B000000;
+        kf = __fsub_rn(t, 0x1p23f);
+    }
+    // (float)(E - 128) for a biased exponent 1 <= E <= 254
+    static __device__ __forceinline__ float unbias(uint32_t E) {
+        return __fsub_rn(__uint_as_float(0x4B000000u | E), 0x1.00010p23f);  // 2^23 + 128
+    }
+};
+template <>
+struct Cv<double> {
+    static __device__ __forceinline__ void round(double q, int32_t& i, double& f) { round_any_f64(q, i, f); }
+    static __device__ __forceinline__ double from_int(int32_t i) { return int_to_float_f64(i); }
+    static __device__ __forceinline__ void floor_bb(double bb, int32_t& k, double& kf) {
+        const double t = __dadd_rz(bb, 0x1p52);
+        k = (int32_t)(__double_as_longlong(t) - 0x4330000000000000ll);
+        kf = __dsub_rn(t, 0x1p52);
+    }
+    // (double)(E - 1024) for a biased exponent 1 <= E <= 2046
+    static __device__ __forceinline__ double unbias(uint64_t E) {
+        return __dsub_rn(__longlong_as_double((long long)(0x4330000000000000ull | E)), 0x1.0000000000400p52);
+    }
+};
+
 // ABS / NOA: bin = rint(x * inv) (Sec. 2.2); reconstruct and check (Sec. 3.1);
 // two-sided range test (Sec. 3.3).  Returns false for an outlier.
 template <typename T>
@@ -119,9 +199,11 @@ __device__ __forceinline__ bool abs_quant(T x, const Consts<T>& c, int32_t& bin)
     using F = Ty<T>;
     const T q = F::mul(x, c.inv);
     if (!(F::fabs_(q) < T(kMaxBinAbs))) return false;
-    const int32_t b = F::rint_i(q);
+    int32_t b;
+    T bf;
+    Cv<T>::round(q, b, bf);  // b = rint(q), bf = (T)b
     if ((b >= kMaxBinAbs) || (b <= -kMaxBinAbs)) return false;
-    const T recon = F::mul(F::from_i(b), c.scale);
+    const T recon = F::mul(bf, c.scale);
     if (!(F::fabs_(F::sub(x, recon)) <= c.ebT)) return false;
     bin = b;
     return true;
@@ -129,27 +211,29 @@ __device__ __forceinline__ bool abs_quant(T x, const Consts<T>& c, int32_t& bin)
 
 template <typename T>
 __device__ __forceinline__ T abs_recon(int32_t bin, const Consts<T>& c) {
-    return Ty<T>::mul(Ty<T>::from_i(bin), c.scale);
+    return Ty<T>::mul(Cv<T>::from_int(bin), c.scale);
 }
 
 // log2approx (Sec. 3.2): one addition of the float 1.mantissa and E - (bias+1).
 template <typename T>
 __device__ __forceinline__ T log2approx(typename Ty<T>::U u) {
     using F = Ty<T>;
-    using U = typename F::U;
-    const int32_t E = (int32_t)((u >> F::kP) & F::kExpAll);
+    const typename F::U E = (u >> F::kP) & F::kExpAll;
     const T one_frac = F::from_bits(F::kOneBits | (u & F::kMant));
-    return F::add(one_frac, F::from_i(E - (F::kBias + 1)));
+    return F::add(one_frac, Cv<T>::unbias(E));
 }
 
 // pow2approx (Sec. 3.2) of bb = RN(Lr + bias), bb in [1, 2 bias + 1):
-// 2^(k - bias) (1 + bb - k), k = floor(bb).
+// 2^(k - bias) (1 + bb - k), k = floor(bb); the fraction is the mantissa of
+// the float bb - (k - 1), which lies in [1, 2) and is exact.
 template <typename T>
 __device__ __forceinline__ typename Ty<T>::U pow2approx_bits(T bb) {
     using F = Ty<T>;
     using U = typename F::U;
-    const int64_t k = F::trunc_i(bb);
-    const T fr = F::sub(bb, F::from_i64(k - 1));
+    int32_t k;
+    T kf;
+    Cv<T>::floor_bb(bb, k, kf);
+    const T fr = F::sub(bb, F::sub(kf, T(1)));
     return ((U)k << F::kP) | (F::bits(fr) & F::kMant);
 }
 
@@ -166,19 +250,28 @@ __device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin)
     const T L = log2approx<T>(u);
     const T q = F::mul(L, c.inv);
     if (!(F::fabs_(q) < T(kMaxBinRel))) return false;
-    const int32_t b = F::rint_i(q);
+    int32_t b;
+    T bf;
+    Cv<T>::round(q, b, bf);
     if ((b >= kMaxBinRel) || (b <= -kMaxBinRel)) return false;
-    const T Lr = F::mul(F::from_i(b), c.scale);
+    const T Lr = F::mul(bf, c.scale);
     const T bb = F::add(Lr, F::bias_f());
     if (!(bb >= T(1) && bb < F::top_bb())) return false;
     const T m = F::from_bits(pow2approx_bits<T>(bb));
     if (!(a <= F::mul(T(2), m) && m <= F::mul(T(2), a))) return false;
     const T d = F::fabs_(F::sub(a, m));  // exact (Sterbenz)
     const T lo = (a < m) ? a : m;
-    const T sc = (lo < F::tiny()) ? F::rescale() : T(1);
-    const T t = F::mul(F::mul(lo, sc), c.chk);
-    if (!(t >= F::nmin())) return false;
-    if (!(F::mul(d, sc) <= t)) return false;
+    T t;
+    bool ok;
+    if (lo < F::tiny()) {  // exact power-of-two rescale keeps t out of the subnormal range
+        const T sc = F::rescale();
+        t = F::mul(F::mul(lo, sc), c.chk);
+        ok = (t >= F::nmin()) && (F::mul(d, sc) <= t);
+    } else {  // scaling by 1 is exact, so it is left out
+        t = F::mul(lo, c.chk);
+        ok = (t >= F::nmin()) && (d <= t);
+    }
+    if (!ok) return false;
     bin = (int32_t)(((uint32_t)b << 1) | (uint32_t)sign_bit);
     return true;
 }
@@ -189,7 +282,7 @@ __device__ __forceinline__ T rel_recon(int32_t bin, const Consts<T>& c) {
     using U = typename F::U;
     const U s = (U)(bin & 1);
     const int32_t b = bin >> 1;  // arithmetic shift: (bin - s) / 2
-    const T Lr = F::mul(F::from_i(b), c.scale);
+    const T Lr = F::mul(Cv<T>::from_int(b), c.scale);
     const T bb = F::add(Lr, F::bias_f());
     return F::from_bits(pow2approx_bits<T>(bb) | (s << (sizeof(U) * 8 - 1)));
 }

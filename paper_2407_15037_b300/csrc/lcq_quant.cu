@@ -193,7 +193,7 @@ constexpr int kSpecThreads = kComputeThreads + 32;
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
 template <typename T, int MODE, int VPT, int STAGES, int SUB>
-__global__ void __launch_bounds__(kSpecThreads) k_quantize(QParams<T> p) {
+__global__ void __launch_bounds__(kSpecThreads, 2) k_quantize(QParams<T> p) {
     using F = Ty<T>;
     constexpr int STILE = kComputeThreads * 4 * VPT;  // values per stage (sub-tile)
     constexpr int TILE = STILE * SUB;                  // values per scan tile
@@ -298,35 +298,62 @@ __global__ void __launch_bounds__(kSpecThreads) k_quantize(QParams<T> p) {
             }
             const T* st = sbuf + (size_t)s * STILE;
             const uint64_t sbase = g * STILE;
-#pragma unroll
-            for (int v = 0; v < VPT; v++) {
-                const int off = v * (kComputeThreads * 4) + tid * 4;
-                const uint64_t e0 = sbase + off;
-                T x[4];
-                load4<T, VPT>(st, p.in, from_smem, off, e0, p.n, x);
-                int32_t bn[4];
-                uint32_t nb = 0;
-#pragma unroll
-                for (int q = 0; q < 4; q++) {
-                    int32_t bin = 0;
-                    bool ok = false;
-                    if (!c.all_outliers)
-                        ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
-                    if (!ok && e0 + q < p.n) nb |= 1u << q;
-                    bn[q] = ok ? bin : 0;
-                }
-                if (e0 + 4 <= p.n) {
-                    __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(bn[0], bn[1], bn[2], bn[3]));
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; q++)
-                        if (e0 + q < p.n) p.bins[e0 + q] = bn[q];
-                }
+            uint32_t* smw = &s_mask[b][sub * SWORDS + warp * 4 + (lane >> 3)];
+            // 4-value outlier nibbles of 8 lanes -> one mask word
+            auto put_word = [&](int v, uint32_t nb) {
                 uint32_t w = nb << ((lane & 7) * 4);
                 w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
                 w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
                 w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
-                if ((lane & 7) == 0) s_mask[b][sub * SWORDS + v * (kComputeThreads / 8) + warp * 4 + (lane >> 3)] = w;
+                if ((lane & 7) == 0) smw[v * (kComputeThreads / 8)] = w;
+            };
+            if (from_smem && !c.all_outliers) {
+                // fast path: a whole sub-tile in shared memory, no bounds checks
+                int32_t* gb = p.bins + sbase;
+#pragma unroll
+                for (int v = 0; v < VPT; v++) {
+                    const int off = v * (kComputeThreads * 4) + tid * 4;
+                    T x[4];
+                    Vec4<T>::load_shared(st + off, x);
+                    int32_t bn[4];
+                    uint32_t nb = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        int32_t bin = 0;
+                        const bool ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
+                        nb |= ok ? 0u : (1u << q);
+                        bn[q] = ok ? bin : 0;
+                    }
+                    __stcs(reinterpret_cast<int4*>(gb + off), make_int4(bn[0], bn[1], bn[2], bn[3]));
+                    put_word(v, nb);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < VPT; v++) {
+                    const int off = v * (kComputeThreads * 4) + tid * 4;
+                    const uint64_t e0 = sbase + off;
+                    T x[4];
+                    load4<T, VPT>(st, p.in, from_smem, off, e0, p.n, x);
+                    int32_t bn[4];
+                    uint32_t nb = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; q++) {
+                        int32_t bin = 0;
+                        bool ok = false;
+                        if (!c.all_outliers)
+                            ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
+                        if (!ok && e0 + q < p.n) nb |= 1u << q;
+                        bn[q] = ok ? bin : 0;
+                    }
+                    if (e0 + 4 <= p.n) {
+                        __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(bn[0], bn[1], bn[2], bn[3]));
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; q++)
+                            if (e0 + q < p.n) p.bins[e0 + q] = bn[q];
+                    }
+                    put_word(v, nb);
+                }
             }
             fence_proxy_async_smem();
             bool stop = named_barrier_or(1, kComputeThreads, s_abort != 0);  // stage s consumed
@@ -602,7 +629,7 @@ struct DParams {
 };
 
 template <typename T, int VPT, int STAGES, int SUB>
-__global__ void __launch_bounds__(kSpecThreads) k_dequantize(DParams<T> p) {
+__global__ void __launch_bounds__(kSpecThreads, 2) k_dequantize(DParams<T> p) {
     using F = Ty<T>;
     constexpr int STILE = kComputeThreads * 4 * VPT;
     constexpr int TILE = STILE * SUB;
@@ -721,6 +748,23 @@ __global__ void __launch_bounds__(kSpecThreads) k_dequantize(DParams<T> p) {
                 const uint64_t gw = g * SWORDS + w;
                 s_mask[b][sub * SWORDS + w] = from_smem ? sb[STILE + w] : (gw < nwords ? p.mask[gw] : 0u);
             }
+            if (from_smem) {
+                // fast path: a whole sub-tile in shared memory, no bounds checks
+                T* go = p.out + sbase;
+#pragma unroll
+                for (int v = 0; v < VPT; v++) {
+                    const int off = v * (kComputeThreads * 4) + tid * 4;
+                    const int word = v * (kComputeThreads / 8) + warp * 4 + (lane >> 3);
+                    const uint32_t nb = (sb[STILE + word] >> ((lane & 7) * 4)) & 0xFu;
+                    const int4 a = *reinterpret_cast<const int4*>(sb + off);
+                    const int32_t bn[4] = {a.x, a.y, a.z, a.w};
+                    T x[4];
+#pragma unroll
+                    for (int q = 0; q < 4; q++)
+                        x[q] = ((nb >> q) & 1u) ? T(0) : (rel ? rel_recon<T>(bn[q], c) : abs_recon<T>(bn[q], c));
+                    Vec4<T>::store(go + off, x);
+                }
+            } else
 #pragma unroll
             for (int v = 0; v < VPT; v++) {
                 const int off = v * (kComputeThreads * 4) + tid * 4;
