@@ -202,6 +202,19 @@ def run_ours(args, world, rank, local):
             for eb in EBS:
                 P.quantize_into(x, bound, eb, q, ws, stream)
 
+    # autotune the tile shape per bound type on this workload (untimed)
+    tuning = {}
+    for bound in BOUNDS:
+        ms = P.lcq.autotune_quantize(x, bound, 1e-3, q, ws, reps=3, stream=stream)
+        tuning["quantize_" + bound] = {"chosen": P.lcq.get_variant(0, P.F32, bound),
+                                       "ms_per_variant": [round(m, 4) for m in ms]}
+    P.quantize_into(x, "abs", 1e-3, q, ws, stream)
+    out_t = torch.empty_like(x)
+    ms = P.lcq.autotune_dequantize(q, out_t, ws, reps=3, stream=stream)
+    tuning["dequantize"] = {"chosen": P.lcq.get_variant(1, P.F32, "abs"),
+                            "ms_per_variant": [round(m, 4) for m in ms]}
+    del out_t
+
     launches_per_step = len(BOUNDS) * len(EBS) + len(EBS)  # + NOA range kernels
     for _ in range(args.warmup):
         step()
@@ -289,8 +302,13 @@ def run_ours(args, world, rank, local):
 
     if args.extras:
         x64 = synth.smooth_field((256, 256, 256), dtype=torch.float64, seed=0, device=dev)
+        q64 = P.alloc_outputs(x64.numel(), x64.dtype, dev)
+        w64 = P.new_workspace(x64.numel(), dev)
         for bound in BOUNDS:
+            P.lcq.autotune_quantize(x64, bound, 1e-3, q64, w64, reps=3, stream=stream)
             extra["f64_256_%s_1e-3" % bound] = time_calls(x64, bound, 1e-3)
+            extra["f64_256_%s_1e-3" % bound]["variant"] = P.lcq.get_variant(0, P.F64, bound)
+        del q64, w64
         del x64
         xs = synth.rel_stress(1 << 28, seed=0, device=dev)
         for eb in (1e-3, 1e-6):
@@ -361,6 +379,7 @@ def run_ours(args, world, rank, local):
             "dequantize_f32_abs_1e-3": {"ms": t_deq * 1e3, "out_GBps": n * 4 / t_deq / 1e9,
                                         "hbm_GBps": n * 8.125 / t_deq / 1e9},
             "other_configs": extra,
+            "autotune": tuning,
         }
         print(json.dumps(line), flush=True)
 

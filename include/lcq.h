@@ -167,6 +167,33 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
                              cudaStream_t stream);
 
 /*
+ * Tile-shape tuning (no counterpart in the paper; it only affects speed, never
+ * results).  The streaming kernels come in lcq_tune_variant_count() tile
+ * shapes ("variants"): lcq_tune_describe gives a variant's 4-value vectors per
+ * thread per stage (a stage holds 1024 * vpt values), its ring depth, the
+ * number of stages per scan tile and the CTAs per SM its register budget
+ * allows.  kind: 0 = quantize, 1 = dequantize (the dequantize choice is per
+ * dtype; bound_type is ignored).  Choices are process-wide and affect later
+ * launches.  lcq_autotune_quantize / lcq_autotune_dequantize run the given
+ * call once per variant as warm-up plus `reps` timed times (CUDA events on
+ * `stream`), select the fastest, and write the per-variant milliseconds to
+ * h_ms[lcq_tune_variant_count()] if it is not NULL.  They synchronise the
+ * stream and overwrite the outputs of the call.
+ */
+int lcq_tune_variant_count(void);
+lcq_status lcq_tune_describe(int variant, int* vpt, int* stages, int* sub, int* min_ctas_per_sm);
+lcq_status lcq_tune_set(int kind, lcq_dtype dtype, lcq_bound_type bound_type, int variant);
+int lcq_tune_get(int kind, lcq_dtype dtype, lcq_bound_type bound_type);
+lcq_status lcq_autotune_quantize(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* d_in,
+                                 uint64_t n, int32_t* d_bins, uint32_t* d_mask, void* d_outliers,
+                                 uint64_t outlier_capacity, lcq_header* d_hdr, void* d_ws,
+                                 size_t ws_bytes, cudaStream_t stream, int reps, float* h_ms);
+lcq_status lcq_autotune_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
+                                   const int32_t* d_bins, const uint32_t* d_mask, const void* d_outliers,
+                                   void* d_out, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                                   int reps, float* h_ms);
+
+/*
  * Allocation-free variant of lcq_quantize.  The paper has no counterpart;
  * this entry point exists for callers that cannot allocate device memory
  * where they quantize (code inside a no-allocation region such as a fixed

@@ -202,7 +202,8 @@ __device__ __forceinline__ bool abs_quant(T x, const Consts<T>& c, int32_t& bin)
     int32_t b;
     T bf;
     Cv<T>::round(q, b, bf);  // b = rint(q), bf = (T)b
-    if ((b >= kMaxBinAbs) || (b <= -kMaxBinAbs)) return false;
+    // Sec. 3.3: (b >= maxbin) || (b <= -maxbin), as one unsigned comparison
+    if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;
     const T recon = F::mul(bf, c.scale);
     if (!(F::fabs_(F::sub(x, recon)) <= c.ebT)) return false;
     bin = b;
@@ -253,7 +254,7 @@ __device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin)
     int32_t b;
     T bf;
     Cv<T>::round(q, b, bf);
-    if ((b >= kMaxBinRel) || (b <= -kMaxBinRel)) return false;
+    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
     const T Lr = F::mul(bf, c.scale);
     const T bb = F::add(Lr, F::bias_f());
     if (!(bb >= T(1) && bb < F::top_bb())) return false;

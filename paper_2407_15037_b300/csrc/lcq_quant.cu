@@ -39,8 +39,22 @@ constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (s
 
 // Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
 // the depth of the shared-memory stage ring.
-constexpr int kVptF32 = 8, kStagesF32 = 3, kSubF32 = 4;  // 8192-value stages (32 KB), 32K-value scan tiles
-constexpr int kVptF64 = 4, kStagesF64 = 3, kSubF64 = 4;  // 4096-value stages (32 KB), 16K-value scan tiles
+// Tile shapes ("variants"): VPT 4-value vectors per compute thread per stage
+// (stage = 1024 VPT values), STAGES ring depth, SUB stages per scan tile,
+// MINB CTAs per SM the register budget must allow.  lcq_tune_* selects one
+// per (kernel, dtype, bound type); lcq_autotune_quantize times them all.
+struct Variant {
+    int vpt, stages, sub, minb;
+};
+constexpr Variant kVariants[] = {
+    {8, 3, 4, 2},  // 0: 32 KB float stages, 2 CTAs/SM
+    {4, 3, 8, 3},  // 1: 16 KB float stages, 3 CTAs/SM
+    {4, 3, 4, 4},  // 2: 16 KB float stages, 4 CTAs/SM
+    {4, 4, 4, 3},  // 3
+    {2, 6, 8, 4},  // 4: 8 KB float stages, 4 CTAs/SM
+    {8, 2, 4, 2},  // 5
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static ScanCfg g_scan = {kDefaultSpin, ~0ull};
 
@@ -192,8 +206,8 @@ constexpr int kComputeThreads = 256;
 constexpr int kSpecThreads = kComputeThreads + 32;
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
-template <typename T, int MODE, int VPT, int STAGES, int SUB>
-__global__ void __launch_bounds__(kSpecThreads, 2) k_quantize(QParams<T> p) {
+template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
+__global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
     using F = Ty<T>;
     constexpr int STILE = kComputeThreads * 4 * VPT;  // values per stage (sub-tile)
     constexpr int TILE = STILE * SUB;                  // values per scan tile
@@ -628,8 +642,8 @@ struct DParams {
     ScanCfg scan;
 };
 
-template <typename T, int VPT, int STAGES, int SUB>
-__global__ void __launch_bounds__(kSpecThreads, 2) k_dequantize(DParams<T> p) {
+template <typename T, int VPT, int STAGES, int SUB, int MINB>
+__global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p) {
     using F = Ty<T>;
     constexpr int STILE = kComputeThreads * 4 * VPT;
     constexpr int TILE = STILE * SUB;
@@ -892,12 +906,12 @@ static int persistent_blocks(K kernel, size_t dyn_smem, int threads, GridCache& 
     return cache.blocks_per_sm[slot] * device_sms(dev);
 }
 
-template <typename T, int MODE, int VPT, int STAGES, int SUB>
+template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
 static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
     static GridCache cache{};
     constexpr int STILE = kComputeThreads * 4 * VPT;
     const size_t smem = (size_t)STAGES * STILE * sizeof(T);
-    auto kern = k_quantize<T, MODE, VPT, STAGES, SUB>;
+    auto kern = k_quantize<T, MODE, VPT, STAGES, SUB, MINB>;
     QParams<T> q = p;
     q.num_tiles = (uint32_t)tiles_of(p.n, STILE * SUB);
     uint64_t grid = (uint64_t)persistent_blocks(kern, smem, kSpecThreads, cache);
@@ -906,12 +920,12 @@ static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
     return cudaPeekAtLastError();
 }
 
-template <typename T, int VPT, int STAGES, int SUB>
+template <typename T, int VPT, int STAGES, int SUB, int MINB>
 static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
     static GridCache cache{};
     constexpr int STILE = kComputeThreads * 4 * VPT;
     const size_t smem = (size_t)STAGES * (STILE + STILE / 32) * 4;
-    auto kern = k_dequantize<T, VPT, STAGES, SUB>;
+    auto kern = k_dequantize<T, VPT, STAGES, SUB, MINB>;
     DParams<T> q = p;
     q.num_tiles = (uint32_t)tiles_of(p.n, STILE * SUB);
     uint64_t grid = (uint64_t)persistent_blocks(kern, smem, kSpecThreads, cache);
@@ -919,6 +933,38 @@ static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
     kern<<<(unsigned)grid, kSpecThreads, smem, st>>>(q);
     return cudaPeekAtLastError();
 }
+
+// Variant dispatch (the template arguments must be compile-time constants).
+#define LCQ_VARIANT_CASES(CALL)                                   \
+    case 0: return CALL(kVariants[0].vpt, kVariants[0].stages, kVariants[0].sub, kVariants[0].minb); \
+    case 1: return CALL(kVariants[1].vpt, kVariants[1].stages, kVariants[1].sub, kVariants[1].minb); \
+    case 2: return CALL(kVariants[2].vpt, kVariants[2].stages, kVariants[2].sub, kVariants[2].minb); \
+    case 3: return CALL(kVariants[3].vpt, kVariants[3].stages, kVariants[3].sub, kVariants[3].minb); \
+    case 4: return CALL(kVariants[4].vpt, kVariants[4].stages, kVariants[4].sub, kVariants[4].minb); \
+    case 5: return CALL(kVariants[5].vpt, kVariants[5].stages, kVariants[5].sub, kVariants[5].minb);
+
+template <typename T, int MODE>
+static cudaError_t launch_quantize_variant(int v, const QParams<T>& p, cudaStream_t st) {
+    switch (v) {
+#define Q_CALL(a, b, c, d) launch_quantize<T, MODE, a, b, c, d>(p, st)
+        LCQ_VARIANT_CASES(Q_CALL)
+#undef Q_CALL
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename T>
+static cudaError_t launch_dequantize_variant(int v, const DParams<T>& p, cudaStream_t st) {
+    switch (v) {
+#define D_CALL(a, b, c, d) launch_dequantize<T, a, b, c, d>(p, st)
+        LCQ_VARIANT_CASES(D_CALL)
+#undef D_CALL
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Selected variant per kernel kind (0 quantize, 1 dequantize), dtype, bound type.
+static int g_variant[2][2][3] = {{{0, 0, 0}, {0, 0, 0}}, {{0, 0, 0}, {0, 0, 0}}};
 
 // RD_f32(d): the largest float not above d.
 static float rd_f32_host(double d) {
@@ -1056,14 +1102,9 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.eb = eb;
         p.eb_abs = eb_abs;
         p.n_total = n;
-        cudaError_t e;
-        if constexpr (sizeof(T) == 4) {
-            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF32, kStagesF32, kSubF32>(p, st)
-                              : launch_quantize<T, LCQ_ABS, kVptF32, kStagesF32, kSubF32>(p, st);
-        } else {
-            e = bt == LCQ_REL ? launch_quantize<T, LCQ_REL, kVptF64, kStagesF64, kSubF64>(p, st)
-                              : launch_quantize<T, LCQ_ABS, kVptF64, kStagesF64, kSubF64>(p, st);
-        }
+        const int var = g_variant[0][dtype][bt];
+        const cudaError_t e = bt == LCQ_REL ? launch_quantize_variant<T, LCQ_REL>(var, p, st)
+                                            : launch_quantize_variant<T, LCQ_ABS>(var, p, st);
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
@@ -1096,9 +1137,7 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
         p.scan = g_scan;
-        cudaError_t e;
-        if constexpr (sizeof(T) == 4) e = launch_dequantize<T, kVptF32, kStagesF32, kSubF32>(p, st);
-        else e = launch_dequantize<T, kVptF64, kStagesF64, kSubF64>(p, st);
+        const cudaError_t e = launch_dequantize_variant<T>(g_variant[1][p.dtype][0], p, st);
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
@@ -1232,6 +1271,109 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
     if (h_hdr->status & LCQ_STATUS_TIMEOUT) return LCQ_ERR_TIMEOUT;
     if (h_hdr->status & LCQ_STATUS_CAPACITY) return LCQ_ERR_CAPACITY;
     return LCQ_OK;
+}
+
+int lcq_tune_variant_count(void) { return kNumVariants; }
+
+lcq_status lcq_tune_describe(int variant, int* vpt, int* stages, int* sub, int* min_ctas_per_sm) {
+    if (variant < 0 || variant >= kNumVariants) return LCQ_ERR_ARG;
+    if (vpt) *vpt = kVariants[variant].vpt;
+    if (stages) *stages = kVariants[variant].stages;
+    if (sub) *sub = kVariants[variant].sub;
+    if (min_ctas_per_sm) *min_ctas_per_sm = kVariants[variant].minb;
+    return LCQ_OK;
+}
+
+lcq_status lcq_tune_set(int kind, lcq_dtype dtype, lcq_bound_type bound_type, int variant) {
+    if (kind < 0 || kind > 1 || (dtype != LCQ_F32 && dtype != LCQ_F64) || (int)bound_type < 0 ||
+        (int)bound_type > 2 || variant < 0 || variant >= kNumVariants)
+        return LCQ_ERR_ARG;
+    g_variant[kind][dtype][kind == 1 ? 0 : bound_type] = variant;
+    return LCQ_OK;
+}
+
+int lcq_tune_get(int kind, lcq_dtype dtype, lcq_bound_type bound_type) {
+    if (kind < 0 || kind > 1 || (dtype != LCQ_F32 && dtype != LCQ_F64) || (int)bound_type < 0 ||
+        (int)bound_type > 2)
+        return -1;
+    return g_variant[kind][dtype][kind == 1 ? 0 : bound_type];
+}
+
+lcq_status lcq_autotune_quantize(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* d_in,
+                                 uint64_t n, int32_t* d_bins, uint32_t* d_mask, void* d_outliers,
+                                 uint64_t outlier_capacity, lcq_header* d_hdr, void* d_ws,
+                                 size_t ws_bytes, cudaStream_t stream, int reps, float* h_ms) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if ((int)bound_type < 0 || (int)bound_type > 2) return LCQ_ERR_ARG;
+    if (reps < 1) reps = 1;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return LCQ_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return LCQ_ERR_CUDA; }
+    const int saved = g_variant[0][dtype][bound_type];
+    int best = saved;
+    float best_ms = 0.0f;
+    lcq_status st = LCQ_OK;
+    for (int v = 0; v < kNumVariants && st == LCQ_OK; v++) {
+        g_variant[0][dtype][bound_type] = v;
+        st = lcq_quantize(dtype, bound_type, eb, d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
+                          d_hdr, d_ws, ws_bytes, stream);  // warm-up
+        cudaEventRecord(a, stream);
+        for (int r = 0; r < reps && st == LCQ_OK; r++)
+            st = lcq_quantize(dtype, bound_type, eb, d_in, n, d_bins, d_mask, d_outliers,
+                              outlier_capacity, d_hdr, d_ws, ws_bytes, stream);
+        cudaEventRecord(b, stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) st = LCQ_ERR_CUDA;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= reps;
+        if (h_ms) h_ms[v] = ms;
+        if (st == LCQ_OK && (v == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    g_variant[0][dtype][bound_type] = st == LCQ_OK ? best : saved;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
+}
+
+lcq_status lcq_autotune_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
+                                   const int32_t* d_bins, const uint32_t* d_mask, const void* d_outliers,
+                                   void* d_out, void* d_ws, size_t ws_bytes, cudaStream_t stream,
+                                   int reps, float* h_ms) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (reps < 1) reps = 1;
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return LCQ_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return LCQ_ERR_CUDA; }
+    const int saved = g_variant[1][dtype][0];
+    int best = saved;
+    float best_ms = 0.0f;
+    lcq_status st = LCQ_OK;
+    for (int v = 0; v < kNumVariants && st == LCQ_OK; v++) {
+        g_variant[1][dtype][0] = v;
+        st = lcq_dequantize(dtype, n, d_hdr, d_bins, d_mask, d_outliers, d_out, nullptr, d_ws, ws_bytes,
+                            stream);
+        cudaEventRecord(a, stream);
+        for (int r = 0; r < reps && st == LCQ_OK; r++)
+            st = lcq_dequantize(dtype, n, d_hdr, d_bins, d_mask, d_outliers, d_out, nullptr, d_ws,
+                                ws_bytes, stream);
+        cudaEventRecord(b, stream);
+        if (cudaEventSynchronize(b) != cudaSuccess) st = LCQ_ERR_CUDA;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, a, b);
+        ms /= reps;
+        if (h_ms) h_ms[v] = ms;
+        if (st == LCQ_OK && (v == 0 || ms < best_ms)) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    g_variant[1][dtype][0] = st == LCQ_OK ? best : saved;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return st;
 }
 
 void lcq_debug_set_scan(uint32_t spin_limit, uint64_t drop_tile) {

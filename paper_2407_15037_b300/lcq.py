@@ -61,6 +61,14 @@ SIGNATURES = {
     "lcq_quantize_host": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
                            _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
     "lcq_debug_set_scan": ([_u32, _u64], None),
+    "lcq_tune_variant_count": ([], ctypes.c_int),
+    "lcq_tune_describe": ([ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "lcq_tune_set": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lcq_tune_get": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lcq_autotune_quantize": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
+                               _vp, _sz, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "lcq_autotune_dequantize": ([ctypes.c_int, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp,
+                                 ctypes.c_int, _vp], ctypes.c_int),
     "lcq_noalloc_max_values": ([], _u64),
     "lcq_quantize_noalloc": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
                               _vp], ctypes.c_int),
@@ -218,6 +226,47 @@ def sync_status(q, stream=None):
     cnt = ctypes.c_uint64()
     code = lib().lcq_sync_status(_ptr(q.header), ctypes.byref(cnt), _stream_ptr(stream, q.bins.device))
     return code, cnt.value
+
+
+def variant_count():
+    return int(lib().lcq_tune_variant_count())
+
+
+def describe_variant(v):
+    a = [ctypes.c_int() for _ in range(4)]
+    _check(lib().lcq_tune_describe(int(v), *[ctypes.byref(x) for x in a]), "lcq_tune_describe")
+    return dict(vpt=a[0].value, stages=a[1].value, sub=a[2].value, min_ctas_per_sm=a[3].value)
+
+
+def set_variant(kind, dtype_code, bound, v):
+    _check(lib().lcq_tune_set(int(kind), int(dtype_code), _bound_code(bound), int(v)), "lcq_tune_set")
+
+
+def get_variant(kind, dtype_code, bound):
+    return int(lib().lcq_tune_get(int(kind), int(dtype_code), _bound_code(bound)))
+
+
+def autotune_quantize(x, bound, eb, q, ws, reps=5, stream=None):
+    """Time every tile-shape variant on this call and keep the fastest;
+    returns the per-variant milliseconds."""
+    nv = variant_count()
+    ms = (ctypes.c_float * nv)()
+    code = lib().lcq_autotune_quantize(
+        _dtype_code(x), _bound_code(bound), float(eb), _ptr(x), x.numel(), _ptr(q.bins),
+        _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header), _ptr(ws), ws.numel(),
+        _stream_ptr(stream, x.device), int(reps), ms)
+    _check(code, "lcq_autotune_quantize")
+    return list(ms)
+
+
+def autotune_dequantize(q, out, ws, reps=5, stream=None):
+    nv = variant_count()
+    ms = (ctypes.c_float * nv)()
+    code = lib().lcq_autotune_dequantize(
+        _dtype_code(out), q.n, _ptr(q.header), _ptr(q.bins), _ptr(q.mask), _ptr(q.outliers),
+        _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream, out.device), int(reps), ms)
+    _check(code, "lcq_autotune_dequantize")
+    return list(ms)
 
 
 def debug_set_scan(spin_limit=0, drop_tile=(1 << 64) - 1):

@@ -176,6 +176,24 @@ def test_host_entry_point_matches_device_path():
     assert torch.equal(outs.header, qd.header.cpu())
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_every_tile_shape_variant_matches_oracle(dtype):
+    """Every tile shape the autotuner may pick gives the same bits."""
+    x = synth.smooth_field((71, 67, 59), dtype=dtype, seed=5, device=DEV)  # ragged: 280,663 values
+    x[::1001] = float("nan")
+    try:
+        for v in range(P.lcq.variant_count()):
+            for bound in BOUNDS:
+                P.lcq.set_variant(0, P.lcq._dtype_code(x), bound, v)
+            P.lcq.set_variant(1, P.lcq._dtype_code(x), "abs", v)
+            for bound in BOUNDS:
+                compare(x, bound, 1e-4)
+    finally:
+        for bound in BOUNDS:
+            P.lcq.set_variant(0, P.lcq._dtype_code(x), bound, 0)
+        P.lcq.set_variant(1, P.lcq._dtype_code(x), "abs", 0)
+
+
 # --------------------------------------------------------- full sizes ----
 
 @pytest.mark.parametrize("bound", BOUNDS)
