@@ -277,6 +277,110 @@ __device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin)
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// Four values at a time (one 128-bit load), float32.  When every lane of the
+// warp has |q| < 2^22 for all four of its values -- the usual case -- one
+// warp-uniform branch selects straight-line code without per-value branches;
+// otherwise the per-value recipes above run.  Both give identical results:
+// the fast code is the same sequence of IEEE operations, and the checks it
+// leaves out are implied by |q| < 2^22 (no integer overflow, |b| <= 2^22 <
+// maxbin).  Returns the 4-bit outlier nibble; bins of outliers are 0.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
+    float q[4];
+    bool small = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        q[k] = __fmul_rn(x[k], c.inv);
+        small &= fabsf(q[k]) < 0x1p22f;
+    }
+    uint32_t nb = 0;
+    if (__all_sync(0xFFFFFFFFu, small)) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float t = __fadd_rn(q[k], 0x1.8p23f);
+            const int32_t bi = __float_as_int(t) - 0x4B400000;
+            const float recon = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
+            const bool ok = fabsf(__fsub_rn(x[k], recon)) <= c.ebT;
+            b[k] = ok ? bi : 0;
+            nb |= ok ? 0u : (1u << k);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int32_t bin = 0;
+            const bool ok = abs_quant<float>(x[k], c, bin);
+            b[k] = ok ? bin : 0;
+            nb |= ok ? 0u : (1u << k);
+        }
+    }
+    return nb;
+}
+
+__device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
+    float q[4], L[4];
+    bool small = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        L[k] = log2approx<float>(__float_as_uint(x[k]));  // finite for every bit pattern
+        q[k] = __fmul_rn(L[k], c.inv);
+        small &= fabsf(q[k]) < 0x1p22f;
+    }
+    uint32_t nb = 0;
+    if (__all_sync(0xFFFFFFFFu, small)) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const uint32_t u = __float_as_uint(x[k]);
+            const uint32_t E = (u >> 23) & 0xFFu;
+            const float a = __uint_as_float(u & 0x7FFFFFFFu);
+            const float t = __fadd_rn(q[k], 0x1.8p23f);
+            const int32_t bi = __float_as_int(t) - 0x4B400000;
+            const float Lr = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
+            const float bb = __fadd_rn(Lr, 127.0f);
+            const float m = __uint_as_float(pow2approx_bits<float>(bb));
+            const float d = fabsf(__fsub_rn(a, m));
+            const float lo = fminf(a, m);
+            bool ok = (E - 1u < 254u) && (bb >= 1.0f) && (bb < 255.0f) &&
+                      (a <= __fmul_rn(2.0f, m)) && (m <= __fmul_rn(2.0f, a));
+            if (lo < 0x1p-62f) {  // rare: exact power-of-two rescale
+                const float tt = __fmul_rn(__fmul_rn(lo, 0x1p64f), c.chk);
+                ok = ok && (tt >= FLT_MIN) && (__fmul_rn(d, 0x1p64f) <= tt);
+            } else {
+                const float tt = __fmul_rn(lo, c.chk);
+                ok = ok && (tt >= FLT_MIN) && (d <= tt);
+            }
+            b[k] = ok ? (int32_t)(((uint32_t)bi << 1) | (u >> 31)) : 0;
+            nb |= ok ? 0u : (1u << k);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int32_t bin = 0;
+            const bool ok = rel_quant<float>(x[k], c, bin);
+            b[k] = ok ? bin : 0;
+            nb |= ok ? 0u : (1u << k);
+        }
+    }
+    return nb;
+}
+
+template <typename T, int MODE>
+__device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<T>& c, int32_t b[4]) {
+    if constexpr (sizeof(T) == 4) {
+        return MODE == LCQ_REL ? rel_quant4_f32(x, c, b) : abs_quant4_f32(x, c, b);
+    } else {
+        uint32_t nb = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int32_t bin = 0;
+            const bool ok = (MODE == LCQ_REL) ? rel_quant<T>(x[k], c, bin) : abs_quant<T>(x[k], c, bin);
+            b[k] = ok ? bin : 0;
+            nb |= ok ? 0u : (1u << k);
+        }
+        return nb;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T rel_recon(int32_t bin, const Consts<T>& c) {
     using F = Ty<T>;

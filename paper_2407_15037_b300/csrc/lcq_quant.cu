@@ -58,6 +58,11 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static ScanCfg g_scan = {kDefaultSpin, ~0ull};
 
+// Shared-memory position of mask word w of a scan tile: the low 5 bits are
+// XOR-ed with the row (w / 32), so that the scan warp's lanes, which read 16
+// or 32 consecutive words each, hit 32 different banks.
+__device__ __forceinline__ int sw(int w) { return w ^ ((w >> 5) & 31); }
+
 // ---------------------------------------------------------------------------
 // Vector access helpers: 4 consecutive values per thread per step.
 // ---------------------------------------------------------------------------
@@ -173,7 +178,7 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
     uint32_t wv[WPL], loc[WPL], cnt = 0;
 #pragma unroll
     for (int j = 0; j < WPL; j++) {
-        wv[j] = s_words[lane * WPL + j];
+        wv[j] = s_words[sw(lane * WPL + j)];
         loc[j] = cnt;
         cnt += __popc(wv[j]);
     }
@@ -186,7 +191,7 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
     }
     const uint32_t ex = incl - cnt;
 #pragma unroll
-    for (int j = 0; j < WPL; j++) s_wpre[lane * WPL + j] = ex + loc[j];
+    for (int j = 0; j < WPL; j++) s_wpre[sw(lane * WPL + j)] = ex + loc[j];
     return __shfl_sync(0xFFFFFFFFu, incl, 31);
 }
 
@@ -205,6 +210,7 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
 constexpr int kComputeThreads = 256;
 constexpr int kSpecThreads = kComputeThreads + 32;
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
 
 template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
 __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
@@ -278,9 +284,9 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             const uint64_t tb = (uint64_t)s_jt[bb] * TILE;
             const uint64_t pbase = s_pbase[bb];
             for (int w = tid; w < WORDS; w += kComputeThreads) {
-                uint32_t mw = s_mask[bb][w];
+                uint32_t mw = s_mask[bb][sw(w)];
                 if (!mw) continue;
-                const uint32_t pre = s_wpre[bb][w];
+                const uint32_t pre = s_wpre[bb][sw(w)];
                 uint32_t below = 0;
                 while (mw) {
                     const int bit = __ffs(mw) - 1;
@@ -312,14 +318,15 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             }
             const T* st = sbuf + (size_t)s * STILE;
             const uint64_t sbase = g * STILE;
-            uint32_t* smw = &s_mask[b][sub * SWORDS + warp * 4 + (lane >> 3)];
+            uint32_t* smw = s_mask[b];
+            const int wbase = sub * SWORDS + warp * 4 + (lane >> 3);
             // 4-value outlier nibbles of 8 lanes -> one mask word
             auto put_word = [&](int v, uint32_t nb) {
                 uint32_t w = nb << ((lane & 7) * 4);
                 w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
                 w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
                 w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
-                if ((lane & 7) == 0) smw[v * (kComputeThreads / 8)] = w;
+                if ((lane & 7) == 0) smw[sw(wbase + v * (kComputeThreads / 8))] = w;
             };
             if (from_smem && !c.all_outliers) {
                 // fast path: a whole sub-tile in shared memory, no bounds checks
@@ -330,14 +337,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                     T x[4];
                     Vec4<T>::load_shared(st + off, x);
                     int32_t bn[4];
-                    uint32_t nb = 0;
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        int32_t bin = 0;
-                        const bool ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
-                        nb |= ok ? 0u : (1u << q);
-                        bn[q] = ok ? bin : 0;
-                    }
+                    const uint32_t nb = quant4<T, MODE>(x, c, bn);
                     __stcs(reinterpret_cast<int4*>(gb + off), make_int4(bn[0], bn[1], bn[2], bn[3]));
                     put_word(v, nb);
                 }
@@ -724,9 +724,9 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
             const uint64_t tb = (uint64_t)s_jt[bb] * TILE;
             const uint64_t pbase = s_pbase[bb];
             for (int w = tid; w < WORDS; w += kComputeThreads) {
-                uint32_t mw = s_mask[bb][w];
+                uint32_t mw = s_mask[bb][sw(w)];
                 if (!mw) continue;
-                const uint32_t pre = s_wpre[bb][w];
+                const uint32_t pre = s_wpre[bb][sw(w)];
                 uint32_t below = 0;
                 while (mw) {
                     const int bit = __ffs(mw) - 1;
@@ -760,7 +760,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
             const uint64_t sbase = g * STILE;
             for (int w = tid; w < SWORDS; w += kComputeThreads) {
                 const uint64_t gw = g * SWORDS + w;
-                s_mask[b][sub * SWORDS + w] = from_smem ? sb[STILE + w] : (gw < nwords ? p.mask[gw] : 0u);
+                s_mask[b][sw(sub * SWORDS + w)] = from_smem ? sb[STILE + w] : (gw < nwords ? p.mask[gw] : 0u);
             }
             if (from_smem) {
                 // fast path: a whole sub-tile in shared memory, no bounds checks
@@ -964,7 +964,8 @@ static cudaError_t launch_dequantize_variant(int v, const DParams<T>& p, cudaStr
 }
 
 // Selected variant per kernel kind (0 quantize, 1 dequantize), dtype, bound type.
-static int g_variant[2][2][3] = {{{0, 0, 0}, {0, 0, 0}}, {{0, 0, 0}, {0, 0, 0}}};
+// Defaults from autotuning on a B300 (float32 512^3 field, float64 256^3 field).
+static int g_variant[2][2][3] = {{{1, 3, 1}, {2, 2, 2}}, {{5, 5, 5}, {2, 2, 2}}};
 
 // RD_f32(d): the largest float not above d.
 static float rd_f32_host(double d) {

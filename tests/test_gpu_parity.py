@@ -181,6 +181,8 @@ def test_every_tile_shape_variant_matches_oracle(dtype):
     """Every tile shape the autotuner may pick gives the same bits."""
     x = synth.smooth_field((71, 67, 59), dtype=dtype, seed=5, device=DEV)  # ragged: 280,663 values
     x[::1001] = float("nan")
+    dc = P.lcq._dtype_code(x)
+    saved = [P.lcq.get_variant(0, dc, b) for b in BOUNDS] + [P.lcq.get_variant(1, dc, "abs")]
     try:
         for v in range(P.lcq.variant_count()):
             for bound in BOUNDS:
@@ -189,9 +191,9 @@ def test_every_tile_shape_variant_matches_oracle(dtype):
             for bound in BOUNDS:
                 compare(x, bound, 1e-4)
     finally:
-        for bound in BOUNDS:
-            P.lcq.set_variant(0, P.lcq._dtype_code(x), bound, 0)
-        P.lcq.set_variant(1, P.lcq._dtype_code(x), "abs", 0)
+        for bound, v in zip(BOUNDS, saved):
+            P.lcq.set_variant(0, dc, bound, v)
+        P.lcq.set_variant(1, dc, "abs", saved[3])
 
 
 # --------------------------------------------------------- full sizes ----
