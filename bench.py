@@ -36,7 +36,7 @@ SHAPE = (512, 512, 512)
 WORKLOAD = ("quantize+verify sweep {ABS,REL,NOA} x eb {1e-2,1e-3,1e-4,1e-5} on a float32 "
             "512^3 field (8 random 3-D sinusoids + N(0,0.01)), outlier compaction included")
 KERNEL_SOURCES = ["paper_2407_15037_b300/csrc/lcq_quant.cu", "paper_2407_15037_b300/csrc/lcq_device.cuh",
-                  "paper_2407_15037_b300/csrc/lcq_pipe.cuh"]
+                  "paper_2407_15037_b300/csrc/lcq_pipe.cuh", "paper_2407_15037_b300/csrc/lcq_tile.cuh"]
 
 
 def kernel_sha():

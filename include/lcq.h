@@ -167,6 +167,68 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
                              cudaStream_t stream);
 
 /*
+ * Batched quantization (no counterpart in the paper, which quantizes one file
+ * at a time): many arrays of different sizes, data types, bound types and
+ * bounds in one persistent launch.  Each array gets exactly the result that
+ * lcq_quantize gives it alone (same bins, mask, outliers and header).
+ *
+ *   lcq_batch_item   one array: the arguments of lcq_quantize.
+ *   lcq_batch_plan_size(count)            device bytes of the plan.
+ *   lcq_batch_workspace_size(items, count) device bytes of the workspace.
+ *   lcq_batch_prepare(...)  validates the items, derives the ABS/REL constants
+ *       on the host, writes the plan (a descriptor table and the scan-tile
+ *       prefix) to d_plan, initialises the workspace, and fills *h_info.  It
+ *       synchronises `stream`.  Errors: LCQ_ERR_ARG / LCQ_ERR_BOUND for the
+ *       first bad item (its index in h_info->bad_item).
+ *   lcq_quantize_batched(info, plan, ws, stream)  enqueues two kernels: a
+ *       header / NOA range pass over all arrays (min/max over finite values
+ *       of every NOA array, its bound derived on the device) and one
+ *       persistent quantize launch over every array's tiles.  No host work,
+ *       no synchronisation, no allocation: it can be captured in a CUDA graph
+ *       and replayed; each replay re-reads the inputs and rewrites every
+ *       output.  Per-array device errors go to that array's header status.
+ *   lcq_batch_tune_*  tile-shape variants of the batched kernel (as for the
+ *       single-array kernels below); lcq_autotune_batched times each on the
+ *       batch itself and keeps the fastest (synchronises the stream).
+ */
+typedef struct lcq_batch_item {
+    uint32_t dtype;            /* lcq_dtype */
+    uint32_t bound_type;       /* lcq_bound_type */
+    double eb;
+    uint64_t n;
+    const void* d_in;
+    int32_t* d_bins;
+    uint32_t* d_mask;
+    void* d_outliers;
+    uint64_t outlier_capacity;
+    lcq_header* d_hdr;
+} lcq_batch_item;
+
+typedef struct lcq_batch_info {
+    uint32_t count;            /* arrays */
+    uint32_t noa_count;        /* NOA arrays */
+    uint64_t total_tiles;      /* 16384-value scan tiles over all arrays */
+    uint64_t noa_chunks;       /* 16384-value range chunks over the NOA arrays */
+    uint64_t total_values;
+    uint64_t total_bytes_in;
+    uint32_t bad_item;         /* index of the first rejected item, or UINT32_MAX */
+    uint32_t reserved;
+} lcq_batch_info;
+
+size_t lcq_batch_plan_size(uint32_t count);
+size_t lcq_batch_workspace_size(const lcq_batch_item* h_items, uint32_t count);
+lcq_status lcq_batch_prepare(const lcq_batch_item* h_items, uint32_t count, void* d_plan,
+                             size_t plan_bytes, void* d_ws, size_t ws_bytes, lcq_batch_info* h_info,
+                             cudaStream_t stream);
+lcq_status lcq_quantize_batched(const lcq_batch_info* h_info, const void* d_plan, void* d_ws,
+                                size_t ws_bytes, cudaStream_t stream);
+int lcq_batch_tune_variant_count(void);
+lcq_status lcq_batch_tune_set(int variant);
+int lcq_batch_tune_get(void);
+lcq_status lcq_autotune_batched(const lcq_batch_info* h_info, const void* d_plan, void* d_ws,
+                                size_t ws_bytes, cudaStream_t stream, int reps, float* h_ms);
+
+/*
  * Tile-shape tuning (no counterpart in the paper; it only affects speed, never
  * results).  The streaming kernels come in lcq_tune_variant_count() tile
  * shapes ("variants"): lcq_tune_describe gives a variant's 4-value vectors per

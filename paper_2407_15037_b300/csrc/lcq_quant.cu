@@ -28,6 +28,8 @@
 
 #include "lcq_device.cuh"
 #include "lcq_pipe.cuh"
+#include "lcq_tile.cuh"
+#include "lcq_host.h"
 
 namespace lcq {
 
@@ -58,59 +60,6 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static ScanCfg g_scan = {kDefaultSpin, ~0ull};
 
-// Shared-memory position of mask word w of a scan tile: the low 5 bits are
-// XOR-ed with the row (w / 32), so that the scan warp's lanes, which read 16
-// or 32 consecutive words each, hit 32 different banks.
-__device__ __forceinline__ int sw(int w) { return w ^ ((w >> 5) & 31); }
-
-// ---------------------------------------------------------------------------
-// Vector access helpers: 4 consecutive values per thread per step.
-// ---------------------------------------------------------------------------
-template <typename T>
-struct Vec4;
-
-template <>
-struct Vec4<float> {
-    static __device__ __forceinline__ void load(const float* p, float v[4]) {
-        const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    }
-    static __device__ __forceinline__ void load_shared(const float* p, float v[4]) {
-        const float4 a = *reinterpret_cast<const float4*>(p);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    }
-    static __device__ __forceinline__ void load_cached(const float* p, float v[4]) {
-        const float4 a = *reinterpret_cast<const float4*>(p);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    }
-    static __device__ __forceinline__ void store(float* p, const float v[4]) {
-        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
-    }
-};
-
-template <>
-struct Vec4<double> {
-    static __device__ __forceinline__ void load(const double* p, double v[4]) {
-        const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
-        const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void load_shared(const double* p, double v[4]) {
-        const double2 a = reinterpret_cast<const double2*>(p)[0];
-        const double2 b = reinterpret_cast<const double2*>(p)[1];
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void load_cached(const double* p, double v[4]) {
-        const double2 a = reinterpret_cast<const double2*>(p)[0];
-        const double2 b = reinterpret_cast<const double2*>(p)[1];
-        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
-    }
-    static __device__ __forceinline__ void store(double* p, const double v[4]) {
-        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
-        __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
-    }
-};
-
 // ---------------------------------------------------------------------------
 // Quantize kernel: persistent CTAs; input tiles stream into a ring of
 // shared-memory stages by bulk asynchronous copies, so that the next tiles
@@ -139,62 +88,6 @@ struct QParams {
     uint64_t n_total;
 };
 
-template <typename T, int VPT>
-__device__ __forceinline__ void load4(const T* sbuf_tile, const T* gin, bool from_smem, int off,
-                                      uint64_t e0, uint64_t n, T x[4]) {
-    if (from_smem) {
-        Vec4<T>::load_shared(sbuf_tile + off, x);
-    } else if (e0 + 4 <= n) {
-        Vec4<T>::load(gin + e0, x);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; k++) x[k] = (e0 + k < n) ? gin[e0 + k] : T(0);
-    }
-}
-
-// Mask words of one tile -> global, 16-byte stores where the tile is whole.
-template <int WPL>
-__device__ __forceinline__ void store_mask_words(uint32_t* gmask, uint64_t gw, uint64_t nwords,
-                                                 const uint32_t* wv) {
-#pragma unroll
-    for (int j = 0; j < WPL; j += 4) {
-        if (gw + j + 4 <= nwords) {
-            __stcs(reinterpret_cast<uint4*>(gmask + gw + j), make_uint4(wv[j], wv[j + 1], wv[j + 2], wv[j + 3]));
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; i++)
-                if (gw + j + i < nwords) gmask[gw + j + i] = wv[j + i];
-        }
-    }
-}
-
-// Warp 0: exclusive prefix popcounts of the tile's mask words into s_wpre;
-// returns the tile's outlier count.  Also stores the words to global memory.
-template <int WPL>
-__device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uint32_t* s_wpre,
-                                                    uint32_t* gmask, uint64_t gw, uint64_t nwords,
-                                                    bool store) {
-    const int lane = threadIdx.x & 31;
-    uint32_t wv[WPL], loc[WPL], cnt = 0;
-#pragma unroll
-    for (int j = 0; j < WPL; j++) {
-        wv[j] = s_words[sw(lane * WPL + j)];
-        loc[j] = cnt;
-        cnt += __popc(wv[j]);
-    }
-    if (store) store_mask_words<WPL>(gmask, gw, nwords, wv);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    const uint32_t ex = incl - cnt;
-#pragma unroll
-    for (int j = 0; j < WPL; j++) s_wpre[sw(lane * WPL + j)] = ex + loc[j];
-    return __shfl_sync(0xFFFFFFFFu, incl, 31);
-}
-
 // Warp-specialised streaming kernels.  A CTA has 8 compute warps and one
 // scan warp.  The compute warps stream the CTA's tiles through a ring of
 // shared-memory stages (bulk asynchronous copies, one sub-tile per stage) and
@@ -207,9 +100,6 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
 // Tickets are taken one scan tile at a time as the ring fills, so the global
 // ticket order follows the order in which CTAs reach their tiles, and every
 // CTA handles its tiles in ticket order (needed for the lookback to progress).
-constexpr int kComputeThreads = 256;
-constexpr int kSpecThreads = kComputeThreads + 32;
-constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 
 
 template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
@@ -281,21 +171,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                 s_abort = 1;
             }
             if (named_barrier_or(1, kComputeThreads, !ok)) return true;
-            const uint64_t tb = (uint64_t)s_jt[bb] * TILE;
-            const uint64_t pbase = s_pbase[bb];
-            for (int w = tid; w < WORDS; w += kComputeThreads) {
-                uint32_t mw = s_mask[bb][sw(w)];
-                if (!mw) continue;
-                const uint32_t pre = s_wpre[bb][sw(w)];
-                uint32_t below = 0;
-                while (mw) {
-                    const int bit = __ffs(mw) - 1;
-                    mw &= mw - 1u;
-                    const uint64_t rank = pbase + pre + below++;
-                    // the tile was read moments ago, so this hits L2
-                    if (rank < p.cap) p.out[rank] = F::bits(p.in[tb + (uint64_t)w * 32 + bit]);
-                }
-            }
+            write_outliers<T>(s_mask[bb], s_wpre[bb], WORDS, p.in + (uint64_t)s_jt[bb] * TILE, s_pbase[bb],
+                              p.out, p.cap);
             named_barrier_sync(1, kComputeThreads);  // buffer bb may be reused
             return false;
         };
@@ -318,57 +195,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             }
             const T* st = sbuf + (size_t)s * STILE;
             const uint64_t sbase = g * STILE;
-            uint32_t* smw = s_mask[b];
-            const int wbase = sub * SWORDS + warp * 4 + (lane >> 3);
-            // 4-value outlier nibbles of 8 lanes -> one mask word
-            auto put_word = [&](int v, uint32_t nb) {
-                uint32_t w = nb << ((lane & 7) * 4);
-                w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
-                w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
-                w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
-                if ((lane & 7) == 0) smw[sw(wbase + v * (kComputeThreads / 8))] = w;
-            };
-            if (from_smem && !c.all_outliers) {
-                // fast path: a whole sub-tile in shared memory, no bounds checks
-                int32_t* gb = p.bins + sbase;
-#pragma unroll
-                for (int v = 0; v < VPT; v++) {
-                    const int off = v * (kComputeThreads * 4) + tid * 4;
-                    T x[4];
-                    Vec4<T>::load_shared(st + off, x);
-                    int32_t bn[4];
-                    const uint32_t nb = quant4<T, MODE>(x, c, bn);
-                    __stcs(reinterpret_cast<int4*>(gb + off), make_int4(bn[0], bn[1], bn[2], bn[3]));
-                    put_word(v, nb);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < VPT; v++) {
-                    const int off = v * (kComputeThreads * 4) + tid * 4;
-                    const uint64_t e0 = sbase + off;
-                    T x[4];
-                    load4<T, VPT>(st, p.in, from_smem, off, e0, p.n, x);
-                    int32_t bn[4];
-                    uint32_t nb = 0;
-#pragma unroll
-                    for (int q = 0; q < 4; q++) {
-                        int32_t bin = 0;
-                        bool ok = false;
-                        if (!c.all_outliers)
-                            ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
-                        if (!ok && e0 + q < p.n) nb |= 1u << q;
-                        bn[q] = ok ? bin : 0;
-                    }
-                    if (e0 + 4 <= p.n) {
-                        __stcs(reinterpret_cast<int4*>(p.bins + e0), make_int4(bn[0], bn[1], bn[2], bn[3]));
-                    } else {
-#pragma unroll
-                        for (int q = 0; q < 4; q++)
-                            if (e0 + q < p.n) p.bins[e0 + q] = bn[q];
-                    }
-                    put_word(v, nb);
-                }
-            }
+            quantize_subtile<T, MODE, VPT>(st, p.in + sbase, from_smem, p.n > sbase ? p.n - sbase : 0,
+                                           p.bins + sbase, s_mask[b], (int)sub * SWORDS, c);
             fence_proxy_async_smem();
             bool stop = named_barrier_or(1, kComputeThreads, s_abort != 0);  // stage s consumed
             if (stop) break;
@@ -469,30 +297,6 @@ __global__ void k_header_empty(lcq_header* h, uint32_t dtype, uint32_t bound, do
 // ABS constants, and writes them to the header.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ typename Ty<T>::U order_key(typename Ty<T>::U u) {
-    using U = typename Ty<T>::U;
-    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
-    return (u & sign) ? ~u : (u | sign);
-}
-template <typename T>
-__device__ __forceinline__ typename Ty<T>::U key_to_bits(typename Ty<T>::U k) {
-    using U = typename Ty<T>::U;
-    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
-    return (k & sign) ? (k & ~sign) : ~k;
-}
-
-template <typename T>
-__device__ __forceinline__ void minmax_accum(T x, typename Ty<T>::U& lo, typename Ty<T>::U& hi) {
-    using F = Ty<T>;
-    using U = typename F::U;
-    const U u = F::bits(x);
-    if (((u >> F::kP) & F::kExpAll) == F::kExpAll) return;  // Inf / NaN
-    const U k = order_key<T>(u);
-    lo = k < lo ? k : lo;
-    hi = k > hi ? k : hi;
-}
-
-template <typename T>
 struct MParams {
     const T* in;
     uint64_t n;
@@ -501,50 +305,6 @@ struct MParams {
     uint64_t* partial;  // 2 per block
     double eb;
 };
-
-template <typename T>
-__device__ void noa_finalize(lcq_header* h, bool any, T mn, T mx, double eb) {
-    using F = Ty<T>;
-    uint32_t mode = 1;
-    double R = 0.0, eb_abs = 0.0;
-    uint64_t ebT_b = 0, eb2_b = 0, inv_b = 0;
-    if (any) {
-        R = __dsub_rd((double)mx, (double)mn);
-        eb_abs = __dmul_rd(eb, R);
-        if (sizeof(T) == 4) {
-            const float ebT = __double2float_rd(eb_abs);
-            const float eb2 = __fmul_rn(2.0f, ebT);
-            const float inv = __fdiv_rn(1.0f, eb2);
-            const bool ok = (ebT >= FLT_MIN && ebT <= FLT_MAX) && (eb2 <= FLT_MAX) &&
-                            (inv >= FLT_MIN && inv <= FLT_MAX);
-            if (ok) {
-                mode = 0;
-                ebT_b = __float_as_uint(ebT);
-                eb2_b = __float_as_uint(eb2);
-                inv_b = __float_as_uint(inv);
-            }
-        } else {
-            const double ebT = eb_abs;
-            const double eb2 = __dmul_rn(2.0, ebT);
-            const double inv = __ddiv_rn(1.0, eb2);
-            const bool ok = (ebT >= DBL_MIN && ebT <= DBL_MAX) && (eb2 <= DBL_MAX) &&
-                            (inv >= DBL_MIN && inv <= DBL_MAX);
-            if (ok) {
-                mode = 0;
-                ebT_b = (uint64_t)__double_as_longlong(ebT);
-                eb2_b = (uint64_t)__double_as_longlong(eb2);
-                inv_b = (uint64_t)__double_as_longlong(inv);
-            }
-        }
-    }
-    h->mode = mode;
-    h->range = R;
-    h->eb_abs = eb_abs;
-    h->ebT_bits = ebT_b;
-    h->scale_bits = eb2_b;
-    h->inv_bits = inv_b;
-    h->chk_bits = 0;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_minmax(MParams<T> p) {
@@ -1142,6 +902,39 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
+}
+
+bool host_consts(lcq_dtype dtype, lcq_bound_type bound, double eb, uint64_t bits[4]) {
+    if (dtype == LCQ_F32) {
+        Consts<float> c{};
+        const bool ok = bound == LCQ_REL ? rel_consts_host<float>(eb, c) : abs_consts_host<float>(eb, c);
+        bits[0] = bits_host(c.ebT); bits[1] = bits_host(c.scale); bits[2] = bits_host(c.inv); bits[3] = bits_host(c.chk);
+        return ok;
+    }
+    Consts<double> c{};
+    const bool ok = bound == LCQ_REL ? rel_consts_host<double>(eb, c) : abs_consts_host<double>(eb, c);
+    bits[0] = bits_host(c.ebT); bits[1] = bits_host(c.scale); bits[2] = bits_host(c.inv); bits[3] = bits_host(c.chk);
+    return ok;
+}
+
+lcq_status check_quantize_args(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* d_in,
+                               uint64_t n, const int32_t* d_bins, const uint32_t* d_mask,
+                               const void* d_outliers, uint64_t outlier_capacity, const lcq_header* d_hdr) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (bound_type != LCQ_ABS && bound_type != LCQ_REL && bound_type != LCQ_NOA) return LCQ_ERR_ARG;
+    if (!d_hdr || !aligned16(d_hdr)) return LCQ_ERR_ARG;
+    if (n > 0 && (!d_in || !d_bins || !d_mask)) return LCQ_ERR_ARG;
+    if (n > 0 && (!aligned16(d_in) || !aligned16(d_bins) || !aligned16(d_mask))) return LCQ_ERR_ARG;
+    if (outlier_capacity > 0 && (!d_outliers || !aligned16(d_outliers))) return LCQ_ERR_ARG;
+    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return LCQ_ERR_BOUND;
+    return LCQ_OK;
+}
+
+int device_sm_count() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return device_sms(dev);
 }
 
 }  // namespace lcq

@@ -1,0 +1,281 @@
+// lcq_tile.cuh -- per-tile building blocks shared by the single-array and the
+// batched streaming kernels: vector access, the 4-value quantize of one ring
+// stage ("sub-tile") into bins and shared-memory mask words, the warp scan of
+// a scan tile's mask words, and the outlier writer.
+#pragma once
+
+#include <cstdint>
+
+#include "lcq_device.cuh"
+
+namespace lcq {
+
+constexpr int kComputeThreads = 256;               // 8 compute warps
+constexpr int kSpecThreads = kComputeThreads + 32;  // + 1 scan warp
+constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
+// Shared-memory position of mask word w of a scan tile: the low 5 bits are
+// XOR-ed with the row (w / 32), so that the scan warp's lanes, which read 16
+// or 32 consecutive words each, hit 32 different banks.
+__device__ __forceinline__ int sw(int w) { return w ^ ((w >> 5) & 31); }
+
+// ---------------------------------------------------------------------------
+// Vector access helpers: 4 consecutive values per thread per step.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Vec4;
+
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void load(const float* p, float v[4]) {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void load_shared(const float* p, float v[4]) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void load_cached(const float* p, float v[4]) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+    static __device__ __forceinline__ void store(float* p, const float v[4]) {
+        __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    }
+};
+
+template <>
+struct Vec4<double> {
+    static __device__ __forceinline__ void load(const double* p, double v[4]) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+        const double2 b = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void load_shared(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void load_cached(const double* p, double v[4]) {
+        const double2 a = reinterpret_cast<const double2*>(p)[0];
+        const double2 b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+    static __device__ __forceinline__ void store(double* p, const double v[4]) {
+        __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+        __stcs(reinterpret_cast<double2*>(p) + 1, make_double2(v[2], v[3]));
+    }
+};
+
+template <typename T, int VPT>
+__device__ __forceinline__ void load4(const T* sbuf_tile, const T* gin, bool from_smem, int off,
+                                      uint64_t e0, uint64_t n, T x[4]) {
+    if (from_smem) {
+        Vec4<T>::load_shared(sbuf_tile + off, x);
+    } else if (e0 + 4 <= n) {
+        Vec4<T>::load(gin + e0, x);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++) x[k] = (e0 + k < n) ? gin[e0 + k] : T(0);
+    }
+}
+
+// Mask words of one tile -> global, 16-byte stores where the tile is whole.
+template <int WPL>
+__device__ __forceinline__ void store_mask_words(uint32_t* gmask, uint64_t gw, uint64_t nwords,
+                                                 const uint32_t* wv) {
+#pragma unroll
+    for (int j = 0; j < WPL; j += 4) {
+        if (gw + j + 4 <= nwords) {
+            __stcs(reinterpret_cast<uint4*>(gmask + gw + j), make_uint4(wv[j], wv[j + 1], wv[j + 2], wv[j + 3]));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (gw + j + i < nwords) gmask[gw + j + i] = wv[j + i];
+        }
+    }
+}
+
+// Warp 0: exclusive prefix popcounts of the tile's mask words into s_wpre;
+// returns the tile's outlier count.  Also stores the words to global memory.
+template <int WPL>
+__device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uint32_t* s_wpre,
+                                                    uint32_t* gmask, uint64_t gw, uint64_t nwords,
+                                                    bool store) {
+    const int lane = threadIdx.x & 31;
+    uint32_t wv[WPL], loc[WPL], cnt = 0;
+#pragma unroll
+    for (int j = 0; j < WPL; j++) {
+        wv[j] = s_words[sw(lane * WPL + j)];
+        loc[j] = cnt;
+        cnt += __popc(wv[j]);
+    }
+    if (store) store_mask_words<WPL>(gmask, gw, nwords, wv);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t ex = incl - cnt;
+#pragma unroll
+    for (int j = 0; j < WPL; j++) s_wpre[sw(lane * WPL + j)] = ex + loc[j];
+    return __shfl_sync(0xFFFFFFFFu, incl, 31);
+}
+
+// Quantize one sub-tile of kComputeThreads x 4 x VPT values: from the
+// shared-memory stage st (from_smem, a whole sub-tile) or else from global
+// memory gin (a ragged or empty sub-tile with nvalid valid values).  Bins go
+// to gbins (the sub-tile's first bin); the sub-tile's mask words go to
+// s_words[sw(word_base + i)].  Called by the kComputeThreads compute threads.
+template <typename T, int MODE, int VPT>
+__device__ __forceinline__ void quantize_subtile(const T* st, const T* gin, bool from_smem,
+                                                 uint64_t nvalid, int32_t* gbins, uint32_t* s_words,
+                                                 int word_base, const Consts<T>& c) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wbase = word_base + warp * 4 + (lane >> 3);
+    // 4-value outlier nibbles of 8 lanes -> one mask word
+    auto put_word = [&](int v, uint32_t nb) {
+        uint32_t w = nb << ((lane & 7) * 4);
+        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 1);
+        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 2);
+        w |= __shfl_xor_sync(0xFFFFFFFFu, w, 4);
+        if ((lane & 7) == 0) s_words[sw(wbase + v * (kComputeThreads / 8))] = w;
+    };
+    if (from_smem && !c.all_outliers) {
+        // fast path: a whole sub-tile in shared memory, no bounds checks
+#pragma unroll
+        for (int v = 0; v < VPT; v++) {
+            const int off = v * (kComputeThreads * 4) + tid * 4;
+            T x[4];
+            Vec4<T>::load_shared(st + off, x);
+            int32_t bn[4];
+            const uint32_t nb = quant4<T, MODE>(x, c, bn);
+            __stcs(reinterpret_cast<int4*>(gbins + off), make_int4(bn[0], bn[1], bn[2], bn[3]));
+            put_word(v, nb);
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < VPT; v++) {
+            const int off = v * (kComputeThreads * 4) + tid * 4;
+            const uint64_t e0 = (uint64_t)off;
+            T x[4];
+            load4<T, VPT>(st, gin, from_smem, off, e0, nvalid, x);
+            int32_t bn[4];
+            uint32_t nb = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                int32_t bin = 0;
+                bool ok = false;
+                if (!c.all_outliers)
+                    ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
+                if (!ok && e0 + q < nvalid) nb |= 1u << q;
+                bn[q] = ok ? bin : 0;
+            }
+            if (e0 + 4 <= nvalid) {
+                __stcs(reinterpret_cast<int4*>(gbins + e0), make_int4(bn[0], bn[1], bn[2], bn[3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (e0 + q < nvalid) gbins[e0 + q] = bn[q];
+            }
+            put_word(v, nb);
+        }
+    }
+}
+
+// Outliers of one scan tile of `words` mask words: the raw bits of input
+// value w*32+bit (read again from global memory; the tile was read moments
+// ago, so this hits L2) go to out[pbase + rank], ranks in index order.
+// Called by the kComputeThreads compute threads.
+template <typename T>
+__device__ __forceinline__ void write_outliers(const uint32_t* s_words, const uint32_t* s_wpre, int words,
+                                               const T* gin, uint64_t pbase,
+                                               typename Ty<T>::U* out, uint64_t cap) {
+    for (int w = threadIdx.x; w < words; w += kComputeThreads) {
+        uint32_t mw = s_words[sw(w)];
+        if (!mw) continue;
+        const uint32_t pre = s_wpre[sw(w)];
+        uint32_t below = 0;
+        while (mw) {
+            const int bit = __ffs(mw) - 1;
+            mw &= mw - 1u;
+            const uint64_t rank = pbase + pre + below++;
+            if (rank < cap) out[rank] = Ty<T>::bits(gin[(uint64_t)w * 32 + bit]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// NOA range (Sec. 2.1.3): finite values as order-preserving integer keys, and
+// the bound derived from the range on the device.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ typename Ty<T>::U order_key(typename Ty<T>::U u) {
+    using U = typename Ty<T>::U;
+    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
+    return (u & sign) ? ~u : (u | sign);
+}
+template <typename T>
+__device__ __forceinline__ typename Ty<T>::U key_to_bits(typename Ty<T>::U k) {
+    using U = typename Ty<T>::U;
+    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
+    return (k & sign) ? (k & ~sign) : ~k;
+}
+
+template <typename T>
+__device__ __forceinline__ void minmax_accum(T x, typename Ty<T>::U& lo, typename Ty<T>::U& hi) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const U u = F::bits(x);
+    if (((u >> F::kP) & F::kExpAll) == F::kExpAll) return;  // Inf / NaN
+    const U k = order_key<T>(u);
+    lo = k < lo ? k : lo;
+    hi = k > hi ? k : hi;
+}
+
+template <typename T>
+__device__ __forceinline__ void noa_finalize(lcq_header* h, bool any, T mn, T mx, double eb) {
+    using F = Ty<T>;
+    uint32_t mode = 1;
+    double R = 0.0, eb_abs = 0.0;
+    uint64_t ebT_b = 0, eb2_b = 0, inv_b = 0;
+    if (any) {
+        R = __dsub_rd((double)mx, (double)mn);
+        eb_abs = __dmul_rd(eb, R);
+        if (sizeof(T) == 4) {
+            const float ebT = __double2float_rd(eb_abs);
+            const float eb2 = __fmul_rn(2.0f, ebT);
+            const float inv = __fdiv_rn(1.0f, eb2);
+            const bool ok = (ebT >= FLT_MIN && ebT <= FLT_MAX) && (eb2 <= FLT_MAX) &&
+                            (inv >= FLT_MIN && inv <= FLT_MAX);
+            if (ok) {
+                mode = 0;
+                ebT_b = __float_as_uint(ebT);
+                eb2_b = __float_as_uint(eb2);
+                inv_b = __float_as_uint(inv);
+            }
+        } else {
+            const double ebT = eb_abs;
+            const double eb2 = __dmul_rn(2.0, ebT);
+            const double inv = __ddiv_rn(1.0, eb2);
+            const bool ok = (ebT >= DBL_MIN && ebT <= DBL_MAX) && (eb2 <= DBL_MAX) &&
+                            (inv >= DBL_MIN && inv <= DBL_MAX);
+            if (ok) {
+                mode = 0;
+                ebT_b = (uint64_t)__double_as_longlong(ebT);
+                eb2_b = (uint64_t)__double_as_longlong(eb2);
+                inv_b = (uint64_t)__double_as_longlong(inv);
+            }
+        }
+    }
+    h->mode = mode;
+    h->range = R;
+    h->eb_abs = eb_abs;
+    h->ebT_bits = ebT_b;
+    h->scale_bits = eb2_b;
+    h->inv_bits = inv_b;
+    h->chk_bits = 0;
+}
+
+}  // namespace lcq

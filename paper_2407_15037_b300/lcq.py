@@ -39,6 +39,25 @@ class Header(ctypes.Structure):
 HEADER_BYTES = ctypes.sizeof(Header)
 
 
+class BatchItem(ctypes.Structure):
+    """Mirror of struct lcq_batch_item."""
+    _fields_ = [
+        ("dtype", ctypes.c_uint32), ("bound_type", ctypes.c_uint32), ("eb", ctypes.c_double),
+        ("n", ctypes.c_uint64), ("d_in", ctypes.c_void_p), ("d_bins", ctypes.c_void_p),
+        ("d_mask", ctypes.c_void_p), ("d_outliers", ctypes.c_void_p),
+        ("outlier_capacity", ctypes.c_uint64), ("d_hdr", ctypes.c_void_p),
+    ]
+
+
+class BatchInfo(ctypes.Structure):
+    """Mirror of struct lcq_batch_info."""
+    _fields_ = [
+        ("count", ctypes.c_uint32), ("noa_count", ctypes.c_uint32), ("total_tiles", ctypes.c_uint64),
+        ("noa_chunks", ctypes.c_uint64), ("total_values", ctypes.c_uint64),
+        ("total_bytes_in", ctypes.c_uint64), ("bad_item", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+    ]
+
+
 class LcqError(RuntimeError):
     def __init__(self, code, what):
         super().__init__("%s failed: %s" % (what, STATUS_NAMES.get(code, str(code))))
@@ -69,6 +88,14 @@ SIGNATURES = {
                                _vp, _sz, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "lcq_autotune_dequantize": ([ctypes.c_int, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp,
                                  ctypes.c_int, _vp], ctypes.c_int),
+    "lcq_batch_plan_size": ([_u32], _sz),
+    "lcq_batch_workspace_size": ([_vp, _u32], _sz),
+    "lcq_batch_prepare": ([_vp, _u32, _vp, _sz, _vp, _sz, _vp, _vp], ctypes.c_int),
+    "lcq_quantize_batched": ([_vp, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_batch_tune_variant_count": ([], ctypes.c_int),
+    "lcq_batch_tune_set": ([ctypes.c_int], ctypes.c_int),
+    "lcq_batch_tune_get": ([], ctypes.c_int),
+    "lcq_autotune_batched": ([_vp, _vp, _vp, _sz, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "lcq_noalloc_max_values": ([], _u64),
     "lcq_quantize_noalloc": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
                               _vp], ctypes.c_int),
@@ -267,6 +294,60 @@ def autotune_dequantize(q, out, ws, reps=5, stream=None):
         _ptr(out), _ptr(ws), ws.numel(), _stream_ptr(stream, out.device), int(reps), ms)
     _check(code, "lcq_autotune_dequantize")
     return list(ms)
+
+
+class Batch:
+    """A prepared batch: the plan and workspace on the device plus the host
+    info; keeps the input and output tensors alive.  `run()` enqueues
+    lcq_quantize_batched (capturable in a CUDA graph)."""
+
+    def __init__(self, arrays, device, stream=None):
+        # arrays: list of (x, bound, eb, Quantized)
+        self.arrays = arrays
+        self.device = torch.device(device)
+        n = len(arrays)
+        items = (BatchItem * n)()
+        for i, (x, bound, eb, q) in enumerate(arrays):
+            _require_cuda(x)
+            items[i] = BatchItem(_dtype_code(x), _bound_code(bound), float(eb), x.numel(), _ptr(x).value,
+                                 _ptr(q.bins).value, _ptr(q.mask).value, _ptr(q.outliers).value,
+                                 q.outliers.numel(), _ptr(q.header).value)
+        self.items = items
+        L = lib()
+        self.plan = torch.empty(int(L.lcq_batch_plan_size(n)), dtype=torch.uint8, device=self.device)
+        self.ws = torch.empty(int(L.lcq_batch_workspace_size(items, n)), dtype=torch.uint8,
+                              device=self.device)
+        self.info = BatchInfo()
+        code = L.lcq_batch_prepare(items, n, _ptr(self.plan), self.plan.numel(), _ptr(self.ws),
+                                   self.ws.numel(), ctypes.byref(self.info),
+                                   _stream_ptr(stream, self.device))
+        if code != 0:
+            raise LcqError(code, "lcq_batch_prepare (item %d)" % self.info.bad_item)
+
+    def run(self, stream=None):
+        code = lib().lcq_quantize_batched(ctypes.byref(self.info), _ptr(self.plan), _ptr(self.ws),
+                                          self.ws.numel(), _stream_ptr(stream, self.device))
+        _check(code, "lcq_quantize_batched")
+
+    def autotune(self, reps=3, stream=None):
+        nv = int(lib().lcq_batch_tune_variant_count())
+        ms = (ctypes.c_float * nv)()
+        code = lib().lcq_autotune_batched(ctypes.byref(self.info), _ptr(self.plan), _ptr(self.ws),
+                                          self.ws.numel(), _stream_ptr(stream, self.device), int(reps), ms)
+        _check(code, "lcq_autotune_batched")
+        return list(ms)
+
+
+def batch_variant_count():
+    return int(lib().lcq_batch_tune_variant_count())
+
+
+def set_batch_variant(v):
+    _check(lib().lcq_batch_tune_set(int(v)), "lcq_batch_tune_set")
+
+
+def get_batch_variant():
+    return int(lib().lcq_batch_tune_get())
 
 
 def debug_set_scan(spin_limit=0, drop_tile=(1 << 64) - 1):

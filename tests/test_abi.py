@@ -50,16 +50,20 @@ def test_binding_covers_the_declarations():
 def test_header_struct_size_matches_c(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include "lcq.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu\\n", sizeof(lcq_header),'
-                   ' offsetof(lcq_header, outlier_count), offsetof(lcq_header, status));return 0;}\n')
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lcq_header),'
+                   ' offsetof(lcq_header, outlier_count), offsetof(lcq_header, status),'
+                   ' sizeof(lcq_batch_item), sizeof(lcq_batch_info), offsetof(lcq_batch_item, d_hdr));'
+                   'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
                     str(src), "-o", str(exe)], check=True)
-    size, off_cnt, off_st = map(int, subprocess.run([str(exe)], capture_output=True, text=True,
-                                                    check=True).stdout.split())
+    size, off_cnt, off_st, bi, binfo, off_hdr = map(int, subprocess.run(
+        [str(exe)], capture_output=True, text=True, check=True).stdout.split())
     H = P.Header
     assert size == ctypes.sizeof(H)
     assert off_cnt == H.outlier_count.offset and off_st == H.status.offset
+    assert bi == ctypes.sizeof(P.BatchItem) and binfo == ctypes.sizeof(P.BatchInfo)
+    assert off_hdr == P.BatchItem.d_hdr.offset
 
 
 def test_host_side_argument_errors_need_no_gpu(lib):
