@@ -408,9 +408,12 @@ def run_batched(P, synth, dev, stream, args):
     t_gen = time.perf_counter() - t0
     batch = P.Batch(items, dev, stream)
     ms_var = batch.autotune(reps=2, stream=stream)
+    cs = torch.cuda.Stream(dev)  # graphs are captured on a side stream
+    cs.wait_stream(stream)
     g = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(g, stream=stream):
-        batch.run(stream=stream)
+    with torch.cuda.graph(g, stream=cs):
+        batch.run(stream=cs)
+    stream.wait_stream(cs)
     g.replay()
     torch.cuda.synchronize(dev)
     reps = 3
