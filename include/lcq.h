@@ -229,6 +229,72 @@ lcq_status lcq_autotune_batched(const lcq_batch_info* h_info, const void* d_plan
                                 size_t ws_bytes, cudaStream_t stream, int reps, float* h_ms);
 
 /*
+ * Hierarchical-grid predictor of quantization bins (no counterpart in the
+ * paper, which keeps the bins and leaves decorrelation to later lossless
+ * stages).  The error guarantee is untouched: prediction works on the exact
+ * integer bins produced and verified by lcq_quantize, and reconstruction
+ * gives back exactly those bins.
+ *   Grid: N^3 int32 bins, index (i*N + j)*N + k, 1 <= N <= 2048.  Anchors
+ *   (coordinates multiples of 8) are kept; a point of stride s = 4, 2, 1
+ *   (level 1, 2, 3: multiples of s, not all multiples of 2s) is predicted from
+ *   bins of coarser levels: interpolation over the 2^c coarse corners along
+ *   its c odd axes, (sum + 2^(c-1)) >> c, coarse positions clamped to the
+ *   last multiple of 2s below N; with a network, plus the int8 correction
+ *     x_t = clamp((stencil bin t - base) >> s_in[level-1], -128, 127) (3x3x3
+ *           coarse stencil around the point rounded down to the coarse grid),
+ *     h_u = clamp((W1 x + b1 + 2^(s1-1)) >> s1, 0, 127),
+ *     o   = (W2 h + b2 + 2^(s2-1)) >> s2,
+ *   one weight set per (level, class of odd axes).  Residual = bin - pred
+ *   modulo 2^32 (anchors: the bin).
+ * lcq_pred_residuals   bins -> residuals (d_params NULL: interpolation only).
+ * lcq_pred_reconstruct residuals -> bins, level by level (exact inverse).
+ * lcq_pred_histogram   counts of residual values in [-2^20, 2^20):
+ *   d_hist[lcq_pred_histogram_words()] = anchors' counts at value + 2^20, then
+ *   predicted points' counts at 2^21 + value + 2^20; values outside the range
+ *   are counted in d_over[0] (anchors) / d_over[1]; points whose bit is set
+ *   in d_mask (the quantizer's outlier mask; may be NULL) are skipped.
+ * Training (straight-through quantisation-aware, all on the device):
+ *   shadow parameters float[lcq_train_param_count()] = 21 networks x 465
+ *   (w1[16][27], b1[16], w2[16], b2 in integer units).  lcq_train_gradients
+ *   takes samples (uint64 (field << 32) | point index into the fields of
+ *   d_bins laid back to back), grouped by network and cut into items of at
+ *   most 256 samples (struct {uint32 net, start, count, pad}; d_item_begin
+ *   [22]: first item of each network); it writes per-item partial sums to
+ *   d_partial[num_items * 466], then d_grad[21 * 465] (gradient of the mean
+ *   squared residual of each network, summed in item order: deterministic)
+ *   and d_loss[21] (sum of squared residuals).  lcq_train_adam applies one
+ *   Adam step (Kingma & Ba) with bias corrections for `step` >= 1.
+ *   lcq_pred_freeze rounds and clamps the shadow parameters into an
+ *   lcq_pred_params block (synchronises the stream).
+ */
+typedef struct lcq_pred_params {
+    int8_t w1[3][7][16][28]; /* [level-1][class-1][hidden][input]; input 27 is padding, 0 */
+    int32_t b1[3][7][16];
+    int8_t w2[3][7][16];
+    int32_t b2[3][7];
+    int32_t s_in[3];
+    int32_t s1, s2;
+    int32_t reserved;
+} lcq_pred_params;
+
+lcq_status lcq_pred_residuals(const int32_t* d_bins, uint32_t N, const lcq_pred_params* d_params,
+                              int32_t* d_res, cudaStream_t stream);
+lcq_status lcq_pred_reconstruct(const int32_t* d_res, uint32_t N, const lcq_pred_params* d_params,
+                                int32_t* d_bins, cudaStream_t stream);
+size_t lcq_pred_histogram_words(void);
+lcq_status lcq_pred_histogram(const int32_t* d_res, uint32_t N, const uint32_t* d_mask, uint32_t* d_hist,
+                              unsigned long long* d_over, cudaStream_t stream);
+uint32_t lcq_train_param_count(void);
+lcq_status lcq_train_gradients(const int32_t* d_bins, uint32_t N, const uint64_t* d_samples, const void* d_items,
+                               uint32_t num_items, const uint32_t* d_item_begin, const float* d_shadow,
+                               const float* d_inv_count, const int32_t* h_s_in, int32_t s1, int32_t s2,
+                               float* d_partial, float* d_grad, float* d_loss, cudaStream_t stream);
+lcq_status lcq_train_adam(float* d_shadow, float* d_m, float* d_v, const float* d_grad, float lr, float beta1,
+                          float beta2, float eps, uint32_t step, cudaStream_t stream);
+lcq_status lcq_pred_freeze(const float* d_shadow, const int32_t* h_s_in, int32_t s1, int32_t s2,
+                           lcq_pred_params* d_params, cudaStream_t stream);
+
+/*
  * Tile-shape tuning (no counterpart in the paper; it only affects speed, never
  * results).  The streaming kernels come in lcq_tune_variant_count() tile
  * shapes ("variants"): lcq_tune_describe gives a variant's 4-value vectors per

@@ -43,8 +43,10 @@ def test_library_exports_every_declared_function(lib):
 
 
 def test_binding_covers_the_declarations():
-    assert set(P.lcq.SIGNATURES) | set(getattr(P, "EXTRA_SIGNATURES", {})) >= \
-        {n for n in _declared_functions() if n in P.lcq.SIGNATURES}
+    from paper_2407_15037_b300 import predictor as PD
+    bound = set(P.lcq.SIGNATURES) | set(PD.SIGNATURES)
+    missing = sorted(_declared_functions() - bound)
+    assert not missing, missing
 
 
 def test_header_struct_size_matches_c(tmp_path):
@@ -53,12 +55,15 @@ def test_header_struct_size_matches_c(tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lcq_header),'
                    ' offsetof(lcq_header, outlier_count), offsetof(lcq_header, status),'
                    ' sizeof(lcq_batch_item), sizeof(lcq_batch_info), offsetof(lcq_batch_item, d_hdr));'
+                   'printf("%zu\\n", sizeof(lcq_pred_params));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
                     str(src), "-o", str(exe)], check=True)
-    size, off_cnt, off_st, bi, binfo, off_hdr = map(int, subprocess.run(
+    size, off_cnt, off_st, bi, binfo, off_hdr, pp = map(int, subprocess.run(
         [str(exe)], capture_output=True, text=True, check=True).stdout.split())
+    from paper_2407_15037_b300 import predictor as PD
+    assert pp == PD.PARAMS_BYTES
     H = P.Header
     assert size == ctypes.sizeof(H)
     assert off_cnt == H.outlier_count.offset and off_st == H.status.offset
