@@ -282,6 +282,7 @@ def run_ours(args, world, rank, local):
 
     # ---- other configurations of the same path (timed per call) ----
     extra = {}
+    pred_res = None
 
     def time_calls(xx, bound, eb, reps=5):
         qq = P.alloc_outputs(xx.numel(), xx.dtype, dev)
@@ -313,6 +314,8 @@ def run_ours(args, world, rank, local):
         del x64
         if args.batched:
             extra["batched_4096"] = run_batched(P, synth, dev, stream, args)
+        if args.predictor:
+            pred_res = run_predictor(P, synth, dev, args)
         xs = synth.rel_stress(1 << 28, seed=0, device=dev)
         for eb in (1e-3, 1e-6):
             extra["rel_stress_2^28_%g" % eb] = time_calls(xs, "rel", eb)
@@ -383,6 +386,9 @@ def run_ours(args, world, rank, local):
                                         "hbm_GBps": n * 8.125 / t_deq / 1e9},
             "other_configs": extra,
             "autotune": tuning,
+            "bits_per_value_learned": pred_res["bits_per_value_learned"] if pred_res else None,
+            "bits_per_value_interp": pred_res["bits_per_value_interp"] if pred_res else None,
+            "predictor": pred_res,
         }
         print(json.dumps(line), flush=True)
 
@@ -439,6 +445,69 @@ def run_batched(P, synth, dev, stream, args):
     return res
 
 
+def run_predictor(P, synth, dev, args):
+    """Learned vs interpolation residual entropy: 64 training and 16 test
+    float32 256^3 Gaussian random fields with power spectrum k^-3, quantized
+    with ABS 1e-3 by the CUDA quantizer; 21 int8 networks trained on the
+    device (QAT, Adam) on the training bins; bits/value on the test bins."""
+    from paper_2407_15037_b300 import predictor as PD
+    N = 256
+    t0 = time.perf_counter()
+
+    def field_bins(seed):
+        q = P.quantize(synth.grf(N, seed=seed, device=dev), "abs", 1e-3)
+        return q
+
+    train = torch.cat([field_bins(s).bins for s in range(args.pred_train_fields)])
+    test = [field_bins(1000 + s) for s in range(args.pred_test_fields)]
+    torch.cuda.synchronize(dev)
+    t_data = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    s_in = PD.choose_s_in(train[:N ** 3].cpu().numpy(), N, rng)
+    tr = PD.Trainer(train, N, samples_per_net=args.pred_samples, seed=1, s_in=s_in)
+    tr.step()
+    mse0 = tr.mean_squared_residual()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.pred_steps - 1):
+        tr.step()
+    b.record()
+    torch.cuda.synchronize(dev)
+    t_step = a.elapsed_time(b) / max(1, args.pred_steps - 1)
+    mse1 = tr.mean_squared_residual()
+    params = tr.freeze()
+    bi, bl, per = [], [], []
+    for q in test:
+        r0 = PD.residuals(q.bins, N)
+        r1 = PD.residuals(q.bins, N, params)
+        x0, d0 = PD.bits_per_value(r0, N, q.mask)
+        x1, d1 = PD.bits_per_value(r1, N, q.mask)
+        assert torch.equal(PD.reconstruct(r1, N, params), q.bins)
+        bi.append(x0)
+        bl.append(x1)
+        per.append({"interp_pred_bits": d0["pred_bits"], "learned_pred_bits": d1["pred_bits"]})
+    # residual kernels' throughput on one test field (bins in, residuals out)
+    q = test[0]
+    times = {}
+    for name, prm in (("interp", None), ("learned", params)):
+        PD.residuals(q.bins, N, prm)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            PD.residuals(q.bins, N, prm)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        t = e0.elapsed_time(e1) / 5 / 1e3
+        times[name] = {"ms": t * 1e3, "GBps_bins_in_res_out": 8 * N ** 3 / t / 1e9}
+    return {"workload": "%d train + %d test float32 %d^3 GRF fields, power k^-3, ABS 1e-3" % (
+                args.pred_train_fields, args.pred_test_fields, N),
+            "bits_per_value_interp": float(np.mean(bi)), "bits_per_value_learned": float(np.mean(bl)),
+            "gain_bits_per_value": float(np.mean(bi) - np.mean(bl)), "per_field": per[:4],
+            "s_in": [int(v) for v in s_in], "train_steps": args.pred_steps,
+            "samples_per_step": int(tr.samples.numel()), "train_ms_per_step": t_step,
+            "train_mse_first": mse0, "train_mse_last": mse1, "data_s": t_data, "residual_kernels": times}
+
+
 def run_profile(args):
     """A short, fixed sequence of calls for ncu captures: three warm-up calls
     and one measured call of the chosen kind on the 512^3 float32 field."""
@@ -475,6 +544,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-predictor", dest="predictor", action="store_false")
+    ap.add_argument("--pred-train-fields", type=int, default=64)
+    ap.add_argument("--pred-test-fields", type=int, default=16)
+    ap.add_argument("--pred-steps", type=int, default=300)
+    ap.add_argument("--pred-samples", type=int, default=65536)
     args = ap.parse_args()
     if args.profile:
         run_profile(args)
