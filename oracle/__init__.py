@@ -189,6 +189,35 @@ def verify_rel(x, xr, eps):
     return int(lib().lcqo_verify_rel(_dtype_code(x), _ptr(x), _ptr(xr), x.size, float(eps)))
 
 
+def _verify_parallel(fn, x, xr, eb, threads=None):
+    x, xr = np.ascontiguousarray(x), np.ascontiguousarray(xr)
+    threads = threads or os.cpu_count() or 1
+    step = max(1, (x.size + threads - 1) // threads)
+    res = [0] * threads
+
+    def run(k):
+        s = k * step
+        e = min(x.size, s + step)
+        res[k] = fn(x[s:e], xr[s:e], eb) if e > s else 0
+
+    ts = [threading.Thread(target=run, args=(k,)) for k in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    return sum(res)
+
+
+def verify_abs_parallel(x, xr, eb, threads=None):
+    """verify_abs over contiguous slices on host threads (same count)."""
+    return _verify_parallel(verify_abs, x, xr, eb, threads)
+
+
+def verify_rel_parallel(x, xr, eps, threads=None):
+    """verify_rel over contiguous slices on host threads (same count)."""
+    return _verify_parallel(verify_rel, x, xr, eps, threads)
+
+
 def log2approx_f32(a):
     return lib().lcqo_log2approx_f32(float(a))
 

@@ -48,7 +48,7 @@ def test_all_patterns_chunked(bound):
         assert cnt == h.outlier_count
         # the decoded chunk stays within the bound (exact verifier)
         xr = P.dequantize(q, ws=ws).cpu().numpy()
-        bad = O.verify_rel(xh, xr, eb) if bound == "rel" else O.verify_abs(xh, xr, eb)
+        bad = O.verify_rel_parallel(xh, xr, eb) if bound == "rel" else O.verify_abs_parallel(xh, xr, eb)
         assert bad == 0
 
 
@@ -73,4 +73,4 @@ def test_all_patterns_noa_single_call():
     torch.cuda.synchronize()
     for start in range(0, FULL, CH):
         xh = _patterns(start, CH).cpu().numpy()
-        assert O.verify_abs(xh, xr[start:start + CH].cpu().numpy(), c.eb_abs) == 0
+        assert O.verify_abs_parallel(xh, xr[start:start + CH].cpu().numpy(), c.eb_abs) == 0
