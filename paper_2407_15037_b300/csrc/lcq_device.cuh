@@ -364,6 +364,168 @@ __device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Const
     return nb;
 }
 
+// ---------------------------------------------------------------------------
+// float64 with few FP64 operations.  The FP64 pipe of this GPU issues only a
+// few operations per clock per SM, so the float64 recipes keep just their
+// multiplications (and, for REL, one addition) on it and do the rest exactly
+// on the bit patterns with integer operations:
+//   * |v| < 2^w and |a| <= |b| as integer comparisons of the (sign-cleared)
+//     bit patterns: for non-negative IEEE doubles, including +Inf and NaN
+//     patterns, numeric order is the order of the bits;
+//   * rint of a double with |q| < 2^30 from its fields, round half to even;
+//   * an integer below 2^53 converted to the double with its exact value;
+//   * log2approx's single addition (1.M + (E - 1024)): the exact sum is the
+//     fixed-point number ((E - 1023) 2^52 + M) 2^-52, rounded to 53 bits with
+//     round-half-even in integer arithmetic (the same rounding as the FP add);
+//   * pow2approx of bb in [1, 2047): floor and fraction read off bb's fields;
+//   * the exact difference of two positive doubles within a factor 2 of each
+//     other (an integer subtraction of aligned significands, always exact).
+// Every helper returns exactly what the double operation(s) it replaces
+// return; the float64 parity tests run both against the oracle.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kD_MANT = 0x000FFFFFFFFFFFFFull;
+constexpr uint64_t kD_SIGN = 0x8000000000000000ull;
+
+__device__ __forceinline__ uint64_t dbits(double v) { return (uint64_t)__double_as_longlong(v); }
+__device__ __forceinline__ double dfrom(uint64_t u) { return __longlong_as_double((long long)u); }
+
+// rint(q) for a double q with |q| < 2^30 (caller checks), round half to even.
+__device__ __forceinline__ int32_t rint_d_small(uint64_t u) {
+    const int e = (int)((u >> 52) & 0x7FF);
+    const int sh = 1075 - e;  // q = m 2^-sh, m = 1.M 2^52
+    if (sh > 53) return 0;    // |q| < 1/2 (or zero / denormal)
+    const uint64_t m = (u & kD_MANT) | (1ull << 52);
+    const uint64_t ip = m >> sh;
+    const uint64_t rem = m & ((1ull << sh) - 1);
+    const uint64_t half = 1ull << (sh - 1);
+    const uint64_t r = ip + ((rem > half || (rem == half && (ip & 1))) ? 1 : 0);
+    return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
+}
+
+// The double with the exact value of integer i, |i| < 2^53.
+__device__ __forceinline__ uint64_t int_to_dbits(int64_t i) {
+    if (i == 0) return 0;
+    const uint64_t sgn = i < 0 ? kD_SIGN : 0;
+    const uint64_t a = (uint64_t)(i < 0 ? -i : i);
+    const int top = 63 - __clzll((long long)a);
+    return sgn | ((uint64_t)(top + 1023) << 52) | ((a << (52 - top)) & kD_MANT);
+}
+
+// RN to a double of the signed fixed-point value T 2^-52, |T| < 2^62.
+__device__ __forceinline__ uint64_t fixed52_to_dbits(int64_t T) {
+    if (T == 0) return 0;
+    const uint64_t sgn = T < 0 ? kD_SIGN : 0;
+    uint64_t a = (uint64_t)(T < 0 ? -T : T);
+    int top = 63 - __clzll((long long)a);
+    uint64_t mant;
+    if (top <= 52) {
+        mant = a << (52 - top);
+    } else {
+        const int sh = top - 52;
+        mant = a >> sh;
+        const uint64_t rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1))) {
+            mant++;
+            if (mant >> 53) {  // rounding carried into a new binade
+                mant >>= 1;
+                top++;
+            }
+        }
+    }
+    return sgn | ((uint64_t)(top - 52 + 1023) << 52) | (mant & kD_MANT);
+}
+
+// log2approx of a positive normal double with bits u (Sec. 3.2), exactly.
+__device__ __forceinline__ uint64_t log2approx_dbits(uint64_t u) {
+    const int64_t E = (int64_t)((u >> 52) & 0x7FF);
+    return fixed52_to_dbits(((E - 1023) << 52) + (int64_t)(u & kD_MANT));
+}
+
+// pow2approx bits of bb in [1, 2047) (caller checks): 2^(k-1023)(1 + bb - k).
+__device__ __forceinline__ uint64_t pow2approx_dbits(uint64_t ub) {
+    int e = (int)((ub >> 52) & 0x7FF) - 1023;  // 0..10 for a valid bb
+    e = e < 0 ? 0 : (e > 10 ? 10 : e);          // garbage in, garbage out, no undefined shift
+    const uint64_t m = ub & kD_MANT;
+    const uint64_t k = (1ull << e) + (m >> (52 - e));
+    return (k << 52) | ((m << e) & kD_MANT);
+}
+
+// Exact |a - b| for positive normal doubles with a/2 <= b <= 2a; returns bits.
+__device__ __forceinline__ uint64_t absdiff_close_dbits(uint64_t ua, uint64_t ub) {
+    if (ua < ub) { const uint64_t t = ua; ua = ub; ub = t; }  // ua >= ub
+    const int ea = (int)(ua >> 52), eb = (int)(ub >> 52);     // eb = ea or ea - 1
+    const uint64_t ma = (ua & kD_MANT) | (1ull << 52), mb = (ub & kD_MANT) | (1ull << 52);
+    const uint64_t D = (ma << (ea - eb)) - mb;                // in units of 2^(eb - 1075)
+    if (D == 0) return 0;
+    const int top = 63 - __clzll((long long)D);               // D < 2^54; the result is exact
+    const int e = eb + top - 52;                              // biased exponent of the difference
+    if (e >= 1) return ((uint64_t)e << 52) | ((D << (52 - top)) & kD_MANT);
+    return D << (eb - 1 > 0 ? eb - 1 : 0);                   // subnormal result: units of 2^-1074
+}
+
+__device__ __forceinline__ bool abs_quant_f64(double x, const Consts<double>& c, int32_t& bin) {
+    const double q = __dmul_rn(x, c.inv);
+    const uint64_t uq = dbits(q) & ~kD_SIGN;
+    if (!(uq < 0x41D0000000000000ull)) return false;  // !(|q| < 2^30): also NaN
+    const int32_t b = rint_d_small(dbits(q));
+    if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
+    const double recon = __dmul_rn(dfrom(int_to_dbits(b)), c.scale);
+    const uint64_t ud = dbits(__dsub_rn(x, recon)) & ~kD_SIGN;
+    if (!(ud <= dbits(c.ebT))) return false;          // !(|x - recon| <= eb_T): also NaN
+    bin = b;
+    return true;
+}
+
+__device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c, int32_t& bin) {
+    const uint64_t u = dbits(x);
+    const uint64_t E = (u >> 52) & 0x7FF;
+    if (E == 0 || E == 0x7FF) return false;  // zero, denormal, Inf, NaN
+    const uint64_t ua = u & ~kD_SIGN;
+    const double q = __dmul_rn(dfrom(log2approx_dbits(u)), c.inv);
+    const uint64_t uq = dbits(q) & ~kD_SIGN;
+    if (!(uq < 0x41C0000000000000ull)) return false;  // !(|q| < 2^29)
+    const int32_t b = rint_d_small(dbits(q));
+    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
+    const double Lr = __dmul_rn(dfrom(int_to_dbits(b)), c.scale);
+    const double bb = __dadd_rn(Lr, 1023.0);
+    const uint64_t ubb = dbits(bb);
+    if (!(ubb >= 0x3FF0000000000000ull && ubb < 0x409FFC0000000000ull)) return false;  // 1 <= bb < 2047
+    const uint64_t um = pow2approx_dbits(ubb);
+    // m/2 <= a <= 2m: doubling adds one to the exponent field (an overflow gives +Inf's bits)
+    if (!(ua <= um + (1ull << 52) && um <= ua + (1ull << 52))) return false;
+    const uint64_t ud = absdiff_close_dbits(ua, um);
+    const uint64_t ulo = ua < um ? ua : um;
+    bool ok;
+    if (ulo < 0x2000000000000000ull) {  // lo < 2^-511: exact rescale by 2^512 (rare)
+        const double sc = 0x1p512;
+        const double t = __dmul_rn(__dmul_rn(dfrom(ulo), sc), c.chk);
+        ok = (t >= DBL_MIN) && (__dmul_rn(dfrom(ud), sc) <= t);
+    } else {
+        const uint64_t ut = dbits(__dmul_rn(dfrom(ulo), c.chk));
+        ok = (ut >= 0x0010000000000000ull) && (ud <= ut);  // t normal, d <= t
+    }
+    if (!ok) return false;
+    bin = (int32_t)(((uint32_t)b << 1) | (uint32_t)(u >> 63));
+    return true;
+}
+
+__device__ __forceinline__ double abs_recon_f64(int32_t bin, const Consts<double>& c) {
+    return __dmul_rn(dfrom(int_to_dbits(bin)), c.scale);
+}
+
+__device__ __forceinline__ double rel_recon_f64(int32_t bin, const Consts<double>& c) {
+    const int32_t b = bin >> 1;
+    const double bb = __dadd_rn(__dmul_rn(dfrom(int_to_dbits(b)), c.scale), 1023.0);
+    return dfrom(pow2approx_dbits(dbits(bb)) | ((uint64_t)(bin & 1) << 63));
+}
+
+// One value: the float32 recipes above, or the float64 ones with few FP64 ops.
+template <typename T, int MODE>
+__device__ __forceinline__ bool quant1(T x, const Consts<T>& c, int32_t& bin) {
+    if constexpr (sizeof(T) == 8) return MODE == LCQ_REL ? rel_quant_f64(x, c, bin) : abs_quant_f64(x, c, bin);
+    else return MODE == LCQ_REL ? rel_quant<T>(x, c, bin) : abs_quant<T>(x, c, bin);
+}
+
 template <typename T, int MODE>
 __device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<T>& c, int32_t b[4]) {
     if constexpr (sizeof(T) == 4) {
@@ -373,7 +535,7 @@ __device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<T>& c, int
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             int32_t bin = 0;
-            const bool ok = (MODE == LCQ_REL) ? rel_quant<T>(x[k], c, bin) : abs_quant<T>(x[k], c, bin);
+            const bool ok = (MODE == LCQ_REL) ? rel_quant_f64(x[k], c, bin) : abs_quant_f64(x[k], c, bin);
             b[k] = ok ? bin : 0;
             nb |= ok ? 0u : (1u << k);
         }
@@ -390,6 +552,13 @@ __device__ __forceinline__ T rel_recon(int32_t bin, const Consts<T>& c) {
     const T Lr = F::mul(Cv<T>::from_int(b), c.scale);
     const T bb = F::add(Lr, F::bias_f());
     return F::from_bits(pow2approx_bits<T>(bb) | (s << (sizeof(U) * 8 - 1)));
+}
+
+// Reconstruction of one value, as the decoder computes it.
+template <typename T>
+__device__ __forceinline__ T recon1(bool rel, int32_t bin, const Consts<T>& c) {
+    if constexpr (sizeof(T) == 8) return rel ? rel_recon_f64(bin, c) : abs_recon_f64(bin, c);
+    else return rel ? rel_recon<T>(bin, c) : abs_recon<T>(bin, c);
 }
 
 // ---------------------------------------------------------------------------

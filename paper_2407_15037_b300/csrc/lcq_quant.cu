@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
                     T x[4];
 #pragma unroll
                     for (int q = 0; q < 4; q++)
-                        x[q] = ((nb >> q) & 1u) ? T(0) : (rel ? rel_recon<T>(bn[q], c) : abs_recon<T>(bn[q], c));
+                        x[q] = ((nb >> q) & 1u) ? T(0) : recon1<T>(rel, bn[q], c);
                     Vec4<T>::store(go + off, x);
                 }
             } else
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
                 T x[4];
 #pragma unroll
                 for (int q = 0; q < 4; q++)
-                    x[q] = ((nb >> q) & 1u) ? T(0) : (rel ? rel_recon<T>(bn[q], c) : abs_recon<T>(bn[q], c));
+                    x[q] = ((nb >> q) & 1u) ? T(0) : recon1<T>(rel, bn[q], c);
                 if (e0 + 4 <= p.n) {
                     Vec4<T>::store(p.out + e0, x);
                 } else {

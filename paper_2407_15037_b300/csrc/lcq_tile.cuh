@@ -167,8 +167,7 @@ __device__ __forceinline__ void quantize_subtile(const T* st, const T* gin, bool
             for (int q = 0; q < 4; q++) {
                 int32_t bin = 0;
                 bool ok = false;
-                if (!c.all_outliers)
-                    ok = (MODE == LCQ_REL) ? rel_quant<T>(x[q], c, bin) : abs_quant<T>(x[q], c, bin);
+                if (!c.all_outliers) ok = quant1<T, MODE>(x[q], c, bin);
                 if (!ok && e0 + q < nvalid) nb |= 1u << q;
                 bn[q] = ok ? bin : 0;
             }

@@ -196,6 +196,32 @@ def test_every_tile_shape_variant_matches_oracle(dtype):
         P.lcq.set_variant(1, dc, "abs", saved[3])
 
 
+def _f64_edge_values(rng, eb):
+    eb2 = 2 * eb
+    k = rng.integers(-(1 << 29), 1 << 29, 20000).astype(np.float64)
+    edges = (k + 0.5) * eb2
+    ulp = np.spacing(np.abs(edges))
+    vals = [edges, edges + ulp, edges - ulp, edges + 2 * ulp, -edges]
+    p2 = np.ldexp(1.0, rng.integers(-1022, 1023, 20000))
+    vals += [p2, np.nextafter(p2, 0), np.nextafter(p2, np.inf), -p2]
+    tiny = np.ldexp(1.0 + rng.random(20000), rng.integers(-1022, -500, 20000))  # around the 2^-511 rescale
+    vals += [tiny, np.nextafter(np.ldexp(1.0, -1022), 0) * rng.random(2000)]    # and below the normals
+    return np.concatenate(vals)
+
+
+@pytest.mark.parametrize("bound", BOUNDS)
+@pytest.mark.parametrize("eb", [1e-3, 1e-7])
+def test_f64_random_bit_patterns_and_edges(bound, eb):
+    """float64 over every exponent: random 64-bit patterns, a band of moderate
+    magnitudes, and structured edges; the float64 recipes work on the bit
+    patterns, so this exercises every branch of them."""
+    rng = np.random.default_rng(int(-np.log10(eb)) * 7 + len(bound))
+    raw = rng.integers(0, np.iinfo(np.uint64).max, 1 << 21, dtype=np.uint64, endpoint=True).view(np.float64)
+    mod = rng.normal(0, 1, 1 << 21) * 10.0 ** rng.integers(-12, 12, 1 << 21)
+    x = np.concatenate([raw, mod, _f64_edge_values(rng, eb)])
+    compare(torch.from_numpy(x).to(DEV), bound, eb)
+
+
 # --------------------------------------------------------- full sizes ----
 
 @pytest.mark.parametrize("bound", BOUNDS)
