@@ -142,6 +142,33 @@ lcq_status lcq_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
                           void* d_out, uint32_t* d_status, void* d_ws, size_t ws_bytes,
                           cudaStream_t stream);
 
+/*
+ * Sharded arrays (Sec. 2.1.3 over the union of contiguous shards held by
+ * several ranks).  ABS and REL need no exchange: each shard quantizes alone
+ * and the outlier payloads concatenate in rank order.  NOA needs the global
+ * finite range before binning:
+ *   lcq_finite_range   writes {has_finite (0 or 1), min, max} of the finite
+ *       values of d_in to d_range (3 doubles, device, 8-byte aligned; min and
+ *       max are exact: values of dtype).  {0, 0, 0} when no value is finite.
+ *       Needs a workspace of lcq_workspace_size(dtype, LCQ_NOA, n) bytes.
+ *   lcq_quantize_noa_range   lcq_quantize with LCQ_NOA, but R = RD(max - min)
+ *       is taken from the caller's range (the combination over all shards:
+ *       has_finite = OR, min = MIN, max = MAX) instead of from d_in.  With
+ *       has_finite = 0 every value becomes an outlier, as for an input with
+ *       no finite value.  Errors: LCQ_ERR_ARG if has_finite is not 0/1, or if
+ *       it is 1 and min/max are not finite, min > max, or (LCQ_F32) min/max
+ *       are not float values; the other errors as lcq_quantize.
+ * Every shard then holds exactly the bins, mask words and outliers that the
+ * unsharded call gives for its index range when shard boundaries are
+ * multiples of 32 values; its header differs only in n and outlier_count.
+ */
+lcq_status lcq_finite_range(lcq_dtype dtype, const void* d_in, uint64_t n, double* d_range, void* d_ws,
+                            size_t ws_bytes, cudaStream_t stream);
+lcq_status lcq_quantize_noa_range(lcq_dtype dtype, double eb, int has_finite, double range_min,
+                                  double range_max, const void* d_in, uint64_t n, int32_t* d_bins,
+                                  uint32_t* d_mask, void* d_outliers, uint64_t outlier_capacity,
+                                  lcq_header* d_hdr, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
 /* Synchronise `stream`, read d_hdr->status and map it to an lcq_status
  * (LCQ_ERR_TIMEOUT before LCQ_ERR_CAPACITY before LCQ_ERR_HEADER).
  * Optionally returns the outlier count.  This one does block the host. */

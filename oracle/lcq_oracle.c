@@ -44,7 +44,9 @@
  *  R6  NOA: min and max over FINITE values only; R = RD(max - min) and
  *      eb_abs = RD(eb * R), both in double with rounding toward -inf; then
  *      ABS with eb_abs.  No finite value, or derived constants that are not
- *      finite and normal, make every element an outlier (lossless).
+ *      finite and normal, make every element an outlier (lossless).  A zero
+ *      range is +0 (R is a length; x - x rounded toward -inf would give -0,
+ *      and which signed zero is min or max must not matter).
  *  R7  -0 and tiny ABS inputs quantize to bin 0 and decode as +0.
  *  R8  Outlier layout: mask bit (i & 31) of word (i >> 5); payload = raw bits
  *      of the outliers in ascending index order; bins of outliers are 0.
@@ -280,6 +282,7 @@ int lcqo_consts_noa_from_range(int dtype, double eb, int32_t any_finite, double 
     if (!user_bound_ok(eb)) return LCQO_BAD_BOUND;
     if (!any_finite) { c->all_outliers = 1; return LCQO_OK; }
     c->R = rd_sub_f64(mx, mn);
+    if (c->R == 0.0) c->R = 0.0; /* R6: a zero range is +0 */
     double eb_abs = rd_mul_f64(eb, c->R);
     if (!derive_abs(dtype, eb_abs, c)) {
         c->all_outliers = 1;

@@ -304,6 +304,7 @@ struct MParams {
     WsHead* ws;
     uint64_t* partial;  // 2 per block
     double eb;
+    double* range_out;  // non-null: write {any, min, max} here instead of the header
 };
 
 template <typename T>
@@ -372,9 +373,33 @@ __global__ void __launch_bounds__(kBlock) k_minmax(MParams<T> p) {
         const bool any = lo <= hi;
         const T mn = F::from_bits(key_to_bits<T>(lo));
         const T mx = F::from_bits(key_to_bits<T>(hi));
-        noa_finalize<T>(p.hdr, any, mn, mx, p.eb);
+        if (p.range_out) {
+            p.range_out[0] = any ? 1.0 : 0.0;
+            p.range_out[1] = any ? (double)mn : 0.0;
+            p.range_out[2] = any ? (double)mx : 0.0;
+        } else {
+            noa_finalize<T>(p.hdr, any, mn, mx, p.eb);
+        }
         atomicExch(&p.ws->done, 0u);
         __threadfence();
+    }
+}
+
+// NOA with a range the caller supplies (the global range of a sharded array,
+// Sec. 2.1.3 applied to the union of the shards): the same derivation as the
+// last block of k_minmax.  For an empty shard it also fills the header.
+template <typename T>
+__global__ void k_noa_given(lcq_header* h, bool any, T mn, T mx, double eb, uint32_t dtype, bool empty) {
+    noa_finalize<T>(h, any, mn, mx, eb);
+    if (empty) {
+        h->magic = LCQ_MAGIC;
+        h->dtype = dtype;
+        h->bound_type = LCQ_NOA;
+        h->n = 0;
+        h->eb = eb;
+        h->outlier_count = 0;
+        h->status = 0;
+        h->reserved = 0;
     }
 }
 
@@ -805,10 +830,12 @@ static uint64_t bits_host(T v) {
     return u;
 }
 
+// given: NOA only; null = derive the range from the input (k_minmax), else
+// {any, min, max} of the caller's range (already validated).
 template <typename T>
 static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint64_t n, int32_t* bins,
                                 uint32_t* mask, void* outl, uint64_t cap, lcq_header* hdr, void* ws,
-                                cudaStream_t st) {
+                                cudaStream_t st, const double* given = nullptr) {
     Consts<T> c{};
     const bool noa = bt == LCQ_NOA;
     if (bt == LCQ_ABS) {
@@ -822,8 +849,12 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     size_t dsz = (desc_bytes(n) + 255) & ~(size_t)255;
     uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz);
 
-    if (noa) {
-        MParams<T> mp{in, n, hdr, head, partial, eb};
+    if (noa && given) {
+        k_noa_given<T><<<1, 1, 0, st>>>(hdr, given[0] != 0.0, (T)given[1], (T)given[2], eb, dtype, n == 0);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+        if (n == 0) return LCQ_OK;
+    } else if (noa) {
+        MParams<T> mp{in, n, hdr, head, partial, eb, nullptr};
         uint64_t blocks = (n / 4 + kBlock - 1) / kBlock;
         if (blocks < 1) blocks = 1;
         if (blocks > (uint64_t)kMinmaxMaxBlocks) blocks = kMinmaxMaxBlocks;
@@ -990,6 +1021,54 @@ lcq_status lcq_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
                                       d_ws, stream);
     return dequantize_impl<double>(n, d_hdr, d_bins, d_mask, d_outliers, (double*)d_out, d_status,
                                    d_ws, stream);
+}
+
+lcq_status lcq_finite_range(lcq_dtype dtype, const void* d_in, uint64_t n, double* d_range, void* d_ws,
+                            size_t ws_bytes, cudaStream_t stream) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (!d_range || (reinterpret_cast<uintptr_t>(d_range) & 7) != 0) return LCQ_ERR_ARG;
+    if (!d_ws || !aligned16(d_ws)) return LCQ_ERR_ARG;
+    if (n > 0 && (!d_in || !aligned16(d_in))) return LCQ_ERR_ARG;
+    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
+    if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
+    WsHead* head = reinterpret_cast<WsHead*>(d_ws);
+    const size_t dsz = (desc_bytes(n) + 255) & ~(size_t)255;
+    uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(d_ws) + kWsHeadBytes + dsz);
+    uint64_t blocks = (n / 4 + kBlock - 1) / kBlock;
+    if (blocks < 1) blocks = 1;
+    if (blocks > (uint64_t)kMinmaxMaxBlocks) blocks = kMinmaxMaxBlocks;
+    if (dtype == LCQ_F32) {
+        MParams<float> mp{(const float*)d_in, n, nullptr, head, partial, 0.0, d_range};
+        k_minmax<float><<<(unsigned)blocks, kBlock, 0, stream>>>(mp);
+    } else {
+        MParams<double> mp{(const double*)d_in, n, nullptr, head, partial, 0.0, d_range};
+        k_minmax<double><<<(unsigned)blocks, kBlock, 0, stream>>>(mp);
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
+}
+
+lcq_status lcq_quantize_noa_range(lcq_dtype dtype, double eb, int has_finite, double range_min,
+                                  double range_max, const void* d_in, uint64_t n, int32_t* d_bins,
+                                  uint32_t* d_mask, void* d_outliers, uint64_t outlier_capacity,
+                                  lcq_header* d_hdr, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    const lcq_status a = check_quantize_args(dtype, LCQ_NOA, eb, d_in, n, d_bins, d_mask, d_outliers,
+                                             outlier_capacity, d_hdr);
+    if (a != LCQ_OK) return a;
+    if (!d_ws || !aligned16(d_ws)) return LCQ_ERR_ARG;
+    if (has_finite != 0 && has_finite != 1) return LCQ_ERR_ARG;
+    if (has_finite) {
+        if (!std::isfinite(range_min) || !std::isfinite(range_max) || !(range_min <= range_max))
+            return LCQ_ERR_ARG;
+        if (dtype == LCQ_F32 && ((double)(float)range_min != range_min || (double)(float)range_max != range_max))
+            return LCQ_ERR_ARG;
+    }
+    if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
+    const double given[3] = {has_finite ? 1.0 : 0.0, has_finite ? range_min : 0.0, has_finite ? range_max : 0.0};
+    if (dtype == LCQ_F32)
+        return quantize_impl<float>(LCQ_NOA, eb, (const float*)d_in, n, d_bins, d_mask, d_outliers,
+                                    outlier_capacity, d_hdr, d_ws, stream, given);
+    return quantize_impl<double>(LCQ_NOA, eb, (const double*)d_in, n, d_bins, d_mask, d_outliers,
+                                 outlier_capacity, d_hdr, d_ws, stream, given);
 }
 
 lcq_status lcq_sync_status(const lcq_header* d_hdr, uint64_t* h_outlier_count, cudaStream_t stream) {

@@ -241,6 +241,7 @@ __device__ __forceinline__ void noa_finalize(lcq_header* h, bool any, T mn, T mx
     uint64_t ebT_b = 0, eb2_b = 0, inv_b = 0;
     if (any) {
         R = __dsub_rd((double)mx, (double)mn);
+        if (R == 0.0) R = 0.0;  // a zero range is +0, whichever signed zeros min and max are
         eb_abs = __dmul_rd(eb, R);
         if (sizeof(T) == 4) {
             const float ebT = __double2float_rd(eb_abs);

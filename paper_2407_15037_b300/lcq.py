@@ -74,6 +74,9 @@ SIGNATURES = {
                       _sz, _vp], ctypes.c_int),
     "lcq_dequantize": ([ctypes.c_int, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp],
                        ctypes.c_int),
+    "lcq_finite_range": ([ctypes.c_int, _vp, _u64, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_quantize_noa_range": ([ctypes.c_int, _dbl, ctypes.c_int, _dbl, _dbl, _vp, _u64, _vp, _vp, _vp, _u64,
+                                _vp, _vp, _sz, _vp], ctypes.c_int),
     "lcq_sync_status": ([_vp, _vp, _vp], ctypes.c_int),
     "lcq_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "lcq_host_stage_size": ([ctypes.c_int, _u64, _u64], _sz),
@@ -222,6 +225,33 @@ def quantize_noalloc_into(x, bound, eb, q, stream=None):
         _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header),
         _stream_ptr(stream, x.device))
     _check(code, "lcq_quantize_noalloc")
+    return q
+
+
+def finite_range(x, ws=None, stream=None):
+    """Enqueue lcq_finite_range; returns a float64 device tensor
+    {has_finite, min, max} (no host synchronisation)."""
+    _require_cuda(x)
+    x = x.reshape(-1)
+    if ws is None:
+        ws = new_workspace(x.numel(), x.device, _dtype_code(x), NOA)
+    out = torch.empty(3, dtype=torch.float64, device=x.device)
+    code = lib().lcq_finite_range(_dtype_code(x), _ptr(x), x.numel(), _ptr(out), _ptr(ws), ws.numel(),
+                                  _stream_ptr(stream, x.device))
+    _check(code, "lcq_finite_range")
+    return out
+
+
+def quantize_noa_range_into(x, eb, rng, q, ws, stream=None):
+    """Enqueue lcq_quantize_noa_range: NOA with the caller's finite range
+    rng = (has_finite, min, max) (host values)."""
+    _require_cuda(x)
+    has, mn, mx = rng
+    code = lib().lcq_quantize_noa_range(
+        _dtype_code(x), float(eb), 1 if has else 0, float(mn) if has else 0.0, float(mx) if has else 0.0,
+        _ptr(x), x.numel(), _ptr(q.bins), _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header),
+        _ptr(ws), ws.numel(), _stream_ptr(stream, x.device))
+    _check(code, "lcq_quantize_noa_range")
     return q
 
 

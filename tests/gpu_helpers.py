@@ -40,7 +40,8 @@ def compare(x, bound, eb, q=None, capacity=None, check_decode=True, oq=None):
         assert np.array(h.scale_bits, dtype=np.uint64).astype(u).view(f) == f(scale)
         assert np.array(h.inv_bits, dtype=np.uint64).astype(u).view(f) == f(inv)
     if bound == "noa":
-        assert h.range == c.R and h.eb_abs == c.eb_abs
+        bits = lambda v: np.float64(v).tobytes()
+        assert bits(h.range) == bits(c.R) and bits(h.eb_abs) == bits(c.eb_abs)
     bins = q.bins.cpu().numpy()
     mismatch = np.flatnonzero(bins != oq.bins)
     assert mismatch.size == 0, "bins differ at %s" % mismatch[:10]

@@ -82,4 +82,16 @@ def test_host_side_argument_errors_need_no_gpu(lib):
     assert lib.lcq_quantize(0, 0, -1.0, None, 0, None, None, None, 0, h, p, 4000, None) == 2
     assert lib.lcq_quantize(0, 0, float("nan"), None, 0, None, None, None, 0, h, p, 4000, None) == 2
     assert lib.lcq_status_string(4) == b"outlier scan wait timed out"
+    # a caller-given NOA range: has_finite 0/1, finite, ordered, float values for float32
+    nr = lambda dt, has, lo, hi: lib.lcq_quantize_noa_range(dt, 1e-3, has, lo, hi, None, 0, None, None, None, 0,
+                                                            h, p, 4000, None)
+    assert nr(0, 2, 0.0, 1.0) == 1
+    assert nr(0, 1, 1.0, 0.0) == 1
+    assert nr(0, 1, float("-inf"), 0.0) == 1
+    assert nr(0, 1, 0.0, float("nan")) == 1
+    assert nr(0, 1, 0.0, 0.1) == 1          # 0.1 is not a float32 value
+    assert lib.lcq_quantize_noa_range(0, -1.0, 1, 0.0, 1.0, None, 0, None, None, None, 0, h, p, 4000, None) == 2
+    assert lib.lcq_finite_range(3, None, 0, p, p, 4000, None) == 1
+    assert lib.lcq_finite_range(0, None, 0, None, p, 4000, None) == 1
+    assert lib.lcq_finite_range(0, None, 0, ctypes.c_void_p(p.value + 4), p, 4000, None) == 1
     assert lib.lcq_workspace_size(0, 0, 1 << 31) > lib.lcq_workspace_size(0, 0, 1 << 20)

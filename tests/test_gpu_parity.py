@@ -89,6 +89,11 @@ def test_noa_degenerate_all_outliers():
     assert oq.count == 10000
     x = torch.full((5000,), float("nan"), device=DEV)
     compare(x, "noa", 1e-3)
+    # only signed zeros: a zero range is +0 in the header on both sides
+    x = torch.zeros(3000, device=DEV)
+    x[::3] = -0.0
+    compare(x, "noa", 1e-3)
+    compare(torch.full((70,), -0.0, dtype=torch.float64, device=DEV), "noa", 1e-3)
 
 
 def test_capacity_overflow_reports_and_stays_in_bounds():

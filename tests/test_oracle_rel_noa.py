@@ -186,3 +186,19 @@ def test_noa_tiny_range_f32_falls_back_to_lossless():
     x = np.array([1.0, np.nextafter(np.float32(1.0), np.float32(2.0))], dtype=np.float32)
     q = O.quantize(x, "noa", 1e-35)
     assert q.consts.all_outliers == 1 and q.count == 2
+
+
+@pytest.mark.parametrize("x", [
+    np.full(9, 3.25, dtype=np.float32),
+    np.array([-2.5, -2.5], dtype=np.float64),
+    np.array([-0.0, 0.0, -0.0], dtype=np.float32),
+    np.array([0.0, -0.0], dtype=np.float64),
+    np.array([np.nan, -0.0], dtype=np.float32),
+])
+def test_noa_zero_range_is_positive_zero(x):
+    # R is a length: every zero range is +0 (x - x rounded toward -inf would
+    # give -0), whatever signed zeros the data holds and in whatever order
+    c = O.consts("noa", x.dtype, 1e-3, x=x)
+    assert np.float64(c.R).tobytes() == np.float64(0.0).tobytes()
+    assert np.float64(c.eb_abs).tobytes() == np.float64(0.0).tobytes()
+    assert c.all_outliers == 1
