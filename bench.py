@@ -187,6 +187,67 @@ def run_reference(args, world, rank):
 
 # --------------------------------------------------------------- our arm --
 
+def run_ablations(P, x, q, ws, dev, stream, reps=5):
+    """The paper's two ablations on the float32 512^3 field: ABS without the
+    double-check (Sec. 6, Tables 7-8: time and exact bound violations) and REL
+    with the CUDA library's log2/exp2 (Sec. 2.3, Tables 4-6: time, outliers,
+    and how many of a sample of its values the host C library's exp2f decodes
+    differently).  Each ablation and its protected counterpart run the same
+    tile-shape variant."""
+    import ctypes
+    import ctypes.util
+    L = P.lcq
+    n = x.numel()
+
+    def timed(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    res = {}
+    qa = L.alloc_outputs(n, x.dtype, dev)
+    libm = ctypes.CDLL(ctypes.util.find_library("m"))
+    libm.exp2f.argtypes = [ctypes.c_float]
+    libm.exp2f.restype = ctypes.c_float
+    for kind, bound in (("abs_no_check", "abs"), ("rel_library", "rel")):
+        v = L.ablation_variant(P.F32, kind)
+        keep_v = L.get_variant(0, P.F32, bound)
+        L.set_variant(0, P.F32, bound, v)
+        for eb in (1e-3, 1e-5):
+            t_p = timed(lambda: P.quantize_into(x, bound, eb, q, ws, stream))
+            t_a = timed(lambda: L.quantize_ablation_into(x, kind, eb, qa, ws, stream))
+            hp, ha = q.read_header(), qa.read_header()
+            r = {"variant": v, "protected_ms": t_p, "ablation_ms": t_a,
+                 "protected_in_GBps": n * 4 / t_p / 1e6, "ablation_in_GBps": n * 4 / t_a / 1e6,
+                 "protected_outliers": int(hp.outlier_count), "ablation_outliers": int(ha.outlier_count)}
+            if kind == "abs_no_check":
+                r["ablation_bound_violations"] = L.count_abs_violations(x, P.dequantize(qa, ws), eb)
+                r["protected_bound_violations"] = L.count_abs_violations(x, P.dequantize(q, ws), eb)
+            else:
+                m_gpu = L.rel_library_reconstruct(qa)
+                idx = torch.nonzero(qa.bins != 0)[:65536, 0]   # accepted values (bin 0 is an outlier or 1.0)
+                bins = qa.bins[idx].cpu().numpy()
+                mg = m_gpu[idx].cpu().numpy()
+                step = np.array([ha.scale_bits], dtype=np.uint64).astype(np.uint32).view(np.float32)[0]
+                Lr = (bins >> 1).astype(np.float32) * np.float32(step)
+                mc = np.array([libm.exp2f(float(v_)) for v_ in Lr], dtype=np.float32)
+                mc = np.where(bins & 1, -mc, mc).astype(np.float32)
+                differ = mc.view(np.uint32) != mg.view(np.uint32)
+                r["host_exp2f_decode_sample"] = int(bins.size)
+                r["host_exp2f_decode_mismatches"] = int(differ.sum())
+                r["host_exp2f_max_ulp_diff"] = int(np.abs(mc.view(np.int32).astype(np.int64) -
+                                                          mg.view(np.int32).astype(np.int64)).max())
+            res["%s_%g" % (kind, eb)] = r
+        L.set_variant(0, P.F32, bound, keep_v)
+    del qa
+    return res
+
+
 def run_ours(args, world, rank, local):
     import paper_2407_15037_b300 as P
     import synth
@@ -303,6 +364,7 @@ def run_ours(args, world, rank, local):
                 "outliers": int(h.outlier_count)}
 
     if args.extras:
+        extra["ablations"] = run_ablations(P, x, q, ws, dev, stream)
         x64 = synth.smooth_field((256, 256, 256), dtype=torch.float64, seed=0, device=dev)
         q64 = P.alloc_outputs(x64.numel(), x64.dtype, dev)
         w64 = P.new_workspace(x64.numel(), dev)

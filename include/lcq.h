@@ -83,7 +83,8 @@ typedef struct lcq_header {
     uint32_t dtype;         /* lcq_dtype */
     uint32_t bound_type;    /* lcq_bound_type */
     uint32_t mode;          /* 0: quantized; 1: every value stored as an outlier
-                               (NOA without a usable range) */
+                               (NOA without a usable range); 2: the REL
+                               library ablation (see lcq_quantize_ablation) */
     uint64_t n;             /* number of values */
     double eb;              /* the bound passed by the caller */
     double range;           /* NOA: R = RD(max - min) over the finite values, else 0 */
@@ -168,6 +169,43 @@ lcq_status lcq_quantize_noa_range(lcq_dtype dtype, double eb, int has_finite, do
                                   double range_max, const void* d_in, uint64_t n, int32_t* d_bins,
                                   uint32_t* d_mask, void* d_outliers, uint64_t outlier_capacity,
                                   lcq_header* d_hdr, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * Ablations of the paper's experiments (not for production use).
+ *   LCQ_ABL_ABS_NO_CHECK  ABS without the reconstruct-and-check step: the
+ *       unprotected quantizer that Sec. 6 (Tables 7-8) measures against.  Bins
+ *       are rint(x / (2 eb_T)) wherever the range tests of Sec. 2.4 / 3.3
+ *       pass; NaN, Inf and out-of-range values are still outliers.  The header
+ *       is an ordinary ABS header, so lcq_dequantize decodes the result, which
+ *       may break the bound (lcq_count_abs_violations counts where).
+ *   LCQ_ABL_REL_LIBRARY   REL with the CUDA math library's log2 / exp2 in
+ *       place of the Sec. 3.2 approximations (the library variant of Sec. 2.3,
+ *       Tables 4-6), still checked on the device with exp2.  Its header has
+ *       mode 2; lcq_dequantize refuses it (LCQ_STATUS_HEADER) and only
+ *       lcq_rel_library_reconstruct (the same library) decodes it.
+ * lcq_quantize_ablation   as lcq_quantize; outputs in the same layout.
+ * lcq_ablation_variant    the tile-shape variant (see lcq_tune_*) the ablation
+ *       kernel runs, -1 for bad arguments; time the protected kernel on the same
+ *       variant for a like-for-like comparison.
+ * lcq_rel_library_reconstruct  d_out[i] = the library decode of bin i where
+ *       mask bit i is clear, 0 where it is set (outliers are not gathered).
+ *       A header that is not an LCQ_ABL_REL_LIBRARY header of n values of
+ *       dtype sets LCQ_STATUS_HEADER in *d_status (if not NULL), d_out untouched.
+ * lcq_count_abs_violations  *d_count (uint64, device, 8-byte aligned) = the
+ *       number of i with |x_i - xr_i| > eb in exact arithmetic; identical bit
+ *       patterns (NaN included) never count, any other non-finite pair does.
+ *       eb >= 0 (LCQ_ERR_BOUND otherwise).  Stream-ordered.
+ */
+typedef enum { LCQ_ABL_ABS_NO_CHECK = 0, LCQ_ABL_REL_LIBRARY = 1 } lcq_ablation;
+lcq_status lcq_quantize_ablation(lcq_ablation kind, lcq_dtype dtype, double eb, const void* d_in, uint64_t n,
+                                 int32_t* d_bins, uint32_t* d_mask, void* d_outliers, uint64_t outlier_capacity,
+                                 lcq_header* d_hdr, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+int lcq_ablation_variant(lcq_dtype dtype, lcq_ablation kind);
+lcq_status lcq_rel_library_reconstruct(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
+                                       const int32_t* d_bins, const uint32_t* d_mask, void* d_out,
+                                       uint32_t* d_status, cudaStream_t stream);
+lcq_status lcq_count_abs_violations(lcq_dtype dtype, double eb, const void* d_x, const void* d_xr, uint64_t n,
+                                    unsigned long long* d_count, cudaStream_t stream);
 
 /* Synchronise `stream`, read d_hdr->status and map it to an lcq_status
  * (LCQ_ERR_TIMEOUT before LCQ_ERR_CAPACITY before LCQ_ERR_HEADER).

@@ -72,6 +72,10 @@ def lib():
             L.lcqo_quantize.restype = u64
             L.lcqo_dequantize.argtypes = [P(Consts), vp, vp, vp, u64, vp]
             L.lcqo_dequantize.restype = None
+            L.lcqo_quantize_unprotected.argtypes = [P(Consts), vp, u64, vp, vp, vp, u64]
+            L.lcqo_quantize_unprotected.restype = u64
+            L.lcqo_rel_library_recon.argtypes = [ctypes.c_int, dbl, vp, vp, u64, vp]
+            L.lcqo_rel_library_recon.restype = None
             L.lcqo_verify_abs.argtypes = [ctypes.c_int, vp, vp, u64, dbl]
             L.lcqo_verify_abs.restype = u64
             L.lcqo_verify_rel.argtypes = [ctypes.c_int, vp, vp, u64, dbl]
@@ -173,6 +177,30 @@ def dequantize(q):
     out = np.empty(n, dtype=np.float32 if c.dtype == F32 else np.float64)
     lib().lcqo_dequantize(ctypes.byref(c), _ptr(q.bins), _ptr(q.mask), _ptr(q.payload), n,
                           _ptr(out))
+    return out
+
+
+def quantize_unprotected(x, eb):
+    """Ablation: ABS without the reconstruct-and-check step (Sec. 6, Tables
+    7-8); the result decodes with dequantize() like any ABS result."""
+    x = np.ascontiguousarray(x)
+    c = consts("abs", x.dtype, eb)
+    n = x.size
+    bins = np.empty(n, dtype=np.int32)
+    mask = np.empty((n + 31) // 32, dtype=np.uint32)
+    pay = np.empty(n, dtype=np.uint32 if c.dtype == F32 else np.uint64)
+    cnt = lib().lcqo_quantize_unprotected(ctypes.byref(c), _ptr(x), n, _ptr(bins), _ptr(mask), _ptr(pay), n)
+    return Quantized(bins, mask, pay[:cnt], int(cnt), c)
+
+
+def rel_library_recon(dtype, step, bins, mask):
+    """Ablation: decode REL bins with the host C library's exp2 (Sec. 2.3);
+    0 where the mask marks an outlier."""
+    bins = np.ascontiguousarray(bins, dtype=np.int32)
+    mask = np.ascontiguousarray(mask, dtype=np.uint32)
+    dt = np.dtype(dtype)
+    out = np.empty(bins.size, dtype=dt)
+    lib().lcqo_rel_library_recon(DTYPES[dt], float(step), _ptr(bins), _ptr(mask), bins.size, _ptr(out))
     return out
 
 

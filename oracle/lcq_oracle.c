@@ -463,6 +463,70 @@ void lcqo_dequantize(const lcqo_consts* c, const int32_t* bins, const uint32_t* 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Ablations (not the method; reference outputs for the ablation kernels).   */
+/* ------------------------------------------------------------------------ */
+
+/* The unprotected ABS quantizer that Sec. 6 (Tables 7-8) compares against:
+ * the bin of Sec. 2.2 with the range tests (R1, Sec. 3.3) but without the
+ * reconstruct-and-check of Sec. 3.1.  c must hold ABS constants. */
+static int abs_elem_unprotected(const lcqo_consts* c, const void* x, uint64_t i, int32_t* bin_out) {
+    int32_t bin;
+    if (c->dtype == LCQO_F32) {
+        float q = ((const float*)x)[i] * (float)c->inv;
+        if (!(fabsf(q) < (float)MAXBIN_ABS)) return 0;
+        bin = (int32_t)rintf(q);
+    } else {
+        double q = ((const double*)x)[i] * c->inv;
+        if (!(fabs(q) < (double)MAXBIN_ABS)) return 0;
+        bin = (int32_t)rint(q);
+    }
+    if ((bin >= MAXBIN_ABS) || (bin <= -MAXBIN_ABS)) return 0;
+    *bin_out = bin;
+    return 1;
+}
+
+uint64_t lcqo_quantize_unprotected(const lcqo_consts* c, const void* x, uint64_t n, int32_t* bins,
+                                   uint32_t* mask, void* payload, uint64_t cap) {
+    uint64_t words = (n + 31u) / 32u;
+    for (uint64_t w = 0; w < words; w++) mask[w] = 0u;
+    uint64_t count = 0;
+    for (uint64_t i = 0; i < n; i++) {
+        int32_t bin = 0;
+        if (abs_elem_unprotected(c, x, i, &bin)) {
+            bins[i] = bin;
+            continue;
+        }
+        bins[i] = 0;
+        mask[i >> 5] |= 1u << (i & 31u);
+        if (count < cap) {
+            if (c->dtype == LCQO_F32) ((uint32_t*)payload)[count] = ((const uint32_t*)x)[i];
+            else ((uint64_t*)payload)[count] = ((const uint64_t*)x)[i];
+        }
+        count++;
+    }
+    return count;
+}
+
+/* Decoder of the REL variant that uses the math library's exp2 (Sec. 2.3),
+ * with THIS host's C library: m = exp2(b * step) for the stored bin 2b + s,
+ * sign s.  Positions whose mask bit is set get 0 (outliers not gathered). */
+void lcqo_rel_library_recon(int dtype, double step, const int32_t* bins, const uint32_t* mask, uint64_t n,
+                            void* out) {
+    for (uint64_t i = 0; i < n; i++) {
+        int outlier = (mask[i >> 5] >> (i & 31u)) & 1u;
+        int32_t s = bins[i] & 1;
+        int32_t b = (bins[i] - s) / 2;
+        if (dtype == LCQO_F32) {
+            float m = outlier ? 0.0f : exp2f((float)b * (float)step);
+            ((float*)out)[i] = (s && !outlier) ? -m : m;
+        } else {
+            double m = outlier ? 0.0 : exp2((double)b * step);
+            ((double*)out)[i] = (s && !outlier) ? -m : m;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Exact verifiers of the bounds (Sec. 2.1) -- independent of the recipe.    */
 /* An element passes if its reconstruction is bit-identical to the input,    */
 /* or both are finite and the bound holds in exact real arithmetic.          */

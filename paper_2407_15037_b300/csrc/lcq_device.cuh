@@ -28,6 +28,15 @@ namespace lcq {
 constexpr int32_t kMaxBinAbs = 1 << 30;
 constexpr int32_t kMaxBinRel = 1 << 29;
 
+// Kernel modes besides LCQ_ABS (also used for NOA) and LCQ_REL: the two
+// ablations of the paper's experiments.  kModeAbsNoCheck is ABS without the
+// reconstruct-and-check step (the unprotected quantizer of Sec. 6, Tables 7
+// and 8); kModeRelLib is REL with the CUDA math library's log2 / exp2 in
+// place of the bit-level approximations (the library variant of Sec. 2.3 and
+// Tables 4-6), still double-checked on the device.
+constexpr int kModeAbsNoCheck = 3;
+constexpr int kModeRelLib = 4;
+
 // ---------------------------------------------------------------------------
 // Type traits: every arithmetic step is a single correctly rounded IEEE op.
 // ---------------------------------------------------------------------------
@@ -194,7 +203,8 @@ struct Cv<double> {
 
 // ABS / NOA: bin = rint(x * inv) (Sec. 2.2); reconstruct and check (Sec. 3.1);
 // two-sided range test (Sec. 3.3).  Returns false for an outlier.
-template <typename T>
+// CHECK = false drops the reconstruct-and-check step (the unprotected ablation).
+template <typename T, bool CHECK = true>
 __device__ __forceinline__ bool abs_quant(T x, const Consts<T>& c, int32_t& bin) {
     using F = Ty<T>;
     const T q = F::mul(x, c.inv);
@@ -204,8 +214,10 @@ __device__ __forceinline__ bool abs_quant(T x, const Consts<T>& c, int32_t& bin)
     Cv<T>::round(q, b, bf);  // b = rint(q), bf = (T)b
     // Sec. 3.3: (b >= maxbin) || (b <= -maxbin), as one unsigned comparison
     if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;
-    const T recon = F::mul(bf, c.scale);
-    if (!(F::fabs_(F::sub(x, recon)) <= c.ebT)) return false;
+    if constexpr (CHECK) {
+        const T recon = F::mul(bf, c.scale);
+        if (!(F::fabs_(F::sub(x, recon)) <= c.ebT)) return false;
+    }
     bin = b;
     return true;
 }
@@ -238,6 +250,24 @@ __device__ __forceinline__ typename Ty<T>::U pow2approx_bits(T bb) {
     return ((U)k << F::kP) | (F::bits(fr) & F::kMant);
 }
 
+// REL acceptance of a reconstruction m (normal, positive) of a = |x|:
+// m/2 <= a <= 2m, then |a - m| (exact by Sterbenz) <= RN(min(a, m) * chk),
+// that product normal; tiny values are rescaled by an exact power of two.
+template <typename T>
+__device__ __forceinline__ bool rel_accept(T a, T m, const Consts<T>& c) {
+    using F = Ty<T>;
+    if (!(a <= F::mul(T(2), m) && m <= F::mul(T(2), a))) return false;
+    const T d = F::fabs_(F::sub(a, m));  // exact (Sterbenz)
+    const T lo = (a < m) ? a : m;
+    if (lo < F::tiny()) {  // exact power-of-two rescale keeps t out of the subnormal range
+        const T sc = F::rescale();
+        const T t = F::mul(F::mul(lo, sc), c.chk);
+        return (t >= F::nmin()) && (F::mul(d, sc) <= t);
+    }
+    const T t = F::mul(lo, c.chk);  // scaling by 1 is exact, so it is left out
+    return (t >= F::nmin()) && (d <= t);
+}
+
 // REL: returns false for an outlier; the stored bin is 2b + signbit.
 template <typename T>
 __device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin) {
@@ -259,22 +289,56 @@ __device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin)
     const T bb = F::add(Lr, F::bias_f());
     if (!(bb >= T(1) && bb < F::top_bb())) return false;
     const T m = F::from_bits(pow2approx_bits<T>(bb));
-    if (!(a <= F::mul(T(2), m) && m <= F::mul(T(2), a))) return false;
-    const T d = F::fabs_(F::sub(a, m));  // exact (Sterbenz)
-    const T lo = (a < m) ? a : m;
-    T t;
-    bool ok;
-    if (lo < F::tiny()) {  // exact power-of-two rescale keeps t out of the subnormal range
-        const T sc = F::rescale();
-        t = F::mul(F::mul(lo, sc), c.chk);
-        ok = (t >= F::nmin()) && (F::mul(d, sc) <= t);
-    } else {  // scaling by 1 is exact, so it is left out
-        t = F::mul(lo, c.chk);
-        ok = (t >= F::nmin()) && (d <= t);
-    }
-    if (!ok) return false;
+    if (!rel_accept<T>(a, m, c)) return false;
     bin = (int32_t)(((uint32_t)b << 1) | (uint32_t)sign_bit);
     return true;
+}
+
+// REL with the math library's log2 / exp2 (ablation): the same bin rule and
+// the same acceptance test, with L = log2(a) and m = exp2(b step).  m must be
+// finite and normal.  The library results differ between devices and
+// libraries (Sec. 2.3), so only a decoder with the same library reproduces m.
+template <typename T>
+__device__ __forceinline__ T lib_log2(T a) {
+    if constexpr (sizeof(T) == 4) return log2f(a);
+    else return log2(a);
+}
+template <typename T>
+__device__ __forceinline__ T lib_exp2(T a) {
+    if constexpr (sizeof(T) == 4) return exp2f(a);
+    else return exp2(a);
+}
+
+template <typename T>
+__device__ __forceinline__ bool rel_quant_lib(T x, const Consts<T>& c, int32_t& bin) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const U u = F::bits(x);
+    const U E = (u >> F::kP) & F::kExpAll;
+    if (E == 0 || E == F::kExpAll) return false;  // zero, denormal, Inf, NaN
+    const U sign_bit = u >> (sizeof(U) * 8 - 1);
+    const T a = F::from_bits(u & ~((U)1 << (sizeof(U) * 8 - 1)));
+    const T q = F::mul(lib_log2<T>(a), c.inv);
+    if (!(F::fabs_(q) < T(kMaxBinRel))) return false;
+    int32_t b;
+    T bf;
+    Cv<T>::round(q, b, bf);
+    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
+    const T m = lib_exp2<T>(F::mul(bf, c.scale));
+    const U Em = (F::bits(m) >> F::kP) & F::kExpAll;
+    if (Em == 0 || Em == F::kExpAll) return false;  // m not finite and normal
+    if (!rel_accept<T>(a, m, c)) return false;
+    bin = (int32_t)(((uint32_t)b << 1) | (uint32_t)sign_bit);
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ T rel_recon_lib(int32_t bin, const Consts<T>& c) {
+    using F = Ty<T>;
+    using U = typename F::U;
+    const U s = (U)(bin & 1);
+    const T m = lib_exp2<T>(F::mul(Cv<T>::from_int(bin >> 1), c.scale));
+    return F::from_bits(F::bits(m) | (s << (sizeof(U) * 8 - 1)));
 }
 
 // ---------------------------------------------------------------------------
@@ -286,6 +350,7 @@ __device__ __forceinline__ bool rel_quant(T x, const Consts<T>& c, int32_t& bin)
 // leaves out are implied by |q| < 2^22 (no integer overflow, |b| <= 2^22 <
 // maxbin).  Returns the 4-bit outlier nibble; bins of outliers are 0.
 // ---------------------------------------------------------------------------
+template <bool CHECK = true>
 __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
     float q[4];
     bool small = true;
@@ -300,8 +365,11 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
         for (int k = 0; k < 4; k++) {
             const float t = __fadd_rn(q[k], 0x1.8p23f);
             const int32_t bi = __float_as_int(t) - 0x4B400000;
-            const float recon = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
-            const bool ok = fabsf(__fsub_rn(x[k], recon)) <= c.ebT;
+            bool ok = true;
+            if constexpr (CHECK) {
+                const float recon = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
+                ok = fabsf(__fsub_rn(x[k], recon)) <= c.ebT;
+            }
             b[k] = ok ? bi : 0;
             nb |= ok ? 0u : (1u << k);
         }
@@ -309,7 +377,7 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             int32_t bin = 0;
-            const bool ok = abs_quant<float>(x[k], c, bin);
+            const bool ok = abs_quant<float, CHECK>(x[k], c, bin);
             b[k] = ok ? bin : 0;
             nb |= ok ? 0u : (1u << k);
         }
@@ -463,15 +531,18 @@ __device__ __forceinline__ uint64_t absdiff_close_dbits(uint64_t ua, uint64_t ub
     return D << (eb - 1 > 0 ? eb - 1 : 0);                   // subnormal result: units of 2^-1074
 }
 
+template <bool CHECK = true>
 __device__ __forceinline__ bool abs_quant_f64(double x, const Consts<double>& c, int32_t& bin) {
     const double q = __dmul_rn(x, c.inv);
     const uint64_t uq = dbits(q) & ~kD_SIGN;
     if (!(uq < 0x41D0000000000000ull)) return false;  // !(|q| < 2^30): also NaN
     const int32_t b = rint_d_small(dbits(q));
     if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
-    const double recon = __dmul_rn(dfrom(int_to_dbits(b)), c.scale);
-    const uint64_t ud = dbits(__dsub_rn(x, recon)) & ~kD_SIGN;
-    if (!(ud <= dbits(c.ebT))) return false;          // !(|x - recon| <= eb_T): also NaN
+    if constexpr (CHECK) {
+        const double recon = __dmul_rn(dfrom(int_to_dbits(b)), c.scale);
+        const uint64_t ud = dbits(__dsub_rn(x, recon)) & ~kD_SIGN;
+        if (!(ud <= dbits(c.ebT))) return false;      // !(|x - recon| <= eb_T): also NaN
+    }
     bin = b;
     return true;
 }
@@ -522,20 +593,29 @@ __device__ __forceinline__ double rel_recon_f64(int32_t bin, const Consts<double
 // One value: the float32 recipes above, or the float64 ones with few FP64 ops.
 template <typename T, int MODE>
 __device__ __forceinline__ bool quant1(T x, const Consts<T>& c, int32_t& bin) {
-    if constexpr (sizeof(T) == 8) return MODE == LCQ_REL ? rel_quant_f64(x, c, bin) : abs_quant_f64(x, c, bin);
-    else return MODE == LCQ_REL ? rel_quant<T>(x, c, bin) : abs_quant<T>(x, c, bin);
+    if constexpr (MODE == kModeRelLib) {
+        return rel_quant_lib<T>(x, c, bin);
+    } else if constexpr (sizeof(T) == 8) {
+        if constexpr (MODE == LCQ_REL) return rel_quant_f64(x, c, bin);
+        else return abs_quant_f64<MODE != kModeAbsNoCheck>(x, c, bin);
+    } else {
+        if constexpr (MODE == LCQ_REL) return rel_quant<T>(x, c, bin);
+        else return abs_quant<T, MODE != kModeAbsNoCheck>(x, c, bin);
+    }
 }
 
 template <typename T, int MODE>
 __device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<T>& c, int32_t b[4]) {
-    if constexpr (sizeof(T) == 4) {
-        return MODE == LCQ_REL ? rel_quant4_f32(x, c, b) : abs_quant4_f32(x, c, b);
+    if constexpr (sizeof(T) == 4 && MODE == LCQ_REL) {
+        return rel_quant4_f32(x, c, b);
+    } else if constexpr (sizeof(T) == 4 && MODE != kModeRelLib) {
+        return abs_quant4_f32<MODE != kModeAbsNoCheck>(x, c, b);
     } else {
         uint32_t nb = 0;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             int32_t bin = 0;
-            const bool ok = (MODE == LCQ_REL) ? rel_quant_f64(x[k], c, bin) : abs_quant_f64(x[k], c, bin);
+            const bool ok = quant1<T, MODE>(x[k], c, bin);
             b[k] = ok ? bin : 0;
             nb |= ok ? 0u : (1u << k);
         }

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                     h->n = p.n_total;
                     h->eb = p.eb;
                     if (!p.consts_from_hdr) {
-                        h->mode = 0;
+                        h->mode = MODE == kModeRelLib ? 2u : 0u;
                         h->range = 0.0;
                         h->eb_abs = p.eb_abs;
                         h->ebT_bits = (uint64_t)F::bits(p.c.ebT);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
         s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.ws->carry);
         // decode only a complete, error-free encoding of exactly these arrays
         const bool ok = p.hdr->magic == LCQ_MAGIC && p.hdr->dtype == p.dtype &&
-                        p.hdr->n == p.n_total && p.hdr->status == 0u &&
+                        p.hdr->n == p.n_total && p.hdr->status == 0u && p.hdr->mode <= 1u &&
                         (p.outl != nullptr || p.hdr->outlier_count == 0);
         s_ok = ok;
         if (!ok) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
@@ -748,6 +748,19 @@ static cudaError_t launch_dequantize_variant(int v, const DParams<T>& p, cudaStr
     return cudaErrorInvalidValue;
 }
 
+// The ablation kernels run one fixed tile shape each: the default shape of
+// the protected kernel they are compared with.
+template <typename T, int MODE>
+constexpr int ablation_variant() {
+    return sizeof(T) == 4 ? (MODE == kModeRelLib ? 3 : 1) : 2;
+}
+
+template <typename T, int MODE>
+static cudaError_t launch_ablation(const QParams<T>& p, cudaStream_t st) {
+    constexpr Variant v = kVariants[ablation_variant<T, MODE>()];
+    return launch_quantize<T, MODE, v.vpt, v.stages, v.sub, v.minb>(p, st);
+}
+
 // Selected variant per kernel kind (0 quantize, 1 dequantize), dtype, bound type.
 // Defaults from autotuning on a B300 (float32 512^3 field, float64 256^3 field).
 static int g_variant[2][2][3] = {{{1, 3, 1}, {2, 2, 2}}, {{5, 5, 5}, {2, 2, 2}}};
@@ -835,7 +848,7 @@ static uint64_t bits_host(T v) {
 template <typename T>
 static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint64_t n, int32_t* bins,
                                 uint32_t* mask, void* outl, uint64_t cap, lcq_header* hdr, void* ws,
-                                cudaStream_t st, const double* given = nullptr) {
+                                cudaStream_t st, const double* given = nullptr, int ablation = 0) {
     Consts<T> c{};
     const bool noa = bt == LCQ_NOA;
     if (bt == LCQ_ABS) {
@@ -895,8 +908,11 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.eb_abs = eb_abs;
         p.n_total = n;
         const int var = g_variant[0][dtype][bt];
-        const cudaError_t e = bt == LCQ_REL ? launch_quantize_variant<T, LCQ_REL>(var, p, st)
-                                            : launch_quantize_variant<T, LCQ_ABS>(var, p, st);
+        cudaError_t e;
+        if (ablation == kModeAbsNoCheck) e = launch_ablation<T, kModeAbsNoCheck>(p, st);
+        else if (ablation == kModeRelLib) e = launch_ablation<T, kModeRelLib>(p, st);
+        else if (bt == LCQ_REL) e = launch_quantize_variant<T, LCQ_REL>(var, p, st);
+        else e = launch_quantize_variant<T, LCQ_ABS>(var, p, st);
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
@@ -1021,6 +1037,35 @@ lcq_status lcq_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header* d_hdr,
                                       d_ws, stream);
     return dequantize_impl<double>(n, d_hdr, d_bins, d_mask, d_outliers, (double*)d_out, d_status,
                                    d_ws, stream);
+}
+
+lcq_status lcq_quantize_ablation(lcq_ablation kind, lcq_dtype dtype, double eb, const void* d_in, uint64_t n,
+                                 int32_t* d_bins, uint32_t* d_mask, void* d_outliers, uint64_t outlier_capacity,
+                                 lcq_header* d_hdr, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (kind != LCQ_ABL_ABS_NO_CHECK && kind != LCQ_ABL_REL_LIBRARY) return LCQ_ERR_ARG;
+    const lcq_bound_type bt = kind == LCQ_ABL_REL_LIBRARY ? LCQ_REL : LCQ_ABS;
+    const lcq_status a = check_quantize_args(dtype, bt, eb, d_in, n, d_bins, d_mask, d_outliers,
+                                             outlier_capacity, d_hdr);
+    if (a != LCQ_OK) return a;
+    if (!d_ws || !aligned16(d_ws)) return LCQ_ERR_ARG;
+    if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
+    const int mode = kind == LCQ_ABL_REL_LIBRARY ? kModeRelLib : kModeAbsNoCheck;
+    if (dtype == LCQ_F32)
+        return quantize_impl<float>(bt, eb, (const float*)d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
+                                    d_hdr, d_ws, stream, nullptr, mode);
+    return quantize_impl<double>(bt, eb, (const double*)d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
+                                 d_hdr, d_ws, stream, nullptr, mode);
+}
+
+int lcq_ablation_variant(lcq_dtype dtype, lcq_ablation kind) {
+    if (kind != LCQ_ABL_ABS_NO_CHECK && kind != LCQ_ABL_REL_LIBRARY) return -1;
+    if (dtype == LCQ_F32)
+        return kind == LCQ_ABL_REL_LIBRARY ? ablation_variant<float, kModeRelLib>()
+                                           : ablation_variant<float, kModeAbsNoCheck>();
+    if (dtype == LCQ_F64)
+        return kind == LCQ_ABL_REL_LIBRARY ? ablation_variant<double, kModeRelLib>()
+                                           : ablation_variant<double, kModeAbsNoCheck>();
+    return -1;
 }
 
 lcq_status lcq_finite_range(lcq_dtype dtype, const void* d_in, uint64_t n, double* d_range, void* d_ws,

@@ -77,6 +77,11 @@ SIGNATURES = {
     "lcq_finite_range": ([ctypes.c_int, _vp, _u64, _vp, _vp, _sz, _vp], ctypes.c_int),
     "lcq_quantize_noa_range": ([ctypes.c_int, _dbl, ctypes.c_int, _dbl, _dbl, _vp, _u64, _vp, _vp, _vp, _u64,
                                 _vp, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_quantize_ablation": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp, _vp, _sz,
+                               _vp], ctypes.c_int),
+    "lcq_ablation_variant": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "lcq_rel_library_reconstruct": ([ctypes.c_int, _u64, _vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "lcq_count_abs_violations": ([ctypes.c_int, _dbl, _vp, _vp, _u64, _vp, _vp], ctypes.c_int),
     "lcq_sync_status": ([_vp, _vp, _vp], ctypes.c_int),
     "lcq_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "lcq_host_stage_size": ([ctypes.c_int, _u64, _u64], _sz),
@@ -253,6 +258,55 @@ def quantize_noa_range_into(x, eb, rng, q, ws, stream=None):
         _ptr(ws), ws.numel(), _stream_ptr(stream, x.device))
     _check(code, "lcq_quantize_noa_range")
     return q
+
+
+ABLATIONS = {"abs_no_check": 0, "rel_library": 1}
+
+
+def quantize_ablation_into(x, kind, eb, q, ws, stream=None):
+    """Enqueue lcq_quantize_ablation ('abs_no_check' | 'rel_library')."""
+    _require_cuda(x)
+    code = lib().lcq_quantize_ablation(
+        ABLATIONS[kind], _dtype_code(x), float(eb), _ptr(x), x.numel(), _ptr(q.bins), _ptr(q.mask),
+        _ptr(q.outliers), q.outliers.numel(), _ptr(q.header), _ptr(ws), ws.numel(), _stream_ptr(stream, x.device))
+    _check(code, "lcq_quantize_ablation")
+    return q
+
+
+def quantize_ablation(x, kind, eb, ws=None, stream=None):
+    _require_cuda(x)
+    x = x.contiguous().reshape(-1)
+    q = alloc_outputs(x.numel(), x.dtype, x.device)
+    if ws is None:
+        ws = new_workspace(x.numel(), x.device, _dtype_code(x))
+    return quantize_ablation_into(x, kind, eb, q, ws, stream)
+
+
+def ablation_variant(dtype_code, kind):
+    return int(lib().lcq_ablation_variant(dtype_code, ABLATIONS[kind]))
+
+
+def rel_library_reconstruct(q, out=None, stream=None, check=True):
+    """Library-exp2 decode of a 'rel_library' result (0 at outliers)."""
+    if out is None:
+        out = torch.empty(q.n, dtype=q.dtype, device=q.bins.device)
+    status = torch.zeros(1, dtype=torch.int32, device=out.device)
+    code = lib().lcq_rel_library_reconstruct(_dtype_code(out), q.n, _ptr(q.header), _ptr(q.bins), _ptr(q.mask),
+                                             _ptr(out), _ptr(status), _stream_ptr(stream, out.device))
+    _check(code, "lcq_rel_library_reconstruct")
+    if check and int(status.item()):
+        raise LcqError(7, "lcq_rel_library_reconstruct (device status %d)" % int(status.item()))
+    return out
+
+
+def count_abs_violations(x, xr, eb, stream=None):
+    """Number of i with |x_i - xr_i| > eb in exact arithmetic (synchronises)."""
+    _require_cuda(x)
+    cnt = torch.empty(1, dtype=torch.int64, device=x.device)
+    code = lib().lcq_count_abs_violations(_dtype_code(x), float(eb), _ptr(x), _ptr(xr), x.numel(), _ptr(cnt),
+                                          _stream_ptr(stream, x.device))
+    _check(code, "lcq_count_abs_violations")
+    return int(cnt.item())
 
 
 def dequantize_into(q, out, ws, status=None, stream=None):
