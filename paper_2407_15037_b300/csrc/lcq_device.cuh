@@ -385,49 +385,93 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
     return nb;
 }
 
+// The fast REL code for four values whose |q| < 2^22 (see rel_quant4_f32).
+// It computes exactly what rel_quant<float> computes, with fewer instructions:
+//  * pow2approx(bb) for 1 <= bb < 255: with k = floor(bb) and frac = bb - k,
+//    its bit pattern (k << 23) | frac 2^23 is the integer bb 2^23 (frac is a
+//    multiple of 2^-23 because bb >= 1), so one exact scaling by 2^23 and one
+//    exact conversion give it;
+//  * 1 <= bb < 255 is one unsigned comparison of bit patterns (bit patterns of
+//    non-negative floats are ordered like the floats; negative ones are huge);
+//  * RATIO = false leaves out the test m/2 <= a <= 2m, which the acceptance
+//    test implies when chk <= 1/2: if it fails, |a - m| > lo exactly, so
+//    d = RN(|a - m|) >= lo (lo is a float), while t = RN(lo chk) <= RN(lo / 2)
+//    < lo (the same holds after the exact rescale), so d <= t fails too;
+//  * the exact rescale for tiny values runs only in warps that have one;
+//  * in a warp without tiny values (every lo = min(a, m) >= 2^-62) and with
+//    RATIO = false, the special-value and bb-range tests are implied as well:
+//    a zero or denormal a, or bb < 1 (m = bb 2^23 converted is then below
+//    2^-126, or 0 for bb < 0), would make lo tiny; an Inf or NaN a makes d
+//    Inf or NaN; bb >= 255 makes m +Inf, a NaN, or a negative value (bit 31
+//    set: then t = RN(lo chk) <= 0 < FLT_MIN); each of these fails d <= t or
+//    t >= FLT_MIN.
+template <bool RATIO>
+__device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float q[4], const Consts<float>& c,
+                                                  int32_t b[4]) {
+    float a[4], m[4], lo[4], bb[4];
+    int32_t bin[4];
+    bool tiny = false;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t u = __float_as_uint(x[k]);
+        a[k] = __uint_as_float(u & 0x7FFFFFFFu);
+        const float t = __fadd_rn(q[k], 0x1.8p23f);
+        bin[k] = (int32_t)(((uint32_t)(__float_as_int(t) - 0x4B400000) << 1) | (u >> 31));
+        const float Lr = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
+        bb[k] = __fadd_rn(Lr, 127.0f);
+        m[k] = __uint_as_float(__float2uint_rz(__fmul_rn(bb[k], 0x1p23f)));
+        lo[k] = fminf(a[k], m[k]);
+        tiny |= lo[k] < 0x1p-62f;
+    }
+    uint32_t nb = 0;
+    if (!RATIO && !__any_sync(0xFFFFFFFFu, tiny)) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const float d = fabsf(__fsub_rn(a[k], m[k]));  // exact (Sterbenz) when accepted
+            const float tt = __fmul_rn(lo[k], c.chk);
+            const bool ok = (tt >= FLT_MIN) && (d <= tt);
+            b[k] = ok ? bin[k] : 0;
+            nb |= ok ? 0u : (1u << k);
+        }
+        return nb;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const uint32_t E = (__float_as_uint(x[k]) >> 23) & 0xFFu;
+        bool ok = (E - 1u < 254u) && (__float_as_uint(bb[k]) - 0x3F800000u < 0x437F0000u - 0x3F800000u);
+        if (RATIO) ok = ok && (a[k] <= __fmul_rn(2.0f, m[k])) && (m[k] <= __fmul_rn(2.0f, a[k]));
+        const float d = fabsf(__fsub_rn(a[k], m[k]));
+        if (lo[k] < 0x1p-62f) {  // exact power-of-two rescale
+            const float tt = __fmul_rn(__fmul_rn(lo[k], 0x1p64f), c.chk);
+            ok = ok && (tt >= FLT_MIN) && (__fmul_rn(d, 0x1p64f) <= tt);
+        } else {
+            const float tt = __fmul_rn(lo[k], c.chk);
+            ok = ok && (tt >= FLT_MIN) && (d <= tt);
+        }
+        b[k] = ok ? bin[k] : 0;
+        nb |= ok ? 0u : (1u << k);
+    }
+    return nb;
+}
+
 __device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
-    float q[4], L[4];
+    float q[4];
     bool small = true;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
-        L[k] = log2approx<float>(__float_as_uint(x[k]));  // finite for every bit pattern
-        q[k] = __fmul_rn(L[k], c.inv);
+        const float L = log2approx<float>(__float_as_uint(x[k]));  // finite for every bit pattern
+        q[k] = __fmul_rn(L, c.inv);
         small &= fabsf(q[k]) < 0x1p22f;
     }
+    if (__all_sync(0xFFFFFFFFu, small))
+        return c.chk <= 0.5f ? rel_fast4_f32<false>(x, q, c, b) : rel_fast4_f32<true>(x, q, c, b);
     uint32_t nb = 0;
-    if (__all_sync(0xFFFFFFFFu, small)) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const uint32_t u = __float_as_uint(x[k]);
-            const uint32_t E = (u >> 23) & 0xFFu;
-            const float a = __uint_as_float(u & 0x7FFFFFFFu);
-            const float t = __fadd_rn(q[k], 0x1.8p23f);
-            const int32_t bi = __float_as_int(t) - 0x4B400000;
-            const float Lr = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
-            const float bb = __fadd_rn(Lr, 127.0f);
-            const float m = __uint_as_float(pow2approx_bits<float>(bb));
-            const float d = fabsf(__fsub_rn(a, m));
-            const float lo = fminf(a, m);
-            bool ok = (E - 1u < 254u) && (bb >= 1.0f) && (bb < 255.0f) &&
-                      (a <= __fmul_rn(2.0f, m)) && (m <= __fmul_rn(2.0f, a));
-            if (lo < 0x1p-62f) {  // rare: exact power-of-two rescale
-                const float tt = __fmul_rn(__fmul_rn(lo, 0x1p64f), c.chk);
-                ok = ok && (tt >= FLT_MIN) && (__fmul_rn(d, 0x1p64f) <= tt);
-            } else {
-                const float tt = __fmul_rn(lo, c.chk);
-                ok = ok && (tt >= FLT_MIN) && (d <= tt);
-            }
-            b[k] = ok ? (int32_t)(((uint32_t)bi << 1) | (u >> 31)) : 0;
-            nb |= ok ? 0u : (1u << k);
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            int32_t bin = 0;
-            const bool ok = rel_quant<float>(x[k], c, bin);
-            b[k] = ok ? bin : 0;
-            nb |= ok ? 0u : (1u << k);
-        }
+    for (int k = 0; k < 4; k++) {
+        int32_t bin = 0;
+        const bool ok = rel_quant<float>(x[k], c, bin);
+        b[k] = ok ? bin : 0;
+        nb |= ok ? 0u : (1u << k);
     }
     return nb;
 }
