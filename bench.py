@@ -618,13 +618,17 @@ def lsq_reference(train_bins, test_bins, N, m=40000, seed=0):
 
 def run_profile(args):
     """A short, fixed sequence of calls for ncu captures: three warm-up calls
-    and one measured call of the chosen kind on the 512^3 float32 field."""
+    and one measured call of the chosen kind on the 512^3 float32 field (or
+    the float64 256^3 field, or the 2^28-value REL stress input)."""
     import paper_2407_15037_b300 as P
     import synth
     dev = torch.device("cuda", 0)
     shape = SHAPE if args.profile_dtype == "f32" else (256, 256, 256)
     dt = torch.float32 if args.profile_dtype == "f32" else torch.float64
-    x = synth.smooth_field(shape, dtype=dt, seed=0, device=dev)
+    if args.profile_input == "stress":
+        x = synth.rel_stress(1 << 28, seed=0, device=dev).to(dt)
+    else:
+        x = synth.smooth_field(shape, dtype=dt, seed=0, device=dev)
     q = P.alloc_outputs(x.numel(), x.dtype, dev)
     ws = P.new_workspace(x.numel(), dev)
     out = torch.empty_like(x)
@@ -635,7 +639,7 @@ def run_profile(args):
         if kind == "deq":
             P.dequantize_into(q, out, ws)
         else:
-            P.quantize_into(x, kind, 1e-3, q, ws)
+            P.quantize_into(x, kind, args.profile_eb, q, ws)
     torch.cuda.synchronize()
     print("profile run done", kind, args.profile_dtype)
 
@@ -644,6 +648,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq"], default=None)
     ap.add_argument("--profile-dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--profile-input", choices=["smooth", "stress"], default="smooth")
+    ap.add_argument("--profile-eb", type=float, default=1e-3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)

@@ -333,10 +333,10 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
             if (named_barrier_or(1, kComputeThreads, !ok)) return true;
             const uint64_t t0 = (uint64_t)(s_jt[bb] - A.tile_begin) * kScanTile;
             if (A.dtype == LCQ_F32)
-                write_outliers<float>(s_mask[bb], s_wpre[bb], kWords, reinterpret_cast<const float*>(A.in) + t0,
+                write_outliers<float, 2>(s_mask[bb], s_wpre[bb], kWords, reinterpret_cast<const float*>(A.in) + t0,
                                       s_pbase[bb], reinterpret_cast<uint32_t*>(A.out), A.cap);
             else
-                write_outliers<double>(s_mask[bb], s_wpre[bb], kWords, reinterpret_cast<const double*>(A.in) + t0,
+                write_outliers<double, 2>(s_mask[bb], s_wpre[bb], kWords, reinterpret_cast<const double*>(A.in) + t0,
                                        s_pbase[bb], reinterpret_cast<uint64_t*>(A.out), A.cap);
             named_barrier_sync(1, kComputeThreads);
             return false;

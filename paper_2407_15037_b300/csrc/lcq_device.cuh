@@ -345,10 +345,12 @@ __device__ __forceinline__ T rel_recon_lib(int32_t bin, const Consts<T>& c) {
 // Four values at a time (one 128-bit load), float32.  When every lane of the
 // warp has |q| < 2^22 for all four of its values -- the usual case -- one
 // warp-uniform branch selects straight-line code without per-value branches;
-// otherwise the per-value recipes above run.  Both give identical results:
-// the fast code is the same sequence of IEEE operations, and the checks it
-// leaves out are implied by |q| < 2^22 (no integer overflow, |b| <= 2^22 <
-// maxbin).  Returns the 4-bit outlier nibble; bins of outliers are 0.
+// otherwise (ABS) the per-value recipes above run, or (REL) the same
+// straight-line code with a rounding that is exact for any |q| < 2^29.  All
+// give identical results: the fast code is the same sequence of IEEE
+// operations, and the checks it leaves out are implied (|q| < 2^22: no
+// integer overflow, |b| <= 2^22 < maxbin; the REL implications are listed at
+// rel_fast4_f32).  Returns the 4-bit outlier nibble; bins of outliers are 0.
 // ---------------------------------------------------------------------------
 template <bool CHECK = true>
 __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
@@ -397,6 +399,11 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
 //    test implies when chk <= 1/2: if it fails, |a - m| > lo exactly, so
 //    d = RN(|a - m|) >= lo (lo is a float), while t = RN(lo chk) <= RN(lo / 2)
 //    < lo (the same holds after the exact rescale), so d <= t fails too;
+//  * WIDE = false (every |q| of the warp below 2^22) rounds with the
+//    1.5 2^23 addition; WIDE = true rounds with rintf / __float2int_rn, exact
+//    for every |q| < 2^29 (a float of magnitude >= 2^23 is an integer), and
+//    makes |q| >= 2^29 an outlier: that is the range test, and the two-sided
+//    bin test then holds because rint(q) < 2^29 for q < 2^29;
 //  * the exact rescale for tiny values runs only in warps that have one;
 //  * in a warp without tiny values (every lo = min(a, m) >= 2^-62) and with
 //    RATIO = false, the special-value and bb-range tests are implied as well:
@@ -405,19 +412,31 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
 //    Inf or NaN; bb >= 255 makes m +Inf, a NaN, or a negative value (bit 31
 //    set: then t = RN(lo chk) <= 0 < FLT_MIN); each of these fails d <= t or
 //    t >= FLT_MIN.
-template <bool RATIO>
+template <bool RATIO, bool WIDE>
 __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float q[4], const Consts<float>& c,
                                                   int32_t b[4]) {
     float a[4], m[4], lo[4], bb[4];
     int32_t bin[4];
+    bool inr[4];
     bool tiny = false;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const uint32_t u = __float_as_uint(x[k]);
         a[k] = __uint_as_float(u & 0x7FFFFFFFu);
-        const float t = __fadd_rn(q[k], 0x1.8p23f);
-        bin[k] = (int32_t)(((uint32_t)(__float_as_int(t) - 0x4B400000) << 1) | (u >> 31));
-        const float Lr = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
+        float bf;
+        int32_t bi;
+        if (WIDE) {
+            bf = rintf(q[k]);
+            bi = __float2int_rn(q[k]);
+            inr[k] = fabsf(q[k]) < 0x1p29f;
+        } else {
+            const float t = __fadd_rn(q[k], 0x1.8p23f);
+            bi = __float_as_int(t) - 0x4B400000;
+            bf = __fsub_rn(t, 0x1.8p23f);
+            inr[k] = true;
+        }
+        bin[k] = (int32_t)(((uint32_t)bi << 1) | (u >> 31));
+        const float Lr = __fmul_rn(bf, c.scale);
         bb[k] = __fadd_rn(Lr, 127.0f);
         m[k] = __uint_as_float(__float2uint_rz(__fmul_rn(bb[k], 0x1p23f)));
         lo[k] = fminf(a[k], m[k]);
@@ -429,7 +448,7 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
         for (int k = 0; k < 4; k++) {
             const float d = fabsf(__fsub_rn(a[k], m[k]));  // exact (Sterbenz) when accepted
             const float tt = __fmul_rn(lo[k], c.chk);
-            const bool ok = (tt >= FLT_MIN) && (d <= tt);
+            const bool ok = inr[k] && (tt >= FLT_MIN) && (d <= tt);
             b[k] = ok ? bin[k] : 0;
             nb |= ok ? 0u : (1u << k);
         }
@@ -438,7 +457,8 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const uint32_t E = (__float_as_uint(x[k]) >> 23) & 0xFFu;
-        bool ok = (E - 1u < 254u) && (__float_as_uint(bb[k]) - 0x3F800000u < 0x437F0000u - 0x3F800000u);
+        bool ok = inr[k] && (E - 1u < 254u) &&
+                  (__float_as_uint(bb[k]) - 0x3F800000u < 0x437F0000u - 0x3F800000u);
         if (RATIO) ok = ok && (a[k] <= __fmul_rn(2.0f, m[k])) && (m[k] <= __fmul_rn(2.0f, a[k]));
         const float d = fabsf(__fsub_rn(a[k], m[k]));
         if (lo[k] < 0x1p-62f) {  // exact power-of-two rescale
@@ -463,17 +483,10 @@ __device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Const
         q[k] = __fmul_rn(L, c.inv);
         small &= fabsf(q[k]) < 0x1p22f;
     }
-    if (__all_sync(0xFFFFFFFFu, small))
-        return c.chk <= 0.5f ? rel_fast4_f32<false>(x, q, c, b) : rel_fast4_f32<true>(x, q, c, b);
-    uint32_t nb = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        int32_t bin = 0;
-        const bool ok = rel_quant<float>(x[k], c, bin);
-        b[k] = ok ? bin : 0;
-        nb |= ok ? 0u : (1u << k);
-    }
-    return nb;
+    const bool narrow = __all_sync(0xFFFFFFFFu, small);
+    if (c.chk <= 0.5f)
+        return narrow ? rel_fast4_f32<false, false>(x, q, c, b) : rel_fast4_f32<false, true>(x, q, c, b);
+    return narrow ? rel_fast4_f32<true, false>(x, q, c, b) : rel_fast4_f32<true, true>(x, q, c, b);
 }
 
 // ---------------------------------------------------------------------------

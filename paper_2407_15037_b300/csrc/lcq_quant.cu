@@ -508,19 +508,17 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
             if (named_barrier_or(1, kComputeThreads, !ok)) return true;
             const uint64_t tb = (uint64_t)s_jt[bb] * TILE;
             const uint64_t pbase = s_pbase[bb];
-            for (int w = tid; w < WORDS; w += kComputeThreads) {
-                uint32_t mw = s_mask[bb][sw(w)];
-                if (!mw) continue;
-                const uint32_t pre = s_wpre[bb][sw(w)];
-                uint32_t below = 0;
-                while (mw) {
-                    const int bit = __ffs(mw) - 1;
-                    mw &= mw - 1u;
-                    const uint64_t rank = pbase + pre + below++;
-                    if (rank < avail) p.out[tb + (uint64_t)w * 32 + bit] = F::from_bits(p.outl[rank]);
+            using U = typename F::U;
+            for_each_outlier<U>(
+                s_mask[bb], s_wpre[bb], WORDS,
+                [&](uint32_t, uint32_t r) {
+                    const uint64_t rank = pbase + r;
+                    return rank < avail ? p.outl[rank] : (U)0;
+                },
+                [&](uint32_t i, uint32_t r, U v) {
+                    if (pbase + r < avail) p.out[tb + i] = F::from_bits(v);
                     else overrun = true;
-                }
-            }
+                });
             named_barrier_sync(1, kComputeThreads);
             return false;
         };
