@@ -461,13 +461,11 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
                   (__float_as_uint(bb[k]) - 0x3F800000u < 0x437F0000u - 0x3F800000u);
         if (RATIO) ok = ok && (a[k] <= __fmul_rn(2.0f, m[k])) && (m[k] <= __fmul_rn(2.0f, a[k]));
         const float d = fabsf(__fsub_rn(a[k], m[k]));
-        if (lo[k] < 0x1p-62f) {  // exact power-of-two rescale
-            const float tt = __fmul_rn(__fmul_rn(lo[k], 0x1p64f), c.chk);
-            ok = ok && (tt >= FLT_MIN) && (__fmul_rn(d, 0x1p64f) <= tt);
-        } else {
-            const float tt = __fmul_rn(lo[k], c.chk);
-            ok = ok && (tt >= FLT_MIN) && (d <= tt);
-        }
+        // exact power-of-two rescale of tiny values; a scale of 1 is exact too,
+        // so selecting the factor gives both branches of rel_quant at once
+        const float sc = lo[k] < 0x1p-62f ? 0x1p64f : 1.0f;
+        const float tt = __fmul_rn(__fmul_rn(lo[k], sc), c.chk);
+        ok = ok && (tt >= FLT_MIN) && (__fmul_rn(d, sc) <= tt);
         b[k] = ok ? bin[k] : 0;
         nb |= ok ? 0u : (1u << k);
     }

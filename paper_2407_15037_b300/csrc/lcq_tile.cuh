@@ -189,12 +189,12 @@ __device__ __forceinline__ void quantize_subtile(const T* st, const T* gin, bool
 // by the kComputeThreads compute threads.  Each warp takes 32 consecutive
 // words at a time and walks them one of two ways: each lane its own word (as
 // many steps as the fullest word has bits; every load and store of a step
-// touches a different line per lane), or the non-empty words one by one with
-// one lane per value (one step per non-empty word; loads and stores
-// coalesced).  It takes the cheaper by a cost in issued instructions plus
-// memory wavefronts: 10 per lane-walk step and 2 per outlier, against 14 per
-// word step.  Either walk takes U steps at a time and issues their U loads
-// before the U stores, so that the loads' latencies overlap.
+// touches a different line per lane), or all 32 words one by one with one
+// lane per value (32 steps; loads and stores coalesced).  It takes the
+// cheaper by a cost in issued instructions plus memory wavefronts: 14 per
+// lane-walk step and 2 per outlier, against 13 per word step.  Either walk
+// takes U steps at a time and issues their U loads before the U stores, so
+// that the loads' latencies overlap.
 template <typename V, int U = 4, typename LD, typename ST>
 __device__ __forceinline__ void for_each_outlier(const uint32_t* s_words, const uint32_t* s_wpre, int words,
                                                  LD&& ld, ST&& st) {
@@ -207,8 +207,7 @@ __device__ __forceinline__ void for_each_outlier(const uint32_t* s_words, const 
         const uint32_t tot = __reduce_add_sync(0xFFFFFFFFu, cnt);
         if (tot == 0) continue;
         const uint32_t maxc = __reduce_max_sync(0xFFFFFFFFu, cnt);
-        uint32_t nz = __ballot_sync(0xFFFFFFFFu, mw != 0u);
-        if (10u * maxc + 2u * tot <= 14u * (uint32_t)__popc(nz)) {
+        if (14u * maxc + 2u * tot <= 13u * 32u + 2u * 32u) {
             uint32_t m = mw, r = pre;
             while (m) {
                 uint32_t iu[U], ru[U];
@@ -230,28 +229,25 @@ __device__ __forceinline__ void for_each_outlier(const uint32_t* s_words, const 
                     if (on[u]) st(iu[u], ru[u], v[u]);
             }
         } else {
-            const uint32_t below = (1u << lane) - 1u;
-            while (nz) {
-                uint32_t iu[U], ru[U];
+            const uint32_t bit = 1u << lane, below = bit - 1u;
+            const uint32_t i0 = (uint32_t)w0 * 32 + lane;
+            for (int j0 = 0; j0 < 32; j0 += U) {
+                uint32_t ru[U];
                 bool on[U];
                 V v[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
-                    const bool has = nz != 0u;
-                    const int j = has ? __ffs(nz) - 1 : 0;
-                    nz &= nz - 1u;
-                    const uint32_t mj = has ? __shfl_sync(0xFFFFFFFFu, mw, j) : 0u;
-                    const uint32_t pj = __shfl_sync(0xFFFFFFFFu, pre, j);
-                    on[u] = (mj >> lane) & 1u;
-                    iu[u] = (uint32_t)(w0 + j) * 32 + lane;
+                    const uint32_t mj = __shfl_sync(0xFFFFFFFFu, mw, j0 + u);
+                    const uint32_t pj = __shfl_sync(0xFFFFFFFFu, pre, j0 + u);
+                    on[u] = (mj & bit) != 0u;
                     ru[u] = pj + __popc(mj & below);
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++)
-                    if (on[u]) v[u] = ld(iu[u], ru[u]);
+                    if (on[u]) v[u] = ld(i0 + 32u * (j0 + u), ru[u]);
 #pragma unroll
                 for (int u = 0; u < U; u++)
-                    if (on[u]) st(iu[u], ru[u], v[u]);
+                    if (on[u]) st(i0 + 32u * (j0 + u), ru[u], v[u]);
             }
         }
     }
