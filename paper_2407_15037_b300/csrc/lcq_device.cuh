@@ -512,6 +512,16 @@ constexpr uint64_t kD_SIGN = 0x8000000000000000ull;
 __device__ __forceinline__ uint64_t dbits(double v) { return (uint64_t)__double_as_longlong(v); }
 __device__ __forceinline__ double dfrom(uint64_t u) { return __longlong_as_double((long long)u); }
 
+// The bits of |v| from the bits u of v: the sign bit cleared by an integer
+// instruction.  Written as inline PTX because the compiler otherwise turns
+// the mask of a double's bit pattern into a floating-point absolute value,
+// which this GPU executes on its FP64 pipe.
+__device__ __forceinline__ uint64_t clear_sign(uint64_t u) {
+    uint64_t r;
+    asm("and.b64 %0, %1, 0x7FFFFFFFFFFFFFFF;" : "=l"(r) : "l"(u));
+    return r;
+}
+
 // rint(q) for a double q with |q| < 2^30 (caller checks), round half to even.
 __device__ __forceinline__ int32_t rint_d_small(uint64_t u) {
     const int e = (int)((u >> 52) & 0x7FF);
@@ -521,6 +531,26 @@ __device__ __forceinline__ int32_t rint_d_small(uint64_t u) {
     const uint64_t ip = m >> sh;
     const uint64_t rem = m & ((1ull << sh) - 1);
     const uint64_t half = 1ull << (sh - 1);
+    const uint64_t r = ip + ((rem > half || (rem == half && (ip & 1))) ? 1 : 0);
+    return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
+}
+
+// rint_d_small, and whether q lies at least 2^-20 away from the midpoint
+// between two integers: |q - rint(q)| <= 1/2 - 2^-20.  With q = m 2^-sh,
+// 1/2 - |q - rint(q)| = |rem - half| 2^-sh; for |q| < 1/2 it is 1/2 - |q|.
+__device__ __forceinline__ int32_t rint_d_small_clear(uint64_t u, bool& clear) {
+    const int e = (int)((u >> 52) & 0x7FF);
+    const int sh = 1075 - e;  // q = m 2^-sh, m = 1.M 2^52
+    const uint64_t m = (u & kD_MANT) | (1ull << 52);
+    if (sh > 53) {  // |q| < 1/2
+        clear = sh > 54 || m <= (1ull << 53) - (1ull << 34);
+        return 0;
+    }
+    const uint64_t ip = m >> sh;
+    const uint64_t rem = m & ((1ull << sh) - 1);
+    const uint64_t half = 1ull << (sh - 1);
+    const uint64_t gap = rem > half ? rem - half : half - rem;
+    clear = gap >= (1ull << (sh - 20));  // sh >= 23 here since |q| < 2^30
     const uint64_t r = ip + ((rem > half || (rem == half && (ip & 1))) ? 1 : 0);
     return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
 }
@@ -586,17 +616,40 @@ __device__ __forceinline__ uint64_t absdiff_close_dbits(uint64_t ua, uint64_t ub
     return D << (eb - 1 > 0 ? eb - 1 : 0);                   // subnormal result: units of 2^-1074
 }
 
+// The double-check of Sec. 3.1 for float64 ABS / NOA, on the FP64 pipe:
+// |RN(x - RN(b eb2))| <= eb_T.  Out of line: only values that lie within
+// 2^-20 of a bin edge run it (see abs_quant_f64).
+static __device__ __noinline__ bool abs_check_f64(double x, int32_t b, double eb2, double ebT) {
+    const double recon = __dmul_rn(dfrom(int_to_dbits(b)), eb2);
+    return clear_sign(dbits(__dsub_rn(x, recon))) <= dbits(ebT);
+}
+
+// ABS / NOA on float64.  q = RN(x inv) and b = rint(q) as always; the
+// double-check then runs only where its outcome is not already certain.
+// With e = eb2 = 2 eb_T (exact), inv = (1/e)(1 + d1), q = x inv (1 + d2)
+// and recon = b e (1 + d3), |di| <= u = 2^-53 (q is normal when b != 0; when
+// q is subnormal, b = 0 and |x| < 2^-1022 e (1 + u) is far below eb_T):
+//   x - b e = e (q / ((1 + d1)(1 + d2)) - b),  so
+//   |x - recon| <= e (|q - b| + 2.0001 u |q| + u |b|)
+//              <= e (|q - b| + 3.0001 u |q| + u / 2)      (|b| <= |q| + 1/2)
+//              <  e (|q - b| + 2^-20)                    (|q| < 2^30).
+// So |q - b| <= 1/2 - 2^-20 gives |x - recon| <= e / 2 = eb_T exactly, and
+// then RN(|x - recon|) <= eb_T as well (eb_T is a double): the check passes.
+// recon must not overflow for this (d3 above): with |x| < 2^1022 and b != 0,
+// |q| >= 1/2 gives e < 2^1023 and |b e| < |x| (1 + 2u) + e / 2 < DBL_MAX.
+// Every other value (a fraction of about 2^-19 of smooth data, and any
+// |x| >= 2^1022) runs the check.
 template <bool CHECK = true>
 __device__ __forceinline__ bool abs_quant_f64(double x, const Consts<double>& c, int32_t& bin) {
     const double q = __dmul_rn(x, c.inv);
-    const uint64_t uq = dbits(q) & ~kD_SIGN;
+    const uint64_t uq = clear_sign(dbits(q));
     if (!(uq < 0x41D0000000000000ull)) return false;  // !(|q| < 2^30): also NaN
-    const int32_t b = rint_d_small(dbits(q));
+    bool clear;
+    const int32_t b = rint_d_small_clear(dbits(q), clear);
     if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
     if constexpr (CHECK) {
-        const double recon = __dmul_rn(dfrom(int_to_dbits(b)), c.scale);
-        const uint64_t ud = dbits(__dsub_rn(x, recon)) & ~kD_SIGN;
-        if (!(ud <= dbits(c.ebT))) return false;      // !(|x - recon| <= eb_T): also NaN
+        clear = clear && clear_sign(dbits(x)) < 0x7FD0000000000000ull;  // |x| < 2^1022
+        if (!clear && !abs_check_f64(x, b, c.scale, c.ebT)) return false;
     }
     bin = b;
     return true;
@@ -606,9 +659,9 @@ __device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c,
     const uint64_t u = dbits(x);
     const uint64_t E = (u >> 52) & 0x7FF;
     if (E == 0 || E == 0x7FF) return false;  // zero, denormal, Inf, NaN
-    const uint64_t ua = u & ~kD_SIGN;
+    const uint64_t ua = clear_sign(u);
     const double q = __dmul_rn(dfrom(log2approx_dbits(u)), c.inv);
-    const uint64_t uq = dbits(q) & ~kD_SIGN;
+    const uint64_t uq = clear_sign(dbits(q));
     if (!(uq < 0x41C0000000000000ull)) return false;  // !(|q| < 2^29)
     const int32_t b = rint_d_small(dbits(q));
     if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3

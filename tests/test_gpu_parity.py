@@ -227,6 +227,29 @@ def test_f64_random_bit_patterns_and_edges(bound, eb):
     compare(torch.from_numpy(x).to(DEV), bound, eb)
 
 
+@pytest.mark.parametrize("bound", ["abs", "noa"])
+@pytest.mark.parametrize("eb", [1e-3, 0.37, 1e300])
+def test_f64_values_near_the_check_threshold(bound, eb):
+    """float64 ABS / NOA skip the double-check where its outcome is certain
+    (|q - b| <= 1/2 - 2^-20, |x| < 2^1022); values just inside and outside
+    that margin, at bin edges of small and large bins, and near DBL_MAX
+    (where b eb2 can overflow) must still match the oracle."""
+    if bound == "noa" and eb == 1e300:
+        pytest.skip("NOA bound is relative to the range")
+    rng = np.random.default_rng(int(eb * 1000) % 97)
+    eb2 = 2 * eb
+    vals = []
+    for k in (rng.integers(-(1 << 29), 1 << 29, 4000), rng.integers(-40, 40, 4000)):
+        k = k.astype(np.float64)
+        for f in (0.25, 0.5, 0.99, 1.0, 1.01, 2.0, 4.0, 64.0):
+            for sgn in (-1.0, 1.0):
+                vals.append((k + 0.5 + sgn * f * 2.0 ** -20) * eb2)
+    big = np.finfo(np.float64).max * (1.0 - rng.random(20000) * 1e-6)
+    vals += [big, -big, np.ldexp(1.0 + rng.random(20000), 1022), np.ldexp(1.0 + rng.random(20000), 1021)]
+    x = np.concatenate(vals)
+    compare(torch.from_numpy(x).to(DEV), bound, eb)
+
+
 # --------------------------------------------------------- full sizes ----
 
 @pytest.mark.parametrize("bound", BOUNDS)
