@@ -222,7 +222,14 @@ const char* lcq_status_string(lcq_status status);
  * the host buffers; returns once everything is back on the host (it
  * synchronises `stream`).  d_stage is a device buffer of at least
  * lcq_host_stage_size(dtype, n, outlier_capacity) bytes (caller-owned).
- * For full copy bandwidth the host buffers should be page-locked.
+ * The work is pipelined in chunks of 2^23 values: the input goes up on one
+ * copy stream, each chunk is quantized on `stream` once it has arrived (NOA:
+ * once all of it has, for the range), and its bins and mask words come down
+ * on another copy stream meanwhile; the outliers come down at the end.  The
+ * result is the one lcq_quantize gives.  The two copy streams and their
+ * events belong to the library (one set per device, made on first use);
+ * calls for one device run one at a time.  For full copy bandwidth the host
+ * buffers should be page-locked.
  */
 size_t lcq_host_stage_size(lcq_dtype dtype, uint64_t n, uint64_t outlier_capacity);
 lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double eb,

@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -841,12 +842,56 @@ static uint64_t bits_host(T v) {
     return u;
 }
 
+// Pipelined host <-> device copies around quantize_impl (lcq_quantize_host):
+// the input goes up in chunks on its own stream, each chunk is quantized as
+// soon as it has arrived, and its bins and mask words go down on a third
+// stream while later chunks are still moving up.
+struct HostIO {
+    const char* h_in;
+    char* d_in;
+    size_t es;
+    int32_t* h_bins;
+    const int32_t* d_bins;
+    uint32_t* h_mask;
+    const uint32_t* d_mask;
+    cudaStream_t h2d, d2h;
+    cudaEvent_t* ev;  // 2 per chunk + 1
+    uint64_t chunk;   // values per chunk, a multiple of 32
+};
+
+static bool host_io_upload(const HostIO& io, uint64_t n, cudaStream_t st) {
+    const uint64_t K = (n + io.chunk - 1) / io.chunk;
+    if (cudaEventRecord(io.ev[2 * K], st) != cudaSuccess) return false;
+    if (cudaStreamWaitEvent(io.h2d, io.ev[2 * K], 0) != cudaSuccess) return false;
+    if (cudaStreamWaitEvent(io.d2h, io.ev[2 * K], 0) != cudaSuccess) return false;
+    for (uint64_t i = 0; i < K; i++) {
+        const uint64_t off = i * io.chunk, len = n - off < io.chunk ? n - off : io.chunk;
+        if (cudaMemcpyAsync(io.d_in + off * io.es, io.h_in + off * io.es, len * io.es, cudaMemcpyHostToDevice,
+                            io.h2d) != cudaSuccess ||
+            cudaEventRecord(io.ev[2 * i], io.h2d) != cudaSuccess)
+            return false;
+    }
+    return true;
+}
+
+static bool host_io_download(const HostIO& io, uint64_t i, uint64_t off, uint64_t len, cudaStream_t st) {
+    if (cudaEventRecord(io.ev[2 * i + 1], st) != cudaSuccess) return false;
+    if (cudaStreamWaitEvent(io.d2h, io.ev[2 * i + 1], 0) != cudaSuccess) return false;
+    const uint64_t w0 = off / 32, w1 = (off + len + 31) / 32;
+    return cudaMemcpyAsync(io.h_bins + off, io.d_bins + off, len * 4, cudaMemcpyDeviceToHost, io.d2h) ==
+               cudaSuccess &&
+           cudaMemcpyAsync(io.h_mask + w0, io.d_mask + w0, (w1 - w0) * 4, cudaMemcpyDeviceToHost, io.d2h) ==
+               cudaSuccess;
+}
+
 // given: NOA only; null = derive the range from the input (k_minmax), else
-// {any, min, max} of the caller's range (already validated).
+// {any, min, max} of the caller's range (already validated).  io: host
+// copies to pipeline with the launches (n > 0), or null.
 template <typename T>
 static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint64_t n, int32_t* bins,
                                 uint32_t* mask, void* outl, uint64_t cap, lcq_header* hdr, void* ws,
-                                cudaStream_t st, const double* given = nullptr, int ablation = 0) {
+                                cudaStream_t st, const double* given = nullptr, int ablation = 0,
+                                const HostIO* io = nullptr) {
     Consts<T> c{};
     const bool noa = bt == LCQ_NOA;
     if (bt == LCQ_ABS) {
@@ -860,6 +905,12 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     size_t dsz = (desc_bytes(n) + 255) & ~(size_t)255;
     uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz);
 
+    if (io) {
+        if (n == 0 || !host_io_upload(*io, n, st)) return LCQ_ERR_CUDA;
+        // NOA needs the whole input for its range before any binning
+        const uint64_t K = (n + io->chunk - 1) / io->chunk;
+        if (noa && !given && cudaStreamWaitEvent(st, io->ev[2 * (K - 1)], 0) != cudaSuccess) return LCQ_ERR_CUDA;
+    }
     if (noa && given) {
         k_noa_given<T><<<1, 1, 0, st>>>(hdr, given[0] != 0.0, (T)given[1], (T)given[2], eb, dtype, n == 0);
         if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
@@ -883,8 +934,11 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         }
         return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
     }
-    for (uint64_t off = 0; off < n; off += kChunk) {
-        const uint64_t len = (n - off) < kChunk ? (n - off) : kChunk;
+    const uint64_t chunk = io ? io->chunk : kChunk;
+    for (uint64_t off = 0; off < n; off += chunk) {
+        const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
+        if (io && !(noa && !given) && cudaStreamWaitEvent(st, io->ev[2 * (off / chunk)], 0) != cudaSuccess)
+            return LCQ_ERR_CUDA;
         QParams<T> p;
         p.in = in + off;
         p.bins = bins + off;
@@ -912,6 +966,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         else if (bt == LCQ_REL) e = launch_quantize_variant<T, LCQ_REL>(var, p, st);
         else e = launch_quantize_variant<T, LCQ_ABS>(var, p, st);
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
+        if (io && !host_io_download(*io, off / chunk, off, len, st)) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
 }
@@ -973,6 +1028,33 @@ lcq_status check_quantize_args(lcq_dtype dtype, lcq_bound_type bound_type, doubl
     if (outlier_capacity > 0 && (!d_outliers || !aligned16(d_outliers))) return LCQ_ERR_ARG;
     if (n >= (1ull << 40)) return LCQ_ERR_ARG;
     if (!(eb > 0.0) || !std::isfinite(eb)) return LCQ_ERR_BOUND;
+    return LCQ_OK;
+}
+
+// Copy streams and events for lcq_quantize_host, one set per device, made
+// on first use and kept; the lock serialises the calls of one device.
+constexpr uint64_t kHostChunk = 1ull << 23;  // values per pipelined chunk (multiple of 32)
+
+struct HostPipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    std::vector<cudaEvent_t> ev;
+};
+static std::mutex g_pipe_mu[64];
+static HostPipe g_pipe[64];
+
+static lcq_status host_pipe(size_t nev, HostPipe** out, std::unique_lock<std::mutex>& lock) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return LCQ_ERR_CUDA;
+    lock = std::unique_lock<std::mutex>(g_pipe_mu[dev]);
+    HostPipe& p = g_pipe[dev];
+    if (!p.h2d && cudaStreamCreateWithFlags(&p.h2d, cudaStreamNonBlocking) != cudaSuccess) return LCQ_ERR_CUDA;
+    if (!p.d2h && cudaStreamCreateWithFlags(&p.d2h, cudaStreamNonBlocking) != cudaSuccess) return LCQ_ERR_CUDA;
+    while (p.ev.size() < nev) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return LCQ_ERR_CUDA;
+        p.ev.push_back(e);
+    }
+    *out = &p;
     return LCQ_OK;
 }
 
@@ -1154,36 +1236,61 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
                              void* d_stage, size_t stage_bytes, void* d_ws, size_t ws_bytes,
                              cudaStream_t stream) {
     if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (bound_type != LCQ_ABS && bound_type != LCQ_REL && bound_type != LCQ_NOA) return LCQ_ERR_ARG;
     if (!h_hdr || !d_stage || !aligned16(d_stage)) return LCQ_ERR_ARG;
     if (n > 0 && (!h_in || !h_bins || !h_mask)) return LCQ_ERR_ARG;
     if (outlier_capacity > 0 && !h_outliers) return LCQ_ERR_ARG;
+    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return LCQ_ERR_BOUND;
     if (stage_bytes < lcq_host_stage_size(dtype, n, outlier_capacity)) return LCQ_ERR_WORKSPACE;
+    if (!d_ws || !aligned16(d_ws)) return LCQ_ERR_ARG;
+    if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
     const size_t es = dtype == LCQ_F64 ? 8 : 4;
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     char* base = (char*)d_stage;
-    void* d_in = base;
+    char* d_in = base;
     int32_t* d_bins = (int32_t*)(base + up(n * es));
     uint32_t* d_mask = (uint32_t*)((char*)d_bins + up(n * 4));
     void* d_out = (char*)d_mask + up(((n + 31) / 32) * 4);
     lcq_header* d_hdr = (lcq_header*)((char*)d_out + up(outlier_capacity * es));
-    if (n && cudaMemcpyAsync(d_in, h_in, n * es, cudaMemcpyHostToDevice, stream) != cudaSuccess)
-        return LCQ_ERR_CUDA;
-    lcq_status s = lcq_quantize(dtype, bound_type, eb, d_in, n, d_bins, d_mask,
-                                outlier_capacity ? d_out : nullptr, outlier_capacity, d_hdr, d_ws,
-                                ws_bytes, stream);
+    void* d_outl = outlier_capacity ? d_out : nullptr;
+    lcq_status s;
+    if (n == 0) {
+        s = lcq_quantize(dtype, bound_type, eb, nullptr, 0, d_bins, d_mask, d_outl, outlier_capacity, d_hdr,
+                         d_ws, ws_bytes, stream);
+        if (s != LCQ_OK) return s;
+        if (cudaMemcpyAsync(h_hdr, d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+            cudaStreamSynchronize(stream) != cudaSuccess)
+            return LCQ_ERR_CUDA;
+        return LCQ_OK;
+    }
+    // the copy streams and events of this device, held for the whole call
+    const uint64_t K = (n + kHostChunk - 1) / kHostChunk;
+    HostPipe* pipe = nullptr;
+    std::unique_lock<std::mutex> lock;
+    if (host_pipe(2 * K + 2, &pipe, lock) != LCQ_OK) return LCQ_ERR_CUDA;
+    HostIO io{(const char*)h_in, d_in, es, h_bins, d_bins, h_mask, d_mask, pipe->h2d, pipe->d2h,
+              pipe->ev.data(), kHostChunk};
+    if (dtype == LCQ_F32)
+        s = quantize_impl<float>(bound_type, eb, (const float*)d_in, n, d_bins, d_mask, d_outl, outlier_capacity,
+                                 d_hdr, d_ws, stream, nullptr, 0, &io);
+    else
+        s = quantize_impl<double>(bound_type, eb, (const double*)d_in, n, d_bins, d_mask, d_outl,
+                                  outlier_capacity, d_hdr, d_ws, stream, nullptr, 0, &io);
+    // drain both copy streams whatever happened, then report
+    const bool ok_end = cudaEventRecord(io.ev[2 * K + 1], stream) == cudaSuccess &&
+                        cudaStreamWaitEvent(io.d2h, io.ev[2 * K + 1], 0) == cudaSuccess &&
+                        cudaMemcpyAsync(h_hdr, d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, io.d2h) ==
+                            cudaSuccess;
+    const bool ok_sync = cudaStreamSynchronize(io.h2d) == cudaSuccess &&
+                         cudaStreamSynchronize(io.d2h) == cudaSuccess &&
+                         cudaStreamSynchronize(stream) == cudaSuccess;
     if (s != LCQ_OK) return s;
-    if (n && cudaMemcpyAsync(h_bins, d_bins, n * 4, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+    if (!ok_end || !ok_sync) return LCQ_ERR_CUDA;
+    const uint64_t cnt = h_hdr->outlier_count < outlier_capacity ? h_hdr->outlier_count : outlier_capacity;
+    if (cnt && (cudaMemcpyAsync(h_outliers, d_out, cnt * es, cudaMemcpyDeviceToHost, io.d2h) != cudaSuccess ||
+                cudaStreamSynchronize(io.d2h) != cudaSuccess))
         return LCQ_ERR_CUDA;
-    if (n && cudaMemcpyAsync(h_mask, d_mask, ((n + 31) / 32) * 4, cudaMemcpyDeviceToHost, stream) !=
-                 cudaSuccess)
-        return LCQ_ERR_CUDA;
-    if (cudaMemcpyAsync(h_hdr, d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-        return LCQ_ERR_CUDA;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return LCQ_ERR_CUDA;
-    uint64_t cnt = h_hdr->outlier_count < outlier_capacity ? h_hdr->outlier_count : outlier_capacity;
-    if (cnt && cudaMemcpyAsync(h_outliers, d_out, cnt * es, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
-        return LCQ_ERR_CUDA;
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return LCQ_ERR_CUDA;
     if (h_hdr->status & LCQ_STATUS_TIMEOUT) return LCQ_ERR_TIMEOUT;
     if (h_hdr->status & LCQ_STATUS_CAPACITY) return LCQ_ERR_CAPACITY;
     return LCQ_OK;

@@ -161,22 +161,32 @@ def test_dequantize_rejects_mismatched_header():
     assert torch.all(out == 7.0)
 
 
-def test_host_entry_point_matches_device_path():
-    x = synth.smooth_field((64, 64, 64), seed=3).to(torch.float32)  # built on the host
-    xp = x.pin_memory()
-    n = x.numel()
+@pytest.mark.parametrize("bound", BOUNDS)
+@pytest.mark.parametrize("dtype,n", [(torch.float32, 64 ** 3), (torch.float32, 3 * (1 << 23) + 12345),
+                                     (torch.float64, (1 << 23) + 77)])
+def test_host_entry_point_matches_device_path(bound, dtype, n):
+    """lcq_quantize_host (host buffers; the input goes up and the results come
+    down in pipelined chunks of 2^23 values) gives exactly what the device
+    entry point gives: one partial chunk, several chunks with a ragged tail,
+    float64, and outliers spread over every chunk."""
+    x = synth.smooth_field((n,), dtype=dtype, seed=3, device=DEV)
+    x[::4099] = float("nan")
+    xp = x.cpu().pin_memory()
+    idt = torch.int32 if dtype == torch.float32 else torch.int64
     outs = P.Quantized(torch.empty(n, dtype=torch.int32).pin_memory(),
                        torch.empty((n + 31) // 32, dtype=torch.int32).pin_memory(),
-                       torch.empty(n, dtype=torch.int32).pin_memory(),
-                       torch.empty(P.lcq.HEADER_BYTES, dtype=torch.uint8).pin_memory(), n, x.dtype)
-    stage = torch.empty(P.host_stage_size(P.F32, n, n), dtype=torch.uint8, device=DEV)
+                       torch.empty(n, dtype=idt).pin_memory(),
+                       torch.empty(P.lcq.HEADER_BYTES, dtype=torch.uint8).pin_memory(), n, dtype)
+    dc = P.lcq._dtype_code(x)
+    stage = torch.empty(P.host_stage_size(dc, n, n), dtype=torch.uint8, device=DEV)
     ws = P.new_workspace(n, DEV)
-    P.quantize_host(xp, "rel", 1e-3, outs, stage, ws)
-    qd = P.quantize(x.to(DEV), "rel", 1e-3)
+    P.quantize_host(xp, bound, 1e-4, outs, stage, ws)
+    qd = P.quantize(x, bound, 1e-4)
     torch.cuda.synchronize()
+    h = qd.read_header()
+    assert h.outlier_count >= n // 4099
     assert torch.equal(outs.bins, qd.bins.cpu())
     assert torch.equal(outs.mask, qd.mask.cpu())
-    h = qd.read_header()
     assert torch.equal(outs.outliers[:h.outlier_count], qd.outliers[:h.outlier_count].cpu())
     assert torch.equal(outs.header, qd.header.cpu())
 
@@ -243,7 +253,8 @@ def test_f64_values_near_the_check_threshold(bound, eb):
         k = k.astype(np.float64)
         for f in (0.25, 0.5, 0.99, 1.0, 1.01, 2.0, 4.0, 64.0):
             for sgn in (-1.0, 1.0):
-                vals.append((k + 0.5 + sgn * f * 2.0 ** -20) * eb2)
+                with np.errstate(over="ignore"):  # beyond DBL_MAX: +-Inf, an outlier on both sides
+                    vals.append((k + 0.5 + sgn * f * 2.0 ** -20) * eb2)
     big = np.finfo(np.float64).max * (1.0 - rng.random(20000) * 1e-6)
     vals += [big, -big, np.ldexp(1.0 + rng.random(20000), 1022), np.ldexp(1.0 + rng.random(20000), 1021)]
     x = np.concatenate(vals)
