@@ -51,6 +51,9 @@ struct alignas(16) Array {
     uint32_t pad;
     double eb;
     uint64_t bits[4];  // ABS/REL constants: ebT, scale, inv, chk (NOA: in the header)
+    uint64_t cert_w;   // float64 REL certainty bounds (Consts::cert_w / cert_emin)
+    uint32_t cert_emin;
+    uint32_t pad2;
 };
 
 struct PlanHead {
@@ -240,6 +243,8 @@ __device__ __forceinline__ void batch_subtile(const Array& A, const void* stage,
         c.inv = Ty<T>::from_bits((U)A.bits[2]);
         c.chk = Ty<T>::from_bits((U)A.bits[3]);
         c.all_outliers = 0;
+        c.cert_w = A.cert_w;
+        c.cert_emin = A.cert_emin;
     }
     const bool full = first + STILE <= A.n;
     const uint64_t nvalid = A.n > first ? A.n - first : 0;
@@ -531,7 +536,8 @@ lcq_status lcq_batch_prepare(const lcq_batch_item* h_items, uint32_t count, void
         A.bound = it.bound_type;
         A.eb = it.eb;
         if (it.bound_type != LCQ_NOA) {
-            if (!host_consts((lcq_dtype)it.dtype, (lcq_bound_type)it.bound_type, it.eb, A.bits)) {
+            if (!host_consts((lcq_dtype)it.dtype, (lcq_bound_type)it.bound_type, it.eb, A.bits, &A.cert_w,
+                             &A.cert_emin)) {
                 h_info->bad_item = i;
                 return LCQ_ERR_BOUND;
             }

@@ -150,6 +150,11 @@ struct Consts {
     T inv;     // ABS/NOA: 1/eb2; REL: 1/step
     T chk;     // REL acceptance factor
     uint32_t all_outliers;
+    // float64 REL: the acceptance test is certain to pass for a normal |x|
+    // with biased exponent >= cert_emin whose mantissa field M satisfies
+    // cert_w <= M < 2^52 - cert_w (see rel_quant_f64); cert_w = 0: never.
+    uint32_t cert_emin;
+    uint64_t cert_w;
 };
 
 template <typename T>
@@ -161,6 +166,8 @@ __device__ __forceinline__ Consts<T> consts_from_header(const lcq_header* h) {
     c.inv = Ty<T>::from_bits((U)h->inv_bits);
     c.chk = Ty<T>::from_bits((U)h->chk_bits);
     c.all_outliers = h->mode;
+    c.cert_emin = 0;
+    c.cert_w = 0;
     return c;
 }
 
@@ -655,17 +662,13 @@ __device__ __forceinline__ bool abs_quant_f64(double x, const Consts<double>& c,
     return true;
 }
 
-__device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c, int32_t& bin) {
-    const uint64_t u = dbits(x);
-    const uint64_t E = (u >> 52) & 0x7FF;
-    if (E == 0 || E == 0x7FF) return false;  // zero, denormal, Inf, NaN
+// The rest of the float64 REL recipe after the bin b: m = pow2approx(RN(RN(b
+// step) + 1023)), the range test of bb, m/2 <= a <= 2m, and |a - m| <=
+// RN(min(a, m) chk) with that product normal (exact rescale below 2^-511).
+// Out of line: rel_quant_f64 calls it only where the outcome is not certain.
+static __device__ __noinline__ bool rel_check_f64(uint64_t u, int32_t b, double step, double chk) {
     const uint64_t ua = clear_sign(u);
-    const double q = __dmul_rn(dfrom(log2approx_dbits(u)), c.inv);
-    const uint64_t uq = clear_sign(dbits(q));
-    if (!(uq < 0x41C0000000000000ull)) return false;  // !(|q| < 2^29)
-    const int32_t b = rint_d_small(dbits(q));
-    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
-    const double Lr = __dmul_rn(dfrom(int_to_dbits(b)), c.scale);
+    const double Lr = __dmul_rn(dfrom(int_to_dbits(b)), step);
     const double bb = __dadd_rn(Lr, 1023.0);
     const uint64_t ubb = dbits(bb);
     if (!(ubb >= 0x3FF0000000000000ull && ubb < 0x409FFC0000000000ull)) return false;  // 1 <= bb < 2047
@@ -674,16 +677,42 @@ __device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c,
     if (!(ua <= um + (1ull << 52) && um <= ua + (1ull << 52))) return false;
     const uint64_t ud = absdiff_close_dbits(ua, um);
     const uint64_t ulo = ua < um ? ua : um;
-    bool ok;
     if (ulo < 0x2000000000000000ull) {  // lo < 2^-511: exact rescale by 2^512 (rare)
         const double sc = 0x1p512;
-        const double t = __dmul_rn(__dmul_rn(dfrom(ulo), sc), c.chk);
-        ok = (t >= DBL_MIN) && (__dmul_rn(dfrom(ud), sc) <= t);
-    } else {
-        const uint64_t ut = dbits(__dmul_rn(dfrom(ulo), c.chk));
-        ok = (ut >= 0x0010000000000000ull) && (ud <= ut);  // t normal, d <= t
+        const double t = __dmul_rn(__dmul_rn(dfrom(ulo), sc), chk);
+        return (t >= DBL_MIN) && (__dmul_rn(dfrom(ud), sc) <= t);
     }
-    if (!ok) return false;
+    const uint64_t ut = dbits(__dmul_rn(dfrom(ulo), chk));
+    return (ut >= 0x0010000000000000ull) && (ud <= ut);  // t normal, d <= t
+}
+
+// REL on float64.  q = RN(L inv), L = log2approx(a), and b = rint(q) as
+// always; the rest of the check runs only where its outcome is not certain.
+// With a = 2^(E-1023) (1 + f), f = M 2^-52, log2approx's exact value plus
+// 1023 is E + f.  Each later rounding moves the log-domain value by at most:
+// L: 2^-44; q: |L| 2.0001 u <= 2^-42 (u = 2^-53, |L| < 1024); Lr = RN(b step):
+// 2^-43; bb = RN(Lr + 1023): 2^-43.  So bb = E + f + (b - q) step + eps with
+// |eps| < 2^-40 and |b - q| <= 1/2.  If f lies at least step/2 + 2^-40 inside
+// its binade (cert_w <= M < 2^52 - cert_w, cert_w = ceil((step/2 + 2^-40)
+// 2^52)), floor(bb) = E: bb is in range, m = 2^(E-1023) (1 + frac(bb)) is in
+// a's binade (so m/2 <= a <= 2m and a - m is exact) and
+// |a - m| <= 2^(E-1023) (step/2 + 2^-40).  The host sets cert_w only if
+// chk - step/2 >= 2^-39, so that this is at most 2^(E-1023) chk (1 - u) <=
+// RN(min(a, m) chk) = t; cert_emin = max(512, 1027 - exponent field of chk)
+// keeps min(a, m) >= 2^-511 (no rescale) and t normal.  The acceptance test
+// then passes.
+__device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c, int32_t& bin) {
+    const uint64_t u = dbits(x);
+    const uint64_t E = (u >> 52) & 0x7FF;
+    if (E == 0 || E == 0x7FF) return false;  // zero, denormal, Inf, NaN
+    const double q = __dmul_rn(dfrom(log2approx_dbits(u)), c.inv);
+    const uint64_t uq = clear_sign(dbits(q));
+    if (!(uq < 0x41C0000000000000ull)) return false;  // !(|q| < 2^29)
+    const int32_t b = rint_d_small(dbits(q));
+    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
+    const uint64_t M = u & kD_MANT;
+    const bool sure = c.cert_w != 0 && E >= c.cert_emin && M >= c.cert_w && M < (1ull << 52) - c.cert_w;
+    if (!sure && !rel_check_f64(u, b, c.scale, c.chk)) return false;
     bin = (int32_t)(((uint32_t)b << 1) | (uint32_t)(u >> 63));
     return true;
 }

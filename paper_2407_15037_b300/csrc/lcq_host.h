@@ -9,8 +9,10 @@
 namespace lcq {
 
 // ABS/REL constants of Sec. 2.2 and the REL reading, as the raw bits stored
-// in lcq_header (ebT, scale, inv, chk); false if the bound is unusable.
-bool host_consts(lcq_dtype dtype, lcq_bound_type bound, double eb, uint64_t bits[4]);
+// in lcq_header (ebT, scale, inv, chk), and the certainty bounds of the
+// float64 REL check (0 otherwise); false if the bound is unusable.
+bool host_consts(lcq_dtype dtype, lcq_bound_type bound, double eb, uint64_t bits[4],
+                 uint64_t* cert_w = nullptr, uint32_t* cert_emin = nullptr);
 
 // Validation shared by lcq_quantize and the batch planner.
 lcq_status check_quantize_args(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* d_in,

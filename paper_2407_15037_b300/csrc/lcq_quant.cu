@@ -804,6 +804,24 @@ bool abs_consts_host<double>(double eb, Consts<double>& c) {
 
 // REL constants: log-domain half step lb = RN(e / RN(1 + e)), step = 2 lb,
 // inv = RN(1/step), acceptance factor chk = RN(e (1 - 2^-p)), e = RD_T(eb).
+// The certainty bounds of the float64 REL check (rel_quant_f64): cert_w =
+// ceil((step/2 + 2^-40) 2^52) and cert_emin = max(512, 1027 - exponent field
+// of chk), or cert_w = 0 unless chk - step/2 >= 2^-39.  With step/2 <= chk <=
+// step the subtraction is exact (Sterbenz); otherwise the test is off.
+void rel_cert_host(double step, double chk, uint64_t* cert_w, uint32_t* cert_emin) {
+    *cert_w = 0;
+    *cert_emin = 0;
+    if (!(chk <= step) || !(chk - 0.5 * step >= 0x1p-39)) return;
+    const double v = std::ceil(std::ldexp(step, 51));  // step/2 in units of 2^-52, rounded up
+    if (!(v < 0x1p50)) return;
+    const uint64_t w = (uint64_t)v + 4096;                // + 2^-40 in units of 2^-52
+    uint64_t cb;
+    std::memcpy(&cb, &chk, 8);
+    const int ec = (int)(cb >> 52);
+    *cert_w = w;
+    *cert_emin = (uint32_t)(1027 - ec > 512 ? 1027 - ec : 512);
+}
+
 template <typename T>
 static bool rel_consts_host(double eb, Consts<T>& c);
 
@@ -818,6 +836,7 @@ bool rel_consts_host<float>(double eb, Consts<float>& c) {
     const float chk = e * 0x1.fffffcp-1f;
     if (!is_normal_f(lb) || !is_normal_f(step) || !is_normal_f(inv) || !is_normal_f(chk)) return false;
     c.ebT = e; c.scale = step; c.inv = inv; c.chk = chk; c.all_outliers = 0;
+    c.cert_w = 0; c.cert_emin = 0;
     return true;
 }
 
@@ -832,6 +851,7 @@ bool rel_consts_host<double>(double eb, Consts<double>& c) {
     const double chk = e * 0x1.ffffffffffffep-1;
     if (!is_normal_d(lb) || !is_normal_d(step) || !is_normal_d(inv) || !is_normal_d(chk)) return false;
     c.ebT = e; c.scale = step; c.inv = inv; c.chk = chk; c.all_outliers = 0;
+    rel_cert_host(step, chk, &c.cert_w, &c.cert_emin);
     return true;
 }
 
@@ -1004,16 +1024,21 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
     return LCQ_OK;
 }
 
-bool host_consts(lcq_dtype dtype, lcq_bound_type bound, double eb, uint64_t bits[4]) {
+bool host_consts(lcq_dtype dtype, lcq_bound_type bound, double eb, uint64_t bits[4], uint64_t* cert_w,
+                 uint32_t* cert_emin) {
     if (dtype == LCQ_F32) {
         Consts<float> c{};
         const bool ok = bound == LCQ_REL ? rel_consts_host<float>(eb, c) : abs_consts_host<float>(eb, c);
         bits[0] = bits_host(c.ebT); bits[1] = bits_host(c.scale); bits[2] = bits_host(c.inv); bits[3] = bits_host(c.chk);
+        if (cert_w) *cert_w = c.cert_w;
+        if (cert_emin) *cert_emin = c.cert_emin;
         return ok;
     }
     Consts<double> c{};
     const bool ok = bound == LCQ_REL ? rel_consts_host<double>(eb, c) : abs_consts_host<double>(eb, c);
     bits[0] = bits_host(c.ebT); bits[1] = bits_host(c.scale); bits[2] = bits_host(c.inv); bits[3] = bits_host(c.chk);
+    if (cert_w) *cert_w = c.cert_w;
+    if (cert_emin) *cert_emin = c.cert_emin;
     return ok;
 }
 

@@ -261,6 +261,29 @@ def test_f64_values_near_the_check_threshold(bound, eb):
     compare(torch.from_numpy(x).to(DEV), bound, eb)
 
 
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-5, 1e-6, 1e-7])
+def test_f64_rel_values_near_the_binade_margin(eb):
+    """float64 REL skips the rest of its check where the reconstruction
+    provably stays in the value's binade and passes (mantissa at least
+    step/2 + 2^-40 inside the binade, exponent high enough); values on both
+    sides of that margin, at both ends of the binade, over a wide range of
+    exponents (around 2^-511 and the smallest normals too) must still match
+    the oracle, with the margin on (eb >= ~1e-6) and off (smaller eb)."""
+    rng = np.random.default_rng(int(-np.log10(eb)))
+    step = 2 * eb / (1 + eb)
+    n = 6000
+    f0 = step / 2 + 2.0 ** -40
+    fr = []
+    for d in (-4.0, -1.0, -2.0 ** -10, 0.0, 2.0 ** -10, 1.0, 4.0):
+        off = d * 2.0 ** -40 + rng.random(n) * 2.0 ** -45
+        fr += [f0 + off, 1.0 - f0 - off]
+    fr.append(rng.random(n))
+    f = np.clip(np.concatenate(fr), 0.0, np.nextafter(1.0, 0.0))
+    e = np.concatenate([rng.integers(-1020, 1023, f.size // 2), rng.integers(-515, -505, f.size - f.size // 2)])
+    x = np.ldexp(1.0 + f, e) * rng.choice([-1.0, 1.0], f.size)
+    compare(torch.from_numpy(x).to(DEV), "rel", eb)
+
+
 # --------------------------------------------------------- full sizes ----
 
 @pytest.mark.parametrize("bound", BOUNDS)
