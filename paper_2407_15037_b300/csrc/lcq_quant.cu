@@ -56,6 +56,7 @@ constexpr Variant kVariants[] = {
     {4, 4, 4, 3},  // 3
     {2, 6, 8, 4},  // 4: 8 KB float stages, 4 CTAs/SM
     {8, 2, 4, 2},  // 5
+    {2, 3, 8, 4},  // 6: 8 KB float / 16 KB double stages: 4 CTAs/SM also for float64
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -725,7 +726,8 @@ static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
     case 2: return CALL(kVariants[2].vpt, kVariants[2].stages, kVariants[2].sub, kVariants[2].minb); \
     case 3: return CALL(kVariants[3].vpt, kVariants[3].stages, kVariants[3].sub, kVariants[3].minb); \
     case 4: return CALL(kVariants[4].vpt, kVariants[4].stages, kVariants[4].sub, kVariants[4].minb); \
-    case 5: return CALL(kVariants[5].vpt, kVariants[5].stages, kVariants[5].sub, kVariants[5].minb);
+    case 5: return CALL(kVariants[5].vpt, kVariants[5].stages, kVariants[5].sub, kVariants[5].minb); \
+    case 6: return CALL(kVariants[6].vpt, kVariants[6].stages, kVariants[6].sub, kVariants[6].minb);
 
 template <typename T, int MODE>
 static cudaError_t launch_quantize_variant(int v, const QParams<T>& p, cudaStream_t st) {
@@ -762,7 +764,7 @@ static cudaError_t launch_ablation(const QParams<T>& p, cudaStream_t st) {
 
 // Selected variant per kernel kind (0 quantize, 1 dequantize), dtype, bound type.
 // Defaults from autotuning on a B300 (float32 512^3 field, float64 256^3 field).
-static int g_variant[2][2][3] = {{{1, 3, 1}, {2, 2, 2}}, {{5, 5, 5}, {2, 2, 2}}};
+static int g_variant[2][2][3] = {{{1, 3, 1}, {6, 6, 6}}, {{5, 5, 5}, {2, 2, 2}}};
 
 // RD_f32(d): the largest float not above d.
 static float rd_f32_host(double d) {
