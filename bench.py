@@ -114,6 +114,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def step_config(world):
+    """The workload of one step (both arms report the same)."""
+    return {"workload": WORKLOAD, "n_values": SHAPE[0] * SHAPE[1] * SHAPE[2], "bound_types": BOUNDS,
+            "bounds": EBS, "parallelism": "replicas x%d" % world,
+            "l2": "inputs larger than L2 (512 MiB per pass vs 126 MB), no flush"}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -178,7 +185,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_values": n},
+            "data": "synthetic", "config": step_config(world),
             "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -430,9 +437,7 @@ def run_ours(args, world, rank, local):
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_values": n, "bound_types": BOUNDS, "bounds": EBS,
-                       "parallelism": "replicas x%d" % world,
-                       "l2": "inputs larger than L2 (512 MiB per pass vs 126 MB), no flush"},
+            "config": step_config(world),
             "pct_hbm_peak_in": 100 * value / world / hbm_peak,
             "roofline": {"bound": "hbm", "kernel": "k_quantize<float,ABS> (ABS/NOA calls)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
