@@ -562,6 +562,15 @@ __device__ __forceinline__ int32_t rint_d_small_clear(uint64_t u, bool& clear) {
     return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
 }
 
+// The double with the exact value of integer i, |i| < 2^20 (32-bit work).
+__device__ __forceinline__ uint64_t small_int_to_dbits(int32_t i) {
+    if (i == 0) return 0;
+    const uint32_t a = (uint32_t)(i < 0 ? -i : i);
+    const int top = 31 - __clz((int)a);
+    const uint32_t hi = ((uint32_t)(top + 1023) << 20) | ((a << (20 - top)) & 0xFFFFFu);
+    return ((uint64_t)(hi | (i < 0 ? 0x80000000u : 0u)) << 32);
+}
+
 // The double with the exact value of integer i, |i| < 2^53.
 __device__ __forceinline__ uint64_t int_to_dbits(int64_t i) {
     if (i == 0) return 0;
@@ -705,7 +714,10 @@ __device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c,
     const uint64_t u = dbits(x);
     const uint64_t E = (u >> 52) & 0x7FF;
     if (E == 0 || E == 0x7FF) return false;  // zero, denormal, Inf, NaN
-    const double q = __dmul_rn(dfrom(log2approx_dbits(u)), c.inv);
+    // log2approx (Sec. 3.2): 1.M + (E - 1024), one FP64 addition (the FP64 pipe
+    // has room here; the integer form, log2approx_dbits, costs ~28 instructions)
+    const double L = __dadd_rn(dfrom(0x3FF0000000000000ull | (u & kD_MANT)), dfrom(small_int_to_dbits((int32_t)E - 1024)));
+    const double q = __dmul_rn(L, c.inv);
     const uint64_t uq = clear_sign(dbits(q));
     if (!(uq < 0x41C0000000000000ull)) return false;  // !(|q| < 2^29)
     const int32_t b = rint_d_small(dbits(q));
