@@ -239,6 +239,35 @@ lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double 
                              cudaStream_t stream);
 
 /*
+ * Many host arrays end to end (no counterpart in the paper): each item is
+ * quantized exactly as lcq_quantize_host would quantize it, and the items
+ * are pipelined across two device stage slots, so that the upload of item
+ * j + 1 overlaps the download of item j.  Items must have n > 0.  d_stage:
+ * at least lcq_host_batch_stage_size(items, count) device bytes (two slots
+ * of the largest item); d_ws: lcq_workspace_size of the largest n.  Each
+ * item's status receives its result; the call returns the first error, or
+ * LCQ_OK, once everything is on the host.  Calls for one device run one at
+ * a time (the copy streams are the library's).
+ */
+typedef struct lcq_host_item {
+    uint32_t dtype;            /* lcq_dtype */
+    uint32_t bound_type;       /* lcq_bound_type */
+    double eb;
+    const void* h_in;          /* host input (page-locked for full bandwidth) */
+    uint64_t n;
+    int32_t* h_bins;           /* host outputs, as lcq_quantize_host */
+    uint32_t* h_mask;
+    void* h_outliers;
+    uint64_t outlier_capacity;
+    lcq_header* h_hdr;
+    int32_t status;            /* out: lcq_status of this item */
+    uint32_t reserved;
+} lcq_host_item;
+size_t lcq_host_batch_stage_size(const lcq_host_item* items, uint32_t count);
+lcq_status lcq_quantize_host_batch(lcq_host_item* items, uint32_t count, void* d_stage, size_t stage_bytes,
+                                   void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
  * Batched quantization (no counterpart in the paper, which quantizes one file
  * at a time): many arrays of different sizes, data types, bound types and
  * bounds in one persistent launch.  Each array gets exactly the result that

@@ -864,8 +864,9 @@ static uint64_t bits_host(T v) {
     return u;
 }
 
-// Pipelined host <-> device copies around quantize_impl (lcq_quantize_host):
-// the input goes up in chunks on its own stream, each chunk is quantized as
+// Pipelined host <-> device copies around quantize_impl (lcq_quantize_host
+// and lcq_quantize_host_batch): the input goes up in chunks on its own
+// stream (host_io_upload, enqueued by the caller), each chunk is quantized as
 // soon as it has arrived, and its bins and mask words go down on a third
 // stream while later chunks are still moving up.
 struct HostIO {
@@ -877,28 +878,28 @@ struct HostIO {
     uint32_t* h_mask;
     const uint32_t* d_mask;
     cudaStream_t h2d, d2h;
-    cudaEvent_t* ev;  // 2 per chunk + 1
-    uint64_t chunk;   // values per chunk, a multiple of 32
+    cudaEvent_t* up_ev;    // one per chunk: its upload has finished
+    cudaEvent_t* done_ev;  // one per chunk: its quantization has finished
+    uint64_t chunk;        // values per chunk, a multiple of 32
 };
 
-static bool host_io_upload(const HostIO& io, uint64_t n, cudaStream_t st) {
-    const uint64_t K = (n + io.chunk - 1) / io.chunk;
-    if (cudaEventRecord(io.ev[2 * K], st) != cudaSuccess) return false;
-    if (cudaStreamWaitEvent(io.h2d, io.ev[2 * K], 0) != cudaSuccess) return false;
-    if (cudaStreamWaitEvent(io.d2h, io.ev[2 * K], 0) != cudaSuccess) return false;
+static uint64_t host_io_chunks(uint64_t n, uint64_t chunk) { return (n + chunk - 1) / chunk; }
+
+static bool host_io_upload(const HostIO& io, uint64_t n) {
+    const uint64_t K = host_io_chunks(n, io.chunk);
     for (uint64_t i = 0; i < K; i++) {
         const uint64_t off = i * io.chunk, len = n - off < io.chunk ? n - off : io.chunk;
         if (cudaMemcpyAsync(io.d_in + off * io.es, io.h_in + off * io.es, len * io.es, cudaMemcpyHostToDevice,
                             io.h2d) != cudaSuccess ||
-            cudaEventRecord(io.ev[2 * i], io.h2d) != cudaSuccess)
+            cudaEventRecord(io.up_ev[i], io.h2d) != cudaSuccess)
             return false;
     }
     return true;
 }
 
 static bool host_io_download(const HostIO& io, uint64_t i, uint64_t off, uint64_t len, cudaStream_t st) {
-    if (cudaEventRecord(io.ev[2 * i + 1], st) != cudaSuccess) return false;
-    if (cudaStreamWaitEvent(io.d2h, io.ev[2 * i + 1], 0) != cudaSuccess) return false;
+    if (cudaEventRecord(io.done_ev[i], st) != cudaSuccess) return false;
+    if (cudaStreamWaitEvent(io.d2h, io.done_ev[i], 0) != cudaSuccess) return false;
     const uint64_t w0 = off / 32, w1 = (off + len + 31) / 32;
     return cudaMemcpyAsync(io.h_bins + off, io.d_bins + off, len * 4, cudaMemcpyDeviceToHost, io.d2h) ==
                cudaSuccess &&
@@ -928,10 +929,10 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz);
 
     if (io) {
-        if (n == 0 || !host_io_upload(*io, n, st)) return LCQ_ERR_CUDA;
         // NOA needs the whole input for its range before any binning
-        const uint64_t K = (n + io->chunk - 1) / io->chunk;
-        if (noa && !given && cudaStreamWaitEvent(st, io->ev[2 * (K - 1)], 0) != cudaSuccess) return LCQ_ERR_CUDA;
+        if (n == 0) return LCQ_ERR_CUDA;
+        const uint64_t K = host_io_chunks(n, io->chunk);
+        if (noa && !given && cudaStreamWaitEvent(st, io->up_ev[K - 1], 0) != cudaSuccess) return LCQ_ERR_CUDA;
     }
     if (noa && given) {
         k_noa_given<T><<<1, 1, 0, st>>>(hdr, given[0] != 0.0, (T)given[1], (T)given[2], eb, dtype, n == 0);
@@ -959,7 +960,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     const uint64_t chunk = io ? io->chunk : kChunk;
     for (uint64_t off = 0; off < n; off += chunk) {
         const uint64_t len = (n - off) < chunk ? (n - off) : chunk;
-        if (io && !(noa && !given) && cudaStreamWaitEvent(st, io->ev[2 * (off / chunk)], 0) != cudaSuccess)
+        if (io && !(noa && !given) && cudaStreamWaitEvent(st, io->up_ev[off / chunk], 0) != cudaSuccess)
             return LCQ_ERR_CUDA;
         QParams<T> p;
         p.in = in + off;
@@ -1257,70 +1258,222 @@ size_t lcq_host_stage_size(lcq_dtype dtype, uint64_t n, uint64_t outlier_capacit
            up(sizeof(lcq_header));
 }
 
+namespace {
+
+// Device layout of one stage slot: input, bins, mask words, outliers, header.
+struct StageSlot {
+    char* d_in;
+    int32_t* d_bins;
+    uint32_t* d_mask;
+    void* d_out;
+    lcq_header* d_hdr;
+};
+
+size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+StageSlot stage_slot(void* base, size_t es, uint64_t n, uint64_t cap) {
+    StageSlot t;
+    t.d_in = (char*)base;
+    t.d_bins = (int32_t*)(t.d_in + up256(n * es));
+    t.d_mask = (uint32_t*)((char*)t.d_bins + up256(n * 4));
+    t.d_out = (char*)t.d_mask + up256(((n + 31) / 32) * 4);
+    t.d_hdr = (lcq_header*)((char*)t.d_out + up256(cap * es));
+    return t;
+}
+
+lcq_status check_host_item(lcq_dtype dtype, lcq_bound_type bound_type, double eb, const void* h_in, uint64_t n,
+                           const int32_t* h_bins, const uint32_t* h_mask, const void* h_outliers,
+                           uint64_t outlier_capacity, const lcq_header* h_hdr) {
+    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
+    if (bound_type != LCQ_ABS && bound_type != LCQ_REL && bound_type != LCQ_NOA) return LCQ_ERR_ARG;
+    if (!h_hdr) return LCQ_ERR_ARG;
+    if (n > 0 && (!h_in || !h_bins || !h_mask)) return LCQ_ERR_ARG;
+    if (outlier_capacity > 0 && !h_outliers) return LCQ_ERR_ARG;
+    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return LCQ_ERR_BOUND;
+    return LCQ_OK;
+}
+
+// Enqueue the quantization of one host item whose upload (io.up_ev) is
+// already enqueued: the chunked launches with their bin / mask downloads,
+// then the header download, after which `hdr_ev` is recorded on io.d2h.
+lcq_status enqueue_host_item(lcq_dtype dtype, lcq_bound_type bt, double eb, uint64_t n, const StageSlot& t,
+                             uint64_t cap, lcq_header* h_hdr, const HostIO& io, cudaEvent_t end_ev,
+                             cudaEvent_t hdr_ev, void* d_ws, cudaStream_t st) {
+    void* d_outl = cap ? t.d_out : nullptr;
+    lcq_status s;
+    if (dtype == LCQ_F32)
+        s = quantize_impl<float>(bt, eb, (const float*)t.d_in, n, t.d_bins, t.d_mask, d_outl, cap, t.d_hdr, d_ws,
+                                 st, nullptr, 0, &io);
+    else
+        s = quantize_impl<double>(bt, eb, (const double*)t.d_in, n, t.d_bins, t.d_mask, d_outl, cap, t.d_hdr,
+                                  d_ws, st, nullptr, 0, &io);
+    const bool ok = cudaEventRecord(end_ev, st) == cudaSuccess &&
+                    cudaStreamWaitEvent(io.d2h, end_ev, 0) == cudaSuccess &&
+                    cudaMemcpyAsync(h_hdr, t.d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, io.d2h) ==
+                        cudaSuccess &&
+                    cudaEventRecord(hdr_ev, io.d2h) == cudaSuccess;
+    if (s != LCQ_OK) return s;
+    return ok ? LCQ_OK : LCQ_ERR_CUDA;
+}
+
+// After the header of an item is on the host: download its outliers.
+lcq_status finish_host_item(const lcq_header* h_hdr, const StageSlot& t, size_t es, void* h_outliers, uint64_t cap,
+                            cudaStream_t d2h) {
+    const uint64_t cnt = h_hdr->outlier_count < cap ? h_hdr->outlier_count : cap;
+    if (cnt && cudaMemcpyAsync(h_outliers, t.d_out, cnt * es, cudaMemcpyDeviceToHost, d2h) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    return LCQ_OK;
+}
+
+lcq_status host_status(const lcq_header* h) {
+    if (h->status & LCQ_STATUS_TIMEOUT) return LCQ_ERR_TIMEOUT;
+    if (h->status & LCQ_STATUS_CAPACITY) return LCQ_ERR_CAPACITY;
+    return LCQ_OK;
+}
+
+}  // namespace
+
 lcq_status lcq_quantize_host(lcq_dtype dtype, lcq_bound_type bound_type, double eb,
                              const void* h_in, uint64_t n, int32_t* h_bins, uint32_t* h_mask,
                              void* h_outliers, uint64_t outlier_capacity, lcq_header* h_hdr,
                              void* d_stage, size_t stage_bytes, void* d_ws, size_t ws_bytes,
                              cudaStream_t stream) {
-    if (dtype != LCQ_F32 && dtype != LCQ_F64) return LCQ_ERR_ARG;
-    if (bound_type != LCQ_ABS && bound_type != LCQ_REL && bound_type != LCQ_NOA) return LCQ_ERR_ARG;
-    if (!h_hdr || !d_stage || !aligned16(d_stage)) return LCQ_ERR_ARG;
-    if (n > 0 && (!h_in || !h_bins || !h_mask)) return LCQ_ERR_ARG;
-    if (outlier_capacity > 0 && !h_outliers) return LCQ_ERR_ARG;
-    if (n >= (1ull << 40)) return LCQ_ERR_ARG;
-    if (!(eb > 0.0) || !std::isfinite(eb)) return LCQ_ERR_BOUND;
+    lcq_status s = check_host_item(dtype, bound_type, eb, h_in, n, h_bins, h_mask, h_outliers, outlier_capacity,
+                                   h_hdr);
+    if (s != LCQ_OK) return s;
+    if (!d_stage || !aligned16(d_stage)) return LCQ_ERR_ARG;
     if (stage_bytes < lcq_host_stage_size(dtype, n, outlier_capacity)) return LCQ_ERR_WORKSPACE;
     if (!d_ws || !aligned16(d_ws)) return LCQ_ERR_ARG;
     if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
     const size_t es = dtype == LCQ_F64 ? 8 : 4;
-    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    char* base = (char*)d_stage;
-    char* d_in = base;
-    int32_t* d_bins = (int32_t*)(base + up(n * es));
-    uint32_t* d_mask = (uint32_t*)((char*)d_bins + up(n * 4));
-    void* d_out = (char*)d_mask + up(((n + 31) / 32) * 4);
-    lcq_header* d_hdr = (lcq_header*)((char*)d_out + up(outlier_capacity * es));
-    void* d_outl = outlier_capacity ? d_out : nullptr;
-    lcq_status s;
+    const StageSlot t = stage_slot(d_stage, es, n, outlier_capacity);
     if (n == 0) {
-        s = lcq_quantize(dtype, bound_type, eb, nullptr, 0, d_bins, d_mask, d_outl, outlier_capacity, d_hdr,
-                         d_ws, ws_bytes, stream);
+        s = lcq_quantize(dtype, bound_type, eb, nullptr, 0, t.d_bins, t.d_mask,
+                         outlier_capacity ? t.d_out : nullptr, outlier_capacity, t.d_hdr, d_ws, ws_bytes, stream);
         if (s != LCQ_OK) return s;
-        if (cudaMemcpyAsync(h_hdr, d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        if (cudaMemcpyAsync(h_hdr, t.d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
             cudaStreamSynchronize(stream) != cudaSuccess)
             return LCQ_ERR_CUDA;
         return LCQ_OK;
     }
     // the copy streams and events of this device, held for the whole call
-    const uint64_t K = (n + kHostChunk - 1) / kHostChunk;
+    const uint64_t K = host_io_chunks(n, kHostChunk);
     HostPipe* pipe = nullptr;
     std::unique_lock<std::mutex> lock;
-    if (host_pipe(2 * K + 2, &pipe, lock) != LCQ_OK) return LCQ_ERR_CUDA;
-    HostIO io{(const char*)h_in, d_in, es, h_bins, d_bins, h_mask, d_mask, pipe->h2d, pipe->d2h,
-              pipe->ev.data(), kHostChunk};
-    if (dtype == LCQ_F32)
-        s = quantize_impl<float>(bound_type, eb, (const float*)d_in, n, d_bins, d_mask, d_outl, outlier_capacity,
-                                 d_hdr, d_ws, stream, nullptr, 0, &io);
-    else
-        s = quantize_impl<double>(bound_type, eb, (const double*)d_in, n, d_bins, d_mask, d_outl,
-                                  outlier_capacity, d_hdr, d_ws, stream, nullptr, 0, &io);
-    // drain both copy streams whatever happened, then report
-    const bool ok_end = cudaEventRecord(io.ev[2 * K + 1], stream) == cudaSuccess &&
-                        cudaStreamWaitEvent(io.d2h, io.ev[2 * K + 1], 0) == cudaSuccess &&
-                        cudaMemcpyAsync(h_hdr, d_hdr, sizeof(lcq_header), cudaMemcpyDeviceToHost, io.d2h) ==
-                            cudaSuccess;
-    const bool ok_sync = cudaStreamSynchronize(io.h2d) == cudaSuccess &&
-                         cudaStreamSynchronize(io.d2h) == cudaSuccess &&
-                         cudaStreamSynchronize(stream) == cudaSuccess;
+    if (host_pipe(2 * K + 3, &pipe, lock) != LCQ_OK) return LCQ_ERR_CUDA;
+    cudaEvent_t* ev = pipe->ev.data();
+    HostIO io{(const char*)h_in, t.d_in, es, h_bins, t.d_bins, h_mask, t.d_mask, pipe->h2d, pipe->d2h,
+              ev, ev + K, kHostChunk};
+    cudaEvent_t start_ev = ev[2 * K], end_ev = ev[2 * K + 1], hdr_ev = ev[2 * K + 2];
+    // the copies start after the work already on `stream`
+    bool ok = cudaEventRecord(start_ev, stream) == cudaSuccess &&
+              cudaStreamWaitEvent(io.h2d, start_ev, 0) == cudaSuccess &&
+              cudaStreamWaitEvent(io.d2h, start_ev, 0) == cudaSuccess && host_io_upload(io, n);
+    s = ok ? enqueue_host_item(dtype, bound_type, eb, n, t, outlier_capacity, h_hdr, io, end_ev, hdr_ev, d_ws,
+                               stream)
+           : LCQ_ERR_CUDA;
+    // drain the copy streams whatever happened, then report
+    ok = cudaStreamSynchronize(io.h2d) == cudaSuccess && cudaStreamSynchronize(io.d2h) == cudaSuccess &&
+         cudaStreamSynchronize(stream) == cudaSuccess;
     if (s != LCQ_OK) return s;
-    if (!ok_end || !ok_sync) return LCQ_ERR_CUDA;
-    const uint64_t cnt = h_hdr->outlier_count < outlier_capacity ? h_hdr->outlier_count : outlier_capacity;
-    if (cnt && (cudaMemcpyAsync(h_outliers, d_out, cnt * es, cudaMemcpyDeviceToHost, io.d2h) != cudaSuccess ||
-                cudaStreamSynchronize(io.d2h) != cudaSuccess))
+    if (!ok) return LCQ_ERR_CUDA;
+    if (finish_host_item(h_hdr, t, es, h_outliers, outlier_capacity, io.d2h) != LCQ_OK ||
+        cudaStreamSynchronize(io.d2h) != cudaSuccess)
         return LCQ_ERR_CUDA;
-    if (h_hdr->status & LCQ_STATUS_TIMEOUT) return LCQ_ERR_TIMEOUT;
-    if (h_hdr->status & LCQ_STATUS_CAPACITY) return LCQ_ERR_CAPACITY;
-    return LCQ_OK;
+    return host_status(h_hdr);
+}
+
+size_t lcq_host_batch_stage_size(const lcq_host_item* items, uint32_t count) {
+    size_t mx = 0;
+    for (uint32_t i = 0; items && i < count; i++) {
+        const size_t b = lcq_host_stage_size((lcq_dtype)items[i].dtype, items[i].n, items[i].outlier_capacity);
+        mx = b > mx ? b : mx;
+    }
+    return count > 1 ? 2 * mx : mx;
+}
+
+lcq_status lcq_quantize_host_batch(lcq_host_item* items, uint32_t count, void* d_stage, size_t stage_bytes,
+                                   void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!items || count == 0) return LCQ_ERR_ARG;
+    if (!d_stage || !aligned16(d_stage) || !d_ws || !aligned16(d_ws)) return LCQ_ERR_ARG;
+    uint64_t nmax = 0, ksum = 0;
+    lcq_status first = LCQ_OK;
+    for (uint32_t i = 0; i < count; i++) {
+        lcq_host_item& it = items[i];
+        it.status = check_host_item((lcq_dtype)it.dtype, (lcq_bound_type)it.bound_type, it.eb, it.h_in, it.n,
+                                    it.h_bins, it.h_mask, it.h_outliers, it.outlier_capacity, it.h_hdr);
+        if (it.status == LCQ_OK && it.n == 0) it.status = LCQ_ERR_ARG;  // empty arrays: use lcq_quantize_host
+        if (it.status != LCQ_OK) return (lcq_status)it.status;
+        nmax = it.n > nmax ? it.n : nmax;
+        ksum += host_io_chunks(it.n, kHostChunk);
+    }
+    if (stage_bytes < lcq_host_batch_stage_size(items, count)) return LCQ_ERR_WORKSPACE;
+    if (ws_bytes < ws_size(nmax)) return LCQ_ERR_WORKSPACE;
+    const size_t slot_bytes = count > 1 ? lcq_host_batch_stage_size(items, count) / 2 : stage_bytes;
+    HostPipe* pipe = nullptr;
+    std::unique_lock<std::mutex> lock;
+    // per item: an upload and a done event per chunk, end, header and slot-free events; one start event
+    if (host_pipe(2 * ksum + 3 * (uint64_t)count + 1, &pipe, lock) != LCQ_OK) return LCQ_ERR_CUDA;
+    cudaEvent_t* ev = pipe->ev.data();
+    cudaEvent_t start_ev = ev[0];
+    size_t evi = 1;
+    std::vector<StageSlot> slot(count);
+    std::vector<cudaEvent_t> hdr_ev(count), free_ev(count);
+    bool ok = cudaEventRecord(start_ev, stream) == cudaSuccess &&
+              cudaStreamWaitEvent(pipe->h2d, start_ev, 0) == cudaSuccess &&
+              cudaStreamWaitEvent(pipe->d2h, start_ev, 0) == cudaSuccess;
+    uint32_t enq = 0;  // items whose work is enqueued
+    for (uint32_t j = 0; ok && j < count; j++) {
+        lcq_host_item& it = items[j];
+        const lcq_dtype dt = (lcq_dtype)it.dtype;
+        const size_t es = dt == LCQ_F64 ? 8 : 4;
+        const uint64_t K = host_io_chunks(it.n, kHostChunk);
+        slot[j] = stage_slot((char*)d_stage + (j & 1) * slot_bytes, es, it.n, it.outlier_capacity);
+        HostIO io{(const char*)it.h_in, slot[j].d_in, es, it.h_bins, slot[j].d_bins, it.h_mask, slot[j].d_mask,
+                  pipe->h2d, pipe->d2h, ev + evi, ev + evi + K, kHostChunk};
+        evi += 2 * K;
+        cudaEvent_t end_ev = ev[evi++];
+        hdr_ev[j] = ev[evi++];
+        free_ev[j] = ev[evi++];
+        // the slot is free once item j-2 is completely downloaded
+        if (j >= 2 && cudaStreamWaitEvent(pipe->h2d, free_ev[j - 2], 0) != cudaSuccess) { ok = false; break; }
+        if (!host_io_upload(io, it.n)) { ok = false; break; }
+        // while item j moves up, item j-1's outliers go down
+        if (j >= 1) {
+            lcq_host_item& pv = items[j - 1];
+            if (cudaEventSynchronize(hdr_ev[j - 1]) != cudaSuccess ||
+                finish_host_item(pv.h_hdr, slot[j - 1], pv.dtype == LCQ_F64 ? 8 : 4, pv.h_outliers,
+                                 pv.outlier_capacity, pipe->d2h) != LCQ_OK ||
+                cudaEventRecord(free_ev[j - 1], pipe->d2h) != cudaSuccess) {
+                ok = false;
+                break;
+            }
+        }
+        it.status = enqueue_host_item(dt, (lcq_bound_type)it.bound_type, it.eb, it.n, slot[j], it.outlier_capacity,
+                                      it.h_hdr, io, end_ev, hdr_ev[j], d_ws, stream);
+        enq = j + 1;
+        if (it.status != LCQ_OK) { ok = false; break; }
+    }
+    if (ok && enq == count) {
+        lcq_host_item& ls = items[count - 1];
+        ok = cudaEventSynchronize(hdr_ev[count - 1]) == cudaSuccess &&
+             finish_host_item(ls.h_hdr, slot[count - 1], ls.dtype == LCQ_F64 ? 8 : 4, ls.h_outliers,
+                              ls.outlier_capacity, pipe->d2h) == LCQ_OK;
+    }
+    const bool ok_sync = cudaStreamSynchronize(pipe->h2d) == cudaSuccess &&
+                         cudaStreamSynchronize(pipe->d2h) == cudaSuccess &&
+                         cudaStreamSynchronize(stream) == cudaSuccess;
+    for (uint32_t j = 0; j < count; j++) {
+        lcq_host_item& it = items[j];
+        if (j >= enq) {
+            if (it.status == LCQ_OK) it.status = LCQ_ERR_CUDA;
+        } else if (it.status == LCQ_OK) {
+            it.status = (ok && ok_sync) ? host_status(it.h_hdr) : LCQ_ERR_CUDA;
+        }
+        if (first == LCQ_OK && it.status != LCQ_OK) first = (lcq_status)it.status;
+    }
+    return first;
 }
 
 int lcq_tune_variant_count(void) { return kNumVariants; }

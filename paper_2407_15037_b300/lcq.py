@@ -58,6 +58,15 @@ class BatchInfo(ctypes.Structure):
     ]
 
 
+class HostItem(ctypes.Structure):
+    """Mirror of struct lcq_host_item."""
+    _fields_ = [("dtype", ctypes.c_uint32), ("bound_type", ctypes.c_uint32), ("eb", ctypes.c_double),
+                ("h_in", ctypes.c_void_p), ("n", ctypes.c_uint64), ("h_bins", ctypes.c_void_p),
+                ("h_mask", ctypes.c_void_p), ("h_outliers", ctypes.c_void_p),
+                ("outlier_capacity", ctypes.c_uint64), ("h_hdr", ctypes.c_void_p),
+                ("status", ctypes.c_int32), ("reserved", ctypes.c_uint32)]
+
+
 class LcqError(RuntimeError):
     def __init__(self, code, what):
         super().__init__("%s failed: %s" % (what, STATUS_NAMES.get(code, str(code))))
@@ -87,6 +96,8 @@ SIGNATURES = {
     "lcq_host_stage_size": ([ctypes.c_int, _u64, _u64], _sz),
     "lcq_quantize_host": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
                            _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_host_batch_stage_size": ([_vp, _u32], _sz),
+    "lcq_quantize_host_batch": ([_vp, _u32, _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
     "lcq_debug_set_scan": ([_u32, _u64], None),
     "lcq_tune_variant_count": ([], ctypes.c_int),
     "lcq_tune_describe": ([ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -455,3 +466,29 @@ def quantize_host(x_host, bound, eb, outputs, stage, ws, stream=None, device=Non
         _stream_ptr(stream, device))
     _check(code, "lcq_quantize_host")
     return outputs
+
+
+def host_items(jobs):
+    """ctypes array of lcq_host_item from (x_host, bound, eb, outputs) tuples."""
+    arr = (HostItem * len(jobs))()
+    for it, (x, bound, eb, o) in zip(arr, jobs):
+        it.dtype, it.bound_type, it.eb = _dtype_code(x), _bound_code(bound), float(eb)
+        it.h_in, it.n = _ptr(x).value, x.numel()
+        it.h_bins, it.h_mask, it.h_outliers = _ptr(o.bins).value, _ptr(o.mask).value, _ptr(o.outliers).value
+        it.outlier_capacity = o.outliers.numel()
+        it.h_hdr = _ptr(o.header).value
+    return arr
+
+
+def host_batch_stage_size(items):
+    return int(lib().lcq_host_batch_stage_size(ctypes.cast(items, _vp), len(items)))
+
+
+def quantize_host_batch(items, stage, ws, stream=None, device=None):
+    """lcq_quantize_host_batch over a host_items() array; blocks until all
+    results are on the host.  Returns the per-item status codes."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    code = lib().lcq_quantize_host_batch(ctypes.cast(items, _vp), len(items), _ptr(stage), stage.numel(), _ptr(ws),
+                                         ws.numel(), _stream_ptr(stream, device))
+    _check(code, "lcq_quantize_host_batch")
+    return [it.status for it in items]

@@ -55,15 +55,17 @@ def test_header_struct_size_matches_c(tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lcq_header),'
                    ' offsetof(lcq_header, outlier_count), offsetof(lcq_header, status),'
                    ' sizeof(lcq_batch_item), sizeof(lcq_batch_info), offsetof(lcq_batch_item, d_hdr));'
-                   'printf("%zu\\n", sizeof(lcq_pred_params));'
+                   'printf("%zu %zu %zu\\n", sizeof(lcq_pred_params), sizeof(lcq_host_item),'
+                   ' offsetof(lcq_host_item, status));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-I", "/usr/local/cuda/include",
                     str(src), "-o", str(exe)], check=True)
-    size, off_cnt, off_st, bi, binfo, off_hdr, pp = map(int, subprocess.run(
+    size, off_cnt, off_st, bi, binfo, off_hdr, pp, hi, off_hs = map(int, subprocess.run(
         [str(exe)], capture_output=True, text=True, check=True).stdout.split())
     from paper_2407_15037_b300 import predictor as PD
     assert pp == PD.PARAMS_BYTES
+    assert hi == ctypes.sizeof(P.lcq.HostItem) and off_hs == P.lcq.HostItem.status.offset
     H = P.Header
     assert size == ctypes.sizeof(H)
     assert off_cnt == H.outlier_count.offset and off_st == H.status.offset

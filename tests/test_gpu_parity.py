@@ -191,6 +191,38 @@ def test_host_entry_point_matches_device_path(bound, dtype, n):
     assert torch.equal(outs.header, qd.header.cpu())
 
 
+def test_host_batch_matches_device_path():
+    """lcq_quantize_host_batch: items of both data types, all bound types,
+    one and several chunks, pipelined over two stage slots; every item gives
+    exactly what the device entry point gives, with its status."""
+    specs = [(torch.float32, "abs", 3 * (1 << 23) + 999), (torch.float64, "rel", 70001),
+             (torch.float32, "noa", (1 << 23) + 32), (torch.float32, "rel", 4096),
+             (torch.float64, "noa", (1 << 23) + 5), (torch.float32, "abs", 1)]
+    jobs, refs = [], []
+    for k, (dt, bound, n) in enumerate(specs):
+        x = synth.smooth_field((n,), dtype=dt, seed=10 + k, device=DEV)
+        x[::3001] = float("nan")
+        xp = x.cpu().pin_memory()
+        idt = torch.int32 if dt == torch.float32 else torch.int64
+        outs = P.Quantized(torch.empty(n, dtype=torch.int32).pin_memory(),
+                           torch.empty((n + 31) // 32, dtype=torch.int32).pin_memory(),
+                           torch.empty(n, dtype=idt).pin_memory(),
+                           torch.empty(P.lcq.HEADER_BYTES, dtype=torch.uint8).pin_memory(), n, dt)
+        jobs.append((xp, bound, 1e-4, outs))
+        refs.append(P.quantize(x, bound, 1e-4))
+    items = P.lcq.host_items(jobs)
+    stage = torch.empty(P.lcq.host_batch_stage_size(items), dtype=torch.uint8, device=DEV)
+    ws = P.new_workspace(max(n for _, _, n in specs), DEV)
+    assert P.lcq.quantize_host_batch(items, stage, ws) == [0] * len(specs)
+    torch.cuda.synchronize()
+    for (xp, bound, eb, outs), qd in zip(jobs, refs):
+        h = qd.read_header()
+        assert torch.equal(outs.bins, qd.bins.cpu())
+        assert torch.equal(outs.mask, qd.mask.cpu())
+        assert torch.equal(outs.outliers[:h.outlier_count], qd.outliers[:h.outlier_count].cpu())
+        assert torch.equal(outs.header, qd.header.cpu())
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_every_tile_shape_variant_matches_oracle(dtype):
     """Every tile shape the autotuner may pick gives the same bits."""
