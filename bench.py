@@ -221,6 +221,60 @@ def link_bandwidth(h_up, h_down, d_buf, dev, reps=4):
             "bytes_per_copy": nb}
 
 
+def run_lossless(P, x, q, ws, dev, stream, reps=5):
+    """The lossless stage after quantization on the float32 512^3 field:
+    bins, or the hierarchical-interpolation residuals of the bins, packed into
+    bit-planes (lcq_pack).  Compression ratio = input bytes / (packed codes +
+    outlier mask + outliers + header); times of encode (residuals + pack) and
+    decode (unpack + reconstruct), each checked to give the bins back."""
+    from paper_2407_15037_b300 import predictor as PD
+    L = P.lcq
+    n = x.numel()
+    N = SHAPE[0]
+    res = {}
+    buf = torch.empty(int(L.lib().lcq_pack_bound(n)), dtype=torch.uint8, device=dev)
+    pws = torch.empty(int(L.lib().lcq_pack_workspace_size(n)), dtype=torch.uint8, device=dev)
+
+    def timed(fn):
+        fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    for bound, eb in (("abs", 1e-3), ("abs", 1e-4), ("rel", 1e-3)):
+        P.quantize_into(x, bound, eb, q, ws, stream)
+        h = q.read_header()
+        side = (n + 31) // 32 * 4 + 4 * h.outlier_count + P.lcq.HEADER_BYTES
+        for pred in (False, True):
+            key = "%s_%g_%s" % (bound, eb, "interp" if pred else "bins")
+            state = {}
+
+            def enc():
+                codes = PD.residuals(q.bins, N) if pred else q.bins
+                state["size"] = L.pack(codes, buf, pws, stream)[1]
+
+            t_enc = timed(enc)
+            size = int(state["size"].item())
+            packed = buf[:size]
+
+            def dec():
+                codes = L.unpack(packed, n, pws, stream, check=False)
+                state["bins"] = PD.reconstruct(codes, N) if pred else codes
+
+            t_dec = timed(dec)
+            assert torch.equal(state["bins"], q.bins), key
+            total = size + side
+            res[key] = {"packed_bytes": size, "total_bytes": total, "ratio": n * 4 / total,
+                        "bits_per_value": 8 * total / n, "encode_ms": t_enc, "decode_ms": t_dec,
+                        "encode_in_GBps": n * 4 / t_enc / 1e6, "decode_out_GBps": n * 4 / t_dec / 1e6}
+    del buf, pws
+    return res
+
+
 def run_ablations(P, x, q, ws, dev, stream, reps=5):
     """The paper's two ablations on the float32 512^3 field: ABS without the
     double-check (Sec. 6, Tables 7-8: time and exact bound violations) and REL
@@ -400,6 +454,7 @@ def run_ours(args, world, rank, local):
 
     if args.extras:
         extra["ablations"] = run_ablations(P, x, q, ws, dev, stream)
+        extra["lossless"] = run_lossless(P, x, q, ws, dev, stream)
         x64 = synth.smooth_field((256, 256, 256), dtype=torch.float64, seed=0, device=dev)
         q64 = P.alloc_outputs(x64.numel(), x64.dtype, dev)
         w64 = P.new_workspace(x64.numel(), dev)

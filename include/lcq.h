@@ -171,6 +171,32 @@ lcq_status lcq_quantize_noa_range(lcq_dtype dtype, double eb, int has_finite, do
                                   lcq_header* d_hdr, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /*
+ * Lossless stage after quantization (no counterpart in the paper, which
+ * hands its bins to LC's lossless stages): bit-plane packing of int32 codes
+ * (bins or predictor residuals).  For n codes in nb = ceil(n/32) blocks of
+ * 32 (the last padded with zeros), z = zigzag(code) = (code << 1) ^ (code >>
+ * 31) and w_b = the bit width of the OR of the block's z (0..32).  Layout:
+ * w_b as uint8 for every block, zero-padded to a multiple of 16 bytes, then
+ * for each block in order w_b uint32 words, word j holding bit j of the
+ * block's 32 z values (bit i = code 32 b + i).  Size 16-aligned(nb) +
+ * 4 sum(w_b) <= lcq_pack_bound(n).
+ *   lcq_pack      d_codes int32[n] -> d_out (at least lcq_pack_bound(n) bytes,
+ *       else LCQ_ERR_CAPACITY); *d_out_bytes (uint64, device, may be NULL)
+ *       receives the size.  Stream-ordered, no host synchronisation.
+ *   lcq_unpack    d_in (in_bytes bytes) -> d_codes int32[n].  A width above
+ *       32 or planes beyond in_bytes set LCQ_STATUS_HEADER in *d_status (which
+ *       the call first zeroes; may be NULL) and decode as zeros.
+ * Both need a workspace of lcq_pack_workspace_size(n) bytes; n > 0; all
+ * pointers 16-byte aligned.
+ */
+size_t lcq_pack_bound(uint64_t n);
+size_t lcq_pack_workspace_size(uint64_t n);
+lcq_status lcq_pack(const int32_t* d_codes, uint64_t n, void* d_out, size_t out_bytes, uint64_t* d_out_bytes,
+                    void* d_ws, size_t ws_bytes, cudaStream_t stream);
+lcq_status lcq_unpack(const void* d_in, size_t in_bytes, uint64_t n, int32_t* d_codes, uint32_t* d_status,
+                      void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/*
  * Ablations of the paper's experiments (not for production use).
  *   LCQ_ABL_ABS_NO_CHECK  ABS without the reconstruct-and-check step: the
  *       unprotected quantizer that Sec. 6 (Tables 7-8) measures against.  Bins

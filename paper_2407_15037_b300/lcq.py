@@ -98,6 +98,10 @@ SIGNATURES = {
                            _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
     "lcq_host_batch_stage_size": ([_vp, _u32], _sz),
     "lcq_quantize_host_batch": ([_vp, _u32, _vp, _sz, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_pack_bound": ([_u64], _sz),
+    "lcq_pack_workspace_size": ([_u64], _sz),
+    "lcq_pack": ([_vp, _u64, _vp, _sz, _vp, _vp, _sz, _vp], ctypes.c_int),
+    "lcq_unpack": ([_vp, _sz, _u64, _vp, _vp, _vp, _sz, _vp], ctypes.c_int),
     "lcq_debug_set_scan": ([_u32, _u64], None),
     "lcq_tune_variant_count": ([], ctypes.c_int),
     "lcq_tune_describe": ([ctypes.c_int, _vp, _vp, _vp, _vp], ctypes.c_int),
@@ -492,3 +496,35 @@ def quantize_host_batch(items, stage, ws, stream=None, device=None):
                                          ws.numel(), _stream_ptr(stream, device))
     _check(code, "lcq_quantize_host_batch")
     return [it.status for it in items]
+
+
+def pack(codes, out=None, ws=None, stream=None):
+    """Bit-plane packing of an int32 CUDA tensor (lcq_pack).  Returns (buffer,
+    size tensor): the packed bytes are buffer[:size] (size is a device int64,
+    no host synchronisation)."""
+    _require_cuda(codes)
+    n = codes.numel()
+    if out is None:
+        out = torch.empty(int(lib().lcq_pack_bound(n)), dtype=torch.uint8, device=codes.device)
+    if ws is None:
+        ws = torch.empty(max(int(lib().lcq_pack_workspace_size(n)), 16), dtype=torch.uint8, device=codes.device)
+    size = torch.empty(1, dtype=torch.int64, device=codes.device)
+    code = lib().lcq_pack(_ptr(codes), n, _ptr(out), out.numel(), _ptr(size), _ptr(ws), ws.numel(),
+                          _stream_ptr(stream, codes.device))
+    _check(code, "lcq_pack")
+    return out, size
+
+
+def unpack(buf, n, ws=None, stream=None, check=True):
+    """Codes back from a packed buffer (uint8 CUDA tensor of its bytes)."""
+    _require_cuda(buf)
+    codes = torch.empty(n, dtype=torch.int32, device=buf.device)
+    if ws is None:
+        ws = torch.empty(max(int(lib().lcq_pack_workspace_size(n)), 16), dtype=torch.uint8, device=buf.device)
+    status = torch.zeros(1, dtype=torch.int32, device=buf.device)
+    code = lib().lcq_unpack(_ptr(buf), buf.numel(), n, _ptr(codes), _ptr(status), _ptr(ws), ws.numel(),
+                            _stream_ptr(stream, buf.device))
+    _check(code, "lcq_unpack")
+    if check and int(status.item()):
+        raise LcqError(7, "lcq_unpack (device status %d)" % int(status.item()))
+    return codes
