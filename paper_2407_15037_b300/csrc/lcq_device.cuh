@@ -495,18 +495,17 @@ __device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Const
 }
 
 // ---------------------------------------------------------------------------
-// float64 with few FP64 operations.  The FP64 pipe of this GPU issues only a
-// few operations per clock per SM, so the float64 recipes keep just their
-// multiplications (and, for REL, one addition) on it and do the rest exactly
-// on the bit patterns with integer operations:
+// float64 with few FP64 operations.  The FP64 pipe of this GPU issues only
+// about 1.6 multiplications per clock per SM, so the float64 recipes keep on
+// it one multiplication per value (q; REL also log2approx's addition), run
+// the double-check there only where its outcome is not already certain (see
+// abs_quant_f64, rel_quant_f64), and do the rest exactly on the bit patterns
+// with integer operations:
 //   * |v| < 2^w and |a| <= |b| as integer comparisons of the (sign-cleared)
 //     bit patterns: for non-negative IEEE doubles, including +Inf and NaN
 //     patterns, numeric order is the order of the bits;
 //   * rint of a double with |q| < 2^30 from its fields, round half to even;
 //   * an integer below 2^53 converted to the double with its exact value;
-//   * log2approx's single addition (1.M + (E - 1024)): the exact sum is the
-//     fixed-point number ((E - 1023) 2^52 + M) 2^-52, rounded to 53 bits with
-//     round-half-even in integer arithmetic (the same rounding as the FP add);
 //   * pow2approx of bb in [1, 2047): floor and fraction read off bb's fields;
 //   * the exact difference of two positive doubles within a factor 2 of each
 //     other (an integer subtraction of aligned significands, always exact).
@@ -578,36 +577,6 @@ __device__ __forceinline__ uint64_t int_to_dbits(int64_t i) {
     const uint64_t a = (uint64_t)(i < 0 ? -i : i);
     const int top = 63 - __clzll((long long)a);
     return sgn | ((uint64_t)(top + 1023) << 52) | ((a << (52 - top)) & kD_MANT);
-}
-
-// RN to a double of the signed fixed-point value T 2^-52, |T| < 2^62.
-__device__ __forceinline__ uint64_t fixed52_to_dbits(int64_t T) {
-    if (T == 0) return 0;
-    const uint64_t sgn = T < 0 ? kD_SIGN : 0;
-    uint64_t a = (uint64_t)(T < 0 ? -T : T);
-    int top = 63 - __clzll((long long)a);
-    uint64_t mant;
-    if (top <= 52) {
-        mant = a << (52 - top);
-    } else {
-        const int sh = top - 52;
-        mant = a >> sh;
-        const uint64_t rem = a & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (mant & 1))) {
-            mant++;
-            if (mant >> 53) {  // rounding carried into a new binade
-                mant >>= 1;
-                top++;
-            }
-        }
-    }
-    return sgn | ((uint64_t)(top - 52 + 1023) << 52) | (mant & kD_MANT);
-}
-
-// log2approx of a positive normal double with bits u (Sec. 3.2), exactly.
-__device__ __forceinline__ uint64_t log2approx_dbits(uint64_t u) {
-    const int64_t E = (int64_t)((u >> 52) & 0x7FF);
-    return fixed52_to_dbits(((E - 1023) << 52) + (int64_t)(u & kD_MANT));
 }
 
 // pow2approx bits of bb in [1, 2047) (caller checks): 2^(k-1023)(1 + bb - k).
@@ -715,7 +684,8 @@ __device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c,
     const uint64_t E = (u >> 52) & 0x7FF;
     if (E == 0 || E == 0x7FF) return false;  // zero, denormal, Inf, NaN
     // log2approx (Sec. 3.2): 1.M + (E - 1024), one FP64 addition (the FP64 pipe
-    // has room here; the integer form, log2approx_dbits, costs ~28 instructions)
+    // has room here; rounding the exact fixed-point sum with integers costs ~28
+    // instructions)
     const double L = __dadd_rn(dfrom(0x3FF0000000000000ull | (u & kD_MANT)), dfrom(small_int_to_dbits((int32_t)E - 1024)));
     const double q = __dmul_rn(L, c.inv);
     const uint64_t uq = clear_sign(dbits(q));
