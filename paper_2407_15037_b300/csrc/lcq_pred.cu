@@ -69,43 +69,60 @@ __device__ __forceinline__ int32_t at(const int32_t* b, int N, int i, int j, int
     return b[((size_t)i * N + j) * N + k];
 }
 
-// Interpolation base of point (i, j, k) (not an anchor).
-__device__ __forceinline__ int32_t interp(const int32_t* b, int N, int i, int j, int k, const Point& pt) {
-    const int s = pt.s, last = ((N - 1) / (2 * s)) * (2 * s);
-    const int i0 = (pt.cls & 1) ? clampc(i - s, last) : i, i1 = (pt.cls & 1) ? clampc(i + s, last) : i;
-    const int j0 = (pt.cls & 2) ? clampc(j - s, last) : j, j1 = (pt.cls & 2) ? clampc(j + s, last) : j;
-    const int k0 = (pt.cls & 4) ? clampc(k - s, last) : k, k1 = (pt.cls & 4) ? clampc(k + s, last) : k;
+// Element offset, relative to point (i, j, k), of a coarse position along
+// each axis: ((ci - i) N + (cj - j)) N + (ck - k), split per axis.  The
+// positions lie within 2 s2 <= 16 of the point, so each term fits in int32
+// for N <= 2048.
+__device__ __forceinline__ int axis_off(int c, int x, int stride) { return (c - x) * stride; }
+
+// Interpolation base of point (i, j, k) (not an anchor); p = &b[i][j][k].
+__device__ __forceinline__ int32_t interp(const int32_t* p, int N, int i, int j, int k, const Point& pt) {
+    const int s = pt.s, last = ((N - 1) / (2 * s)) * (2 * s), NN = N * N;
+    const int i0 = (pt.cls & 1) ? axis_off(clampc(i - s, last), i, NN) : 0;
+    const int i1 = (pt.cls & 1) ? axis_off(clampc(i + s, last), i, NN) : 0;
+    const int j0 = (pt.cls & 2) ? axis_off(clampc(j - s, last), j, N) : 0;
+    const int j1 = (pt.cls & 2) ? axis_off(clampc(j + s, last), j, N) : 0;
+    const int k0 = (pt.cls & 4) ? clampc(k - s, last) - k : 0;
+    const int k1 = (pt.cls & 4) ? clampc(k + s, last) - k : 0;
     const int c = __popc(pt.cls);
     long long acc = 0;
     // enumerate the 2^c distinct corners: along an even axis both ends coincide
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         if ((q & ~pt.cls) != 0) continue;
-        acc += at(b, N, (q & 1) ? i1 : i0, (q & 2) ? j1 : j0, (q & 4) ? k1 : k0);
+        acc += p[((q & 1) ? i1 : i0) + ((q & 2) ? j1 : j0) + ((q & 4) ? k1 : k0)];
     }
     return (int32_t)((acc + (1ll << (c - 1))) >> c);
 }
 
-// The 27 stencil inputs packed 4 per int32 (byte 3 of word 6 is 0).
-__device__ __forceinline__ void stencil(const int32_t* b, int N, int i, int j, int k, const Point& pt,
+// The 27 stencil inputs packed 4 per int32 (byte 3 of word 6 is 0);
+// p = &b[i][j][k].
+__device__ __forceinline__ void stencil(const int32_t* p, int N, int i, int j, int k, const Point& pt,
                                         int32_t base, int s_in, int32_t xw[7]) {
-    const int s2 = 2 * pt.s, last = ((N - 1) / s2) * s2;
+    const int s2 = 2 * pt.s, last = ((N - 1) / s2) * s2, NN = N * N;
     const int fi = (i / s2) * s2, fj = (j / s2) * s2, fk = (k / s2) * s2;
+    int oi[3], oj[3], ok[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        oi[d] = axis_off(clampc(fi + s2 * (d - 1), last), i, NN);
+        oj[d] = axis_off(clampc(fj + s2 * (d - 1), last), j, N);
+        ok[d] = clampc(fk + s2 * (d - 1), last) - k;
+    }
 #pragma unroll
     for (int w = 0; w < 7; w++) xw[w] = 0;
 #pragma unroll
     for (int t = 0; t < kNin; t++) {
-        const int di = t / 9 - 1, dj = (t / 3) % 3 - 1, dk = t % 3 - 1;
-        const int32_t c = at(b, N, clampc(fi + s2 * di, last), clampc(fj + s2 * dj, last), clampc(fk + s2 * dk, last));
+        const int32_t c = p[oi[t / 9] + oj[(t / 3) % 3] + ok[t % 3]];
         int32_t d = (c - base) >> s_in;  // |c - base| < 2^31: both bins lie in (-2^30, 2^30)
         d = d < -128 ? -128 : (d > 127 ? 127 : d);
         xw[t >> 2] |= (int32_t)((uint32_t)(d & 0xFF) << (8 * (t & 3)));
     }
 }
 
-// Parameters in shared memory, W1 rows as 7 packed int32 words.
+// Parameters in shared memory, W1 rows as 7 packed int32 words and a zero
+// eighth, so that a row is two 16-byte loads.
 struct SmemParams {
-    int32_t w1[kNets][kNhid][7];
+    int4 w1[kNets][kNhid][2];
     int32_t b1[kNets][kNhid];
     int32_t w2[kNets][4];
     int32_t b2[kNets];
@@ -116,7 +133,8 @@ struct SmemParams {
 __device__ __forceinline__ void load_params(SmemParams& sp, const lcq_pred_params* gp) {
     const int32_t* w1 = reinterpret_cast<const int32_t*>(gp->w1);
     const int32_t* w2 = reinterpret_cast<const int32_t*>(gp->w2);
-    for (int x = threadIdx.x; x < kNets * kNhid * 7; x += blockDim.x) (&sp.w1[0][0][0])[x] = w1[x];
+    int32_t* sw1 = reinterpret_cast<int32_t*>(&sp.w1[0][0][0]);
+    for (int x = threadIdx.x; x < kNets * kNhid * 8; x += blockDim.x) sw1[x] = (x & 7) < 7 ? w1[(x >> 3) * 7 + (x & 7)] : 0;
     for (int x = threadIdx.x; x < kNets * kNhid; x += blockDim.x) (&sp.b1[0][0])[x] = (&gp->b1[0][0][0])[x];
     for (int x = threadIdx.x; x < kNets * 4; x += blockDim.x) (&sp.w2[0][0])[x] = w2[x];
     for (int x = threadIdx.x; x < kNets; x += blockDim.x) sp.b2[x] = (&gp->b2[0][0])[x];
@@ -129,8 +147,14 @@ __device__ __forceinline__ int32_t network(const SmemParams& sp, int net, const 
 #pragma unroll
     for (int u = 0; u < kNhid; u++) {
         int32_t z = sp.b1[net][u];
-#pragma unroll
-        for (int w = 0; w < 7; w++) z = __dp4a(xw[w], sp.w1[net][u][w], z);
+        const int4 a = sp.w1[net][u][0], c = sp.w1[net][u][1];
+        z = __dp4a(xw[0], a.x, z);
+        z = __dp4a(xw[1], a.y, z);
+        z = __dp4a(xw[2], a.z, z);
+        z = __dp4a(xw[3], a.w, z);
+        z = __dp4a(xw[4], c.x, z);
+        z = __dp4a(xw[5], c.y, z);
+        z = __dp4a(xw[6], c.z, z);
         int32_t h = (z + (1 << (sp.s1 - 1))) >> sp.s1;
         h = h < 0 ? 0 : (h > 127 ? 127 : h);
         hw[u >> 2] |= h << (8 * (u & 3));
@@ -143,10 +167,11 @@ __device__ __forceinline__ int32_t network(const SmemParams& sp, int net, const 
 
 __device__ __forceinline__ int32_t predict_point(const int32_t* b, int N, int i, int j, int k, const Point& pt,
                                                  const SmemParams* sp) {
-    int32_t base = interp(b, N, i, j, k, pt);
+    const int32_t* p = b + (((size_t)i * N + j) * N + k);
+    int32_t base = interp(p, N, i, j, k, pt);
     if (sp) {
         int32_t xw[7];
-        stencil(b, N, i, j, k, pt, base, sp->s_in[pt.level - 1], xw);
+        stencil(p, N, i, j, k, pt, base, sp->s_in[pt.level - 1], xw);
         base = (int32_t)((uint32_t)base + (uint32_t)network(*sp, (pt.level - 1) * 7 + (pt.cls - 1), xw));
     }
     return base;
@@ -286,9 +311,10 @@ __global__ void __launch_bounds__(kTrainBlock) k_train_partial(TParams p) {
         const int32_t* b = p.bins + (size_t)f * N * N * N;
         Point pt = classify(i, j, k);
         (void)level; (void)cls;
-        const int32_t base = interp(b, N, i, j, k, pt);
+        const int32_t* pp = b + (size_t)e;
+        const int32_t base = interp(pp, N, i, j, k, pt);
         int32_t xw[7];
-        stencil(b, N, i, j, k, pt, base, p.s_in[pt.level - 1], xw);
+        stencil(pp, N, i, j, k, pt, base, p.s_in[pt.level - 1], xw);
         float x[kNin];
 #pragma unroll
         for (int q = 0; q < kNin; q++) x[q] = (float)(int8_t)((xw[q >> 2] >> (8 * (q & 3))) & 0xFF);
