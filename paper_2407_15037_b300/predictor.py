@@ -72,6 +72,26 @@ def params_to_device(params, device):
     return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
 
 
+def save_params(params, path):
+    """Write frozen parameters (a uint8 device tensor from Trainer.freeze or
+    params_to_device, or a PredParams) as the raw little-endian bytes of
+    struct lcq_pred_params."""
+    raw = bytes(params) if isinstance(params, PredParams) else bytes(params.cpu().numpy())
+    if len(raw) != PARAMS_BYTES:
+        raise ValueError("predictor parameters must be %d bytes" % PARAMS_BYTES)
+    with open(path, "wb") as f:
+        f.write(raw)
+
+
+def load_params(path, device):
+    """Frozen parameters written by save_params, as a uint8 device tensor."""
+    with open(path, "rb") as f:
+        raw = f.read()
+    if len(raw) != PARAMS_BYTES:
+        raise ValueError("%s: %d bytes, expected %d" % (path, len(raw), PARAMS_BYTES))
+    return torch.frombuffer(bytearray(raw), dtype=torch.uint8).to(device)
+
+
 def params_from_device(t):
     p = PredParams()
     ctypes.memmove(ctypes.addressof(p), bytes(t.cpu().numpy()), PARAMS_BYTES)
@@ -224,6 +244,24 @@ class Trainer:
     def mean_squared_residual(self):
         torch.cuda.synchronize(self.dev)
         return float(self.loss.double().sum().item() / (self.samples.numel()))
+
+    def state_dict(self):
+        """Training state for checkpoints: float32 shadow parameters, Adam
+        moments, step count and the fixed shifts (host tensors)."""
+        return {"shadow": self.shadow.cpu(), "m": self.m.cpu(), "v": self.v.cpu(), "t": self.t,
+                "s_in": self.s_in.copy(), "s1": self.s1, "s2": self.s2, "lr": self.lr}
+
+    def load_state_dict(self, st):
+        """Resume from state_dict(); the sample set is the constructor's
+        (same fields and seed give the same samples)."""
+        if st["shadow"].numel() != self.shadow.numel():
+            raise ValueError("checkpoint for a different network shape")
+        self.shadow.copy_(st["shadow"].to(self.dev))
+        self.m.copy_(st["m"].to(self.dev))
+        self.v.copy_(st["v"].to(self.dev))
+        self.t = int(st["t"])
+        self.s_in = np.asarray(st["s_in"], dtype=np.int32)
+        self.s1, self.s2, self.lr = int(st["s1"]), int(st["s2"]), float(st["lr"])
 
     def freeze(self):
         out = torch.zeros(PARAMS_BYTES, dtype=torch.uint8, device=self.dev)

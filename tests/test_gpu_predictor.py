@@ -169,3 +169,30 @@ def test_trained_network_beats_interpolation_on_held_out_fields():
         gain.append(b0 - b1)
         assert torch.equal(PD.reconstruct(r1, N, params), q.bins)
     assert min(gain) > 0, gain
+
+
+def test_checkpoint_resume_is_exact(tmp_path):
+    """Training resumed from a state_dict continues bit for bit as if it had
+    not stopped; frozen parameters survive save_params / load_params."""
+    N = 32
+    fields = torch.cat([torch.from_numpy(
+        np.rint(synth.grf(N, seed=s).numpy() / 2e-3).astype(np.int32)) for s in range(2)]).to(DEV)
+    a = PD.Trainer(fields, N, samples_per_net=600, seed=4, s_in=(3, 3, 2))
+    for _ in range(5):
+        a.step()
+    st = a.state_dict()
+    torch.save(st, tmp_path / "ckpt.pt")
+    for _ in range(5):
+        a.step()
+    b = PD.Trainer(fields, N, samples_per_net=600, seed=4, s_in=(3, 3, 2))
+    b.load_state_dict(torch.load(tmp_path / "ckpt.pt", weights_only=False))
+    for _ in range(5):
+        b.step()
+    torch.cuda.synchronize()
+    assert torch.equal(a.shadow, b.shadow) and a.t == b.t
+    fa = a.freeze()
+    PD.save_params(fa, tmp_path / "params.bin")
+    fb = PD.load_params(tmp_path / "params.bin", DEV)
+    assert torch.equal(fa, fb)
+    assert torch.equal(PD.residuals(fields[:N ** 3], N, fa), PD.residuals(fields[:N ** 3], N, fb))
+
