@@ -347,10 +347,19 @@ def run_ours(args, world, rank, local):
     q = P.alloc_outputs(n, x.dtype, dev)
     ws = P.new_workspace(n, dev)
 
-    def step():
+    abs_events = []  # (start, end) around every ABS call of the timed steps
+
+    def step(record=False):
         for bound in BOUNDS:
             for eb in EBS:
-                P.quantize_into(x, bound, eb, q, ws, stream)
+                if record and bound == "abs":
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    P.quantize_into(x, bound, eb, q, ws, stream)
+                    b.record(stream)
+                    abs_events.append((a, b))
+                else:
+                    P.quantize_into(x, bound, eb, q, ws, stream)
 
     # autotune the tile shape per bound type on this workload (untimed)
     tuning = {}
@@ -377,7 +386,7 @@ def run_ours(args, world, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        step()
+        step(record=True)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
@@ -387,27 +396,30 @@ def run_ours(args, world, rank, local):
     bytes_step = len(BOUNDS) * len(EBS) * x.numel() * 4
     value = world * args.steps * bytes_step / (ms / 1e3) / 1e9
 
-    # ---- per-call times (live, CUDA events on the launching stream) ----
+    # ---- per-call times: the median of 9 event-timed calls after one untimed
+    # call (the paper's convention), CUDA events on the launching stream ----
     per = {}
-    reps = 10
     for bound in BOUNDS:
         for eb in EBS:
-            P.quantize_into(x, bound, eb, q, ws, stream)  # untimed: the first call of each configuration
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(reps):
+            P.quantize_into(x, bound, eb, q, ws, stream)
+            evs = []
+            for _ in range(9):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
                 P.quantize_into(x, bound, eb, q, ws, stream)
-            b.record(stream)
+                b.record(stream)
+                evs.append((a, b))
             torch.cuda.synchronize(dev)
             h = q.read_header()
-            t = a.elapsed_time(b) / reps / 1e3
+            t = float(np.median([a.elapsed_time(b) for a, b in evs])) / 1e3
             per["%s_%g" % (bound, eb)] = {"ms": t * 1e3, "outliers": int(h.outlier_count),
                                          "in_GBps": n * 4 / t / 1e9}
     peaks, peak_kind = measured_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
-    # dominant kernel: k_quantize<float, ABS> (ABS and NOA calls, 8 of 12 per step)
+    # dominant kernel: k_quantize<float, ABS> (ABS and NOA calls, 8 of 12 per step); its
+    # average launch time over the ABS calls of the timed steps (each ABS call is one launch)
     abs_keys = ["abs_%g" % e for e in EBS]
-    t_abs = float(np.mean([per[k]["ms"] for k in abs_keys])) / 1e3
+    t_abs = float(np.mean([a.elapsed_time(b) for a, b in abs_events])) / 1e3
     outl_abs = float(np.mean([per[k]["outliers"] for k in abs_keys]))
     alg_bytes = n * (4 + 4) + (n + 31) // 32 * 4 + 4 * outl_abs  # in + bins + mask + payload
     achieved = alg_bytes / t_abs / 1e9
@@ -421,14 +433,16 @@ def run_ours(args, world, rank, local):
     out = torch.empty_like(x)
     dstat = torch.zeros(1, dtype=torch.int32, device=dev)
     P.quantize_into(x, "abs", 1e-3, q, ws, stream)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     P.dequantize_into(q, out, ws, dstat, stream)
-    a.record(stream)
-    for _ in range(reps):
+    evs = []
+    for _ in range(9):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         P.dequantize_into(q, out, ws, dstat, stream)
-    b.record(stream)
+        b.record(stream)
+        evs.append((a, b))
     torch.cuda.synchronize(dev)
-    t_deq = a.elapsed_time(b) / reps / 1e3
+    t_deq = float(np.median([a.elapsed_time(b) for a, b in evs])) / 1e3
 
     # ---- other configurations of the same path (timed per call) ----
     extra = {}
@@ -555,7 +569,8 @@ def run_ours(args, world, rank, local):
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_source": peak_kind,
                          "alg_bytes_per_launch": alg_bytes, "traffic": traffic,
-                         "avg_launch_ms": t_abs * 1e3},
+                         "avg_launch_ms": t_abs * 1e3,
+                         "launches_timed": len(abs_events)},
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,
             "e2e": e2e,
