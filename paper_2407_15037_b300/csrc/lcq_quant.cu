@@ -6,19 +6,23 @@
 //   [NOA only] k_minmax: finite min/max (ordered-integer keys, warp + block
 //       reductions, per-block partials, last block combines) -> R, eb*R and
 //       the ABS constants, written to the header in device memory (Sec. 2.1.3).
-//   k_quantize: each CTA takes a tile of TILE values by atomic ticket, loads
-//       them with 128-bit loads, computes bin, reconstruction and the bound
-//       check per value (Sec. 2.2, 3.1-3.3), stores the bins with 128-bit
-//       stores, builds the tile's outlier mask with warp shuffles, scans the
-//       mask popcounts and runs a bounded decoupled lookback over the tiles
-//       to place the tile's outliers in ascending index order.
-// k_dequantize mirrors it: the same lookback over mask popcounts gives each
-// tile's payload offset; values are reconstructed with the encoder's exact
-// operations (Sec. 3.1, no double-check on decode, Sec. 6).
+//   k_quantize: persistent CTAs of 8 compute warps and 1 scan warp.  Stages
+//       of the input arrive in shared memory by bulk asynchronous copies
+//       (cp.async.bulk + mbarrier) in a ring; scan tiles (several stages) are
+//       handed out by an atomic ticket.  Compute warps quantize, verify and
+//       store bins per value (Sec. 2.2, 3.1-3.3) and build the outlier mask
+//       words; the scan warp scans each finished tile's mask, publishes its
+//       count and runs a bounded decoupled lookback for the tile's payload
+//       offset; the compute warps then write that tile's outliers (raw bits,
+//       ascending index order) while the next tile streams in.
+// k_dequantize mirrors it: bins and mask words arrive by bulk copies, the same
+// lookback gives each tile's payload offset, and values are reconstructed with
+// the encoder's exact operations (Sec. 3.1; no double-check on decode, Sec. 6).
 //
 // Arrays longer than kChunk values are processed as several launches; the
 // running outlier count carries from one chunk to the next in device memory,
-// so a call never waits on the host.
+// so a call never waits on the host.  lcq_quantize_host / _host_batch use the
+// same per-range launches to pipeline host copies with the kernels.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
