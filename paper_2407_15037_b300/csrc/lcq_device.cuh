@@ -411,13 +411,22 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
 //    for every |q| < 2^29 (a float of magnitude >= 2^23 is an integer), and
 //    makes |q| >= 2^29 an outlier: that is the range test, and the two-sided
 //    bin test then holds because rint(q) < 2^29 for q < 2^29;
-//  * the exact rescale for tiny values runs only in warps that have one;
-//  * in a warp without tiny values (every lo = min(a, m) >= 2^-62) and with
-//    RATIO = false, the special-value and bb-range tests are implied as well:
-//    a zero or denormal a, or bb < 1 (m = bb 2^23 converted is then below
-//    2^-126, or 0 for bb < 0), would make lo tiny; an Inf or NaN a makes d
-//    Inf or NaN; bb >= 255 makes m +Inf, a NaN, or a negative value (bit 31
-//    set: then t = RN(lo chk) <= 0 < FLT_MIN); each of these fails d <= t or
+//  * the exact rescale for tiny values runs only in warps that have one, and
+//    with RATIO = false "tiny" means lo < T = 2^(1 - e_c) (e_c = the biased
+//    exponent of chk <= 1/2, so T >= FLT_MIN / chk and T >= 2^-125) rather
+//    than the recipe's 2^-62: for T <= lo < 2^-62 the rescale is exact both
+//    ways (lo chk >= FLT_MIN, so RN(lo 2^64 chk) = RN(lo chk) 2^64 and
+//    d 2^64 <= t <=> d <= RN(lo chk)), so skipping it changes nothing;
+//  * a warp whose only tiny values are zeros and denormals (a < FLT_MIN, all
+//    outliers) or NaN still takes the straight-line code, which then rejects
+//    a < FLT_MIN explicitly (NaN fails that comparison too);
+//  * in a warp without tiny values (every lo = min(a, m) >= T, apart from
+//    the rejected a < FLT_MIN) and with RATIO = false, the special-value and
+//    bb-range tests are implied as well: a zero or denormal a is rejected
+//    explicitly or makes lo tiny; bb < 1 (m = bb 2^23 converted is then below
+//    2^-126 < T, or 0 for bb < 0) makes lo tiny; an Inf or NaN a makes d Inf
+//    or NaN; bb >= 255 makes m +Inf, a NaN, or a negative value (bit 31 set:
+//    then t = RN(lo chk) <= 0 < FLT_MIN); each of these fails d <= t or
 //    t >= FLT_MIN.
 template <bool RATIO, bool WIDE>
 __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float q[4], const Consts<float>& c,
@@ -426,6 +435,8 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
     int32_t bin[4];
     bool inr[4];
     bool tiny = false;
+    // tiny threshold: 2^(1 - e_c) for chk <= 1/2 (see above), else the recipe's 2^-62
+    const float T = RATIO ? 0x1p-62f : __uint_as_float((128u - ((__float_as_uint(c.chk) >> 23) & 0xFFu)) << 23);
 #pragma unroll
     for (int k = 0; k < 4; k++) {
         const uint32_t u = __float_as_uint(x[k]);
@@ -447,19 +458,35 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
         bb[k] = __fadd_rn(Lr, 127.0f);
         m[k] = __uint_as_float(__float2uint_rz(__fmul_rn(bb[k], 0x1p23f)));
         lo[k] = fminf(a[k], m[k]);
-        tiny |= lo[k] < 0x1p-62f;
+        tiny |= lo[k] < T;
     }
     uint32_t nb = 0;
-    if (!RATIO && !__any_sync(0xFFFFFFFFu, tiny)) {
+    if (!RATIO) {
+        if (!__any_sync(0xFFFFFFFFu, tiny)) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            const float d = fabsf(__fsub_rn(a[k], m[k]));  // exact (Sterbenz) when accepted
-            const float tt = __fmul_rn(lo[k], c.chk);
-            const bool ok = inr[k] && (tt >= FLT_MIN) && (d <= tt);
-            b[k] = ok ? bin[k] : 0;
-            nb |= ok ? 0u : (1u << k);
+            for (int k = 0; k < 4; k++) {
+                const float d = fabsf(__fsub_rn(a[k], m[k]));  // exact (Sterbenz) when accepted
+                const float tt = __fmul_rn(lo[k], c.chk);
+                const bool ok = inr[k] && (tt >= FLT_MIN) && (d <= tt);
+                b[k] = ok ? bin[k] : 0;
+                nb |= ok ? 0u : (1u << k);
+            }
+            return nb;
         }
-        return nb;
+        bool tiny2 = false;  // tiny values other than zeros, denormals and NaN
+#pragma unroll
+        for (int k = 0; k < 4; k++) tiny2 |= lo[k] < T && a[k] >= FLT_MIN;
+        if (!__any_sync(0xFFFFFFFFu, tiny2)) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const float d = fabsf(__fsub_rn(a[k], m[k]));
+                const float tt = __fmul_rn(lo[k], c.chk);
+                const bool ok = inr[k] && (a[k] >= FLT_MIN) && (tt >= FLT_MIN) && (d <= tt);
+                b[k] = ok ? bin[k] : 0;
+                nb |= ok ? 0u : (1u << k);
+            }
+            return nb;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) {
