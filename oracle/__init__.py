@@ -18,10 +18,14 @@ import numpy as np
 
 from . import build as _build
 
-F32, F64 = 0, 1
+F32, F64, F16, BF16 = 0, 1, 2, 3
 ABS, REL, NOA = 0, 1, 2
 BOUND_NAMES = {"abs": ABS, "rel": REL, "noa": NOA}
-DTYPES = {np.dtype(np.float32): F32, np.dtype(np.float64): F64}
+DTYPES = {np.dtype(np.float32): F32, np.dtype(np.float64): F64, np.dtype(np.float16): F16}
+# numpy has no bfloat16: bfloat16 arrays travel as uint16 bit patterns with
+# fmt="bf16" (binary16 arrays may be float16, or uint16 with fmt="f16")
+FORMATS = {"f16": F16, "bf16": BF16}
+PAYLOAD = {F32: np.uint32, F64: np.uint64, F16: np.uint16, BF16: np.uint16}
 
 
 class Consts(ctypes.Structure):
@@ -86,6 +90,10 @@ def lib():
                 getattr(L, nm).restype = None
             L.lcqo_sweep_f32.argtypes = [P(Consts), u64, u64, dbl, P(u64)]
             L.lcqo_sweep_f32.restype = None
+            L.lcqo_widen16_array.argtypes = [ctypes.c_int, vp, vp, u64]
+            L.lcqo_widen16_array.restype = None
+            L.lcqo_round16_array.argtypes = [ctypes.c_int, vp, vp, u64]
+            L.lcqo_round16_array.restype = None
             _lib = L
     if not _lib.lcqo_fp_env_ok():
         raise RuntimeError("oracle: FTZ/DAZ set or rounding mode is not to-nearest")
@@ -100,21 +108,40 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None and a.size else ctypes.c_void_p(0)
 
 
-def _dtype_code(x):
+def _dtype_code(x, fmt=None):
+    if fmt is not None:
+        if FORMATS[fmt] == F16 and np.dtype(x.dtype) == np.float16:
+            return F16
+        if np.dtype(x.dtype) != np.uint16:
+            raise TypeError("oracle: fmt=%r takes uint16 bit patterns" % fmt)
+        return FORMATS[fmt]
     try:
         return DTYPES[np.dtype(x.dtype)]
     except KeyError:
-        raise TypeError("oracle: float32 or float64 input required") from None
+        raise TypeError("oracle: float32, float64 or float16 input required (bfloat16: uint16 bits, "
+                        "fmt='bf16')") from None
+
+
+def _fmt_of(code):
+    return {F16: "f16", BF16: "bf16"}.get(code)
+
+
+def dtype_code(dtype):
+    """Oracle dtype code of a numpy float dtype or of 'f16' / 'bf16'."""
+    if isinstance(dtype, str) and dtype in FORMATS:
+        return FORMATS[dtype]
+    return DTYPES[np.dtype(dtype)]
 
 
 def consts(bound, dtype, eb, x=None, rng=None):
-    """Derived constants (Sec. 2.2 and readings R2-R6).
+    """Derived constants (Sec. 2.2 and readings R2-R6, R11).
 
-    bound: 'abs' | 'rel' | 'noa'; dtype: numpy float dtype; for NOA give the
-    input x, or rng=(any_finite, mn, mx) for a range computed elsewhere.
+    bound: 'abs' | 'rel' | 'noa'; dtype: numpy float dtype, or 'f16' /
+    'bf16'; for NOA give the input x, or rng=(any_finite, mn, mx) for a range
+    computed elsewhere.
     """
     b = BOUND_NAMES[bound] if isinstance(bound, str) else bound
-    d = DTYPES[np.dtype(dtype)]
+    d = dtype_code(dtype)
     c = Consts()
     L = lib()
     if b == ABS:
@@ -126,18 +153,20 @@ def consts(bound, dtype, eb, x=None, rng=None):
                                           ctypes.byref(c))
     else:
         x = np.ascontiguousarray(x)
+        if _dtype_code(x, _fmt_of(d)) != d:
+            raise TypeError("oracle: input does not match dtype %r" % (dtype,))
         st = L.lcqo_consts_noa(d, float(eb), _ptr(x), x.size, ctypes.byref(c))
     if st != 0:
         raise BoundError("oracle: bound %r rejected (status %d)" % (eb, st))
     return c
 
 
-def value_range(x):
+def value_range(x, fmt=None):
     """(any_finite, min, max) over the finite values of x (reading R6)."""
     x = np.ascontiguousarray(x)
     any_ = ctypes.c_int32()
     mn, mx = ctypes.c_double(), ctypes.c_double()
-    lib().lcqo_range(_dtype_code(x), _ptr(x), x.size, ctypes.byref(any_), ctypes.byref(mn),
+    lib().lcqo_range(_dtype_code(x, fmt), _ptr(x), x.size, ctypes.byref(any_), ctypes.byref(mn),
                      ctypes.byref(mx))
     return bool(any_.value), mn.value, mx.value
 
@@ -146,7 +175,7 @@ def value_range(x):
 class Quantized:
     bins: np.ndarray      # int32[n]
     mask: np.ndarray      # uint32[ceil(n/32)]
-    payload: np.ndarray   # uint32 or uint64 [count] (raw bits)
+    payload: np.ndarray   # uint32, uint64 or uint16 [count] (raw bits)
     count: int
     consts: Consts
 
@@ -154,27 +183,31 @@ class Quantized:
 def quantize_with(c, x, capacity=None):
     """Quantize x with precomputed constants c (bins, mask, payload, count)."""
     x = np.ascontiguousarray(x)
-    if _dtype_code(x) != c.dtype:
+    if _dtype_code(x, _fmt_of(c.dtype)) != c.dtype:
         raise TypeError("oracle: dtype does not match the constants")
     n = x.size
     cap = n if capacity is None else int(capacity)
     bins = np.empty(n, dtype=np.int32)
     mask = np.empty((n + 31) // 32, dtype=np.uint32)
-    pay = np.empty(max(cap, 0), dtype=np.uint32 if c.dtype == F32 else np.uint64)
+    pay = np.empty(max(cap, 0), dtype=PAYLOAD[c.dtype])
     cnt = lib().lcqo_quantize(ctypes.byref(c), _ptr(x), n, _ptr(bins), _ptr(mask), _ptr(pay), cap)
     return Quantized(bins, mask, pay[:min(cnt, cap)], int(cnt), c)
 
 
-def quantize(x, bound, eb, capacity=None):
+def quantize(x, bound, eb, capacity=None, fmt=None):
+    """fmt: None (x is float32/64/16), or 'f16' / 'bf16' for uint16 bits."""
     x = np.ascontiguousarray(x)
-    c = consts(bound, x.dtype, eb, x=x)
+    d = _dtype_code(x, fmt)
+    c = consts(bound, _fmt_of(d) or x.dtype, eb, x=x)
     return quantize_with(c, x, capacity)
 
 
 def dequantize(q):
+    """Decoded values: float32 / float64 / float16 arrays; bfloat16 as uint16
+    bit patterns."""
     c = q.consts
     n = q.bins.size
-    out = np.empty(n, dtype=np.float32 if c.dtype == F32 else np.float64)
+    out = np.empty(n, dtype={F32: np.float32, F64: np.float64, F16: np.float16, BF16: np.uint16}[c.dtype])
     lib().lcqo_dequantize(ctypes.byref(c), _ptr(q.bins), _ptr(q.mask), _ptr(q.payload), n,
                           _ptr(out))
     return out
@@ -184,6 +217,8 @@ def quantize_unprotected(x, eb):
     """Ablation: ABS without the reconstruct-and-check step (Sec. 6, Tables
     7-8); the result decodes with dequantize() like any ABS result."""
     x = np.ascontiguousarray(x)
+    if _dtype_code(x) not in (F32, F64):
+        raise TypeError("oracle: the ablations take float32 or float64")
     c = consts("abs", x.dtype, eb)
     n = x.size
     bins = np.empty(n, dtype=np.int32)
@@ -204,17 +239,40 @@ def rel_library_recon(dtype, step, bins, mask):
     return out
 
 
-def verify_abs(x, xr, eb):
+def verify_abs(x, xr, eb, fmt=None):
     """Exact count of elements with |x - x'| > eb (Sec. 2.1.1); 0 means sound."""
     x, xr = np.ascontiguousarray(x), np.ascontiguousarray(xr)
-    return int(lib().lcqo_verify_abs(_dtype_code(x), _ptr(x), _ptr(xr), x.size, float(eb)))
+    d = _dtype_code(x, fmt)
+    if _dtype_code(xr, fmt) != d or xr.size != x.size:
+        raise TypeError("oracle: x and x' differ in type or size")
+    return int(lib().lcqo_verify_abs(d, _ptr(x), _ptr(xr), x.size, float(eb)))
 
 
-def verify_rel(x, xr, eps):
+def verify_rel(x, xr, eps, fmt=None):
     """Exact count of elements outside |x|/(1+eps) <= |x'| <= |x|(1+eps) with
     equal sign (Sec. 2.1.2); bit-identical reconstructions always pass."""
     x, xr = np.ascontiguousarray(x), np.ascontiguousarray(xr)
-    return int(lib().lcqo_verify_rel(_dtype_code(x), _ptr(x), _ptr(xr), x.size, float(eps)))
+    d = _dtype_code(x, fmt)
+    if _dtype_code(xr, fmt) != d or xr.size != x.size:
+        raise TypeError("oracle: x and x' differ in type or size")
+    return int(lib().lcqo_verify_rel(d, _ptr(x), _ptr(xr), x.size, float(eps)))
+
+
+def widen16(h, fmt):
+    """The float32 values of 16-bit patterns h (uint16) in format fmt (R11)."""
+    h = np.ascontiguousarray(h, dtype=np.uint16)
+    out = np.empty(h.size, dtype=np.float32)
+    lib().lcqo_widen16_array(FORMATS[fmt], _ptr(h), _ptr(out), h.size)
+    return out
+
+
+def round16(x, fmt):
+    """float32 values (not NaN) rounded to nearest-even in format fmt; uint16
+    bit patterns (R11)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.empty(x.size, dtype=np.uint16)
+    lib().lcqo_round16_array(FORMATS[fmt], _ptr(x), _ptr(out), x.size)
+    return out
 
 
 def _verify_parallel(fn, x, xr, eb, threads=None):

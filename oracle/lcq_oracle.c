@@ -53,6 +53,14 @@
  *  R9  No flush-to-zero / denormals-are-zero anywhere (checked at run time).
  *  R10 One recipe, one answer: the bound admits many bins; parity is defined
  *      against this recipe only.
+ *  R11 16-bit inputs (IEEE binary16 "f16", bfloat16 "bf16"; the paper covers
+ *      float and double only): every value widens exactly to a float and
+ *      takes the float recipe with the float constants of R2/R4/R6, except
+ *      that the reconstruction the check of Sec. 3.1 tests is the one the
+ *      decoder outputs, the float reconstruction rounded to nearest-even in
+ *      the 16-bit format.  REL specials are those of the widened float (an
+ *      f16 subnormal is a normal float and is quantized).  Outlier payloads
+ *      are the raw 16-bit patterns.
  */
 #include <float.h>
 #include <fenv.h>
@@ -66,6 +74,8 @@
 
 #define LCQO_F32 0
 #define LCQO_F64 1
+#define LCQO_F16 2  /* IEEE binary16, reading R11 */
+#define LCQO_BF16 3 /* bfloat16, reading R11 */
 #define LCQO_ABS 0
 #define LCQO_REL 1
 #define LCQO_NOA 2
@@ -80,7 +90,7 @@
 /* Derived constants of one quantization.  Float32 values are held exactly in
  * the double fields. */
 typedef struct {
-    int32_t dtype;        /* LCQO_F32 / LCQO_F64 */
+    int32_t dtype;        /* LCQO_F32 / LCQO_F64 / LCQO_F16 / LCQO_BF16 */
     int32_t bound;        /* LCQO_ABS / LCQO_REL / LCQO_NOA */
     int32_t all_outliers; /* NOA without a usable range: store everything */
     int32_t pad;
@@ -140,6 +150,66 @@ static float f32_from(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
 static uint64_t f64_bits(double f) { uint64_t u; memcpy(&u, &f, 8); return u; }
 static double f64_from(uint64_t u) { double f; memcpy(&f, &u, 8); return f; }
 
+static int dtype_ok(int dtype) { return dtype >= LCQO_F32 && dtype <= LCQO_BF16; }
+static int is_16bit(int dtype) { return dtype == LCQO_F16 || dtype == LCQO_BF16; }
+
+/* ------------------------------------------------------------------------ */
+/* 16-bit binary formats (reading R11): sign bit 15, then an exponent field  */
+/* of 15 - fb bits with bias `bias`, then fb fraction bits.  binary16:       */
+/* fb = 10, bias 15; bfloat16: fb = 7, bias 127.  Written from the format    */
+/* definitions with exact double arithmetic.                                 */
+/* ------------------------------------------------------------------------ */
+static int fmt_fb(int dtype) { return dtype == LCQO_F16 ? 10 : 7; }
+static int fmt_bias(int dtype) { return dtype == LCQO_F16 ? 15 : 127; }
+
+/* The value of a 16-bit pattern as a float (exact: both formats are subsets
+ * of binary32).  NaN keeps its sign and fraction bits at the top of the
+ * float's fraction. */
+static float widen16(uint16_t h, int fb, int bias) {
+    const uint32_t eall = (1u << (15 - fb)) - 1u;
+    const uint32_t s = (uint32_t)h >> 15, E = ((uint32_t)h >> fb) & eall, f = (uint32_t)h & ((1u << fb) - 1u);
+    if (E == eall) return f32_from((s << 31) | 0x7F800000u | (f << (23 - fb)));
+    double v = (E == 0u) ? ldexp((double)f, 1 - bias - fb) : ldexp((double)(f + (1u << fb)), (int)E - bias - fb);
+    return (float)(s ? -v : v);
+}
+
+/* x (not NaN) rounded to nearest, ties to even, in the 16-bit format; raw
+ * bits.  Magnitudes whose rounding reaches 2^(emax+1) become infinity. */
+static uint16_t round16(float x, int fb, int bias) {
+    const uint32_t eall = (1u << (15 - fb)) - 1u;
+    const uint16_t sgn = signbit(x) ? 0x8000u : 0u;
+    const uint16_t inf = (uint16_t)(sgn | (eall << fb));
+    const double a = fabs((double)x);
+    if (isinf(a)) return inf;
+    if (a == 0.0) return sgn;
+    const int emin = 1 - bias, emax = (int)eall - 1 - bias;
+    int e;
+    frexp(a, &e);
+    e -= 1; /* a in [2^e, 2^(e+1)) */
+    if (e < emin) e = emin;
+    const double ulp = ldexp(1.0, e - fb);
+    const double r = rint(a / ulp) * ulp; /* a / ulp exact; rint rounds half to even */
+    if (r >= ldexp(1.0, emax + 1)) return inf;
+    if (r < ldexp(1.0, emin)) return (uint16_t)(sgn | (uint16_t)(r / ldexp(1.0, emin - fb)));
+    frexp(r, &e);
+    e -= 1;
+    const uint32_t f = (uint32_t)(r / ldexp(1.0, e - fb)) - (1u << fb);
+    return (uint16_t)(sgn | (uint16_t)(((uint32_t)(e + bias) << fb) | f));
+}
+
+/* The decoder's 16-bit output for a float reconstruction, as a float. */
+static float through16(float r, int dtype) {
+    return widen16(round16(r, fmt_fb(dtype), fmt_bias(dtype)), fmt_fb(dtype), fmt_bias(dtype));
+}
+
+void lcqo_widen16_array(int dtype, const uint16_t* h, float* out, uint64_t n) {
+    for (uint64_t i = 0; i < n; i++) out[i] = widen16(h[i], fmt_fb(dtype), fmt_bias(dtype));
+}
+
+void lcqo_round16_array(int dtype, const float* x, uint16_t* out, uint64_t n) {
+    for (uint64_t i = 0; i < n; i++) out[i] = round16(x[i], fmt_fb(dtype), fmt_bias(dtype));
+}
+
 /* ------------------------------------------------------------------------ */
 /* log2 / pow2 approximations (Sec. 3.2)                                     */
 /* ------------------------------------------------------------------------ */
@@ -195,7 +265,7 @@ static int user_bound_ok(double eb) { return eb > 0.0 && isfinite(eb); }
  * the bound).  Returns 1 iff every derived constant is finite and normal. */
 static int derive_abs(int dtype, double eb_abs, lcqo_consts* c) {
     c->eb_abs = eb_abs;
-    if (dtype == LCQO_F32) {
+    if (dtype != LCQO_F64) { /* float32 and the 16-bit formats (R11): float constants */
         float ebT = rd_f32(eb_abs);
         if (fpclassify(ebT) != FP_NORMAL) return 0;
         float eb2 = 2.0f * ebT;
@@ -217,7 +287,7 @@ static int derive_abs(int dtype, double eb_abs, lcqo_consts* c) {
 
 int lcqo_consts_abs(int dtype, double eb, lcqo_consts* c) {
     memset(c, 0, sizeof(*c));
-    if (dtype != LCQO_F32 && dtype != LCQO_F64) return LCQO_BAD_ARG;
+    if (!dtype_ok(dtype)) return LCQO_BAD_ARG;
     c->dtype = dtype; c->bound = LCQO_ABS; c->eb = eb;
     if (!user_bound_ok(eb)) return LCQO_BAD_BOUND;
     return derive_abs(dtype, eb, c) ? LCQO_OK : LCQO_BAD_BOUND;
@@ -226,10 +296,10 @@ int lcqo_consts_abs(int dtype, double eb, lcqo_consts* c) {
 /* Reading R4 (REL constants). */
 int lcqo_consts_rel(int dtype, double eb, lcqo_consts* c) {
     memset(c, 0, sizeof(*c));
-    if (dtype != LCQO_F32 && dtype != LCQO_F64) return LCQO_BAD_ARG;
+    if (!dtype_ok(dtype)) return LCQO_BAD_ARG;
     c->dtype = dtype; c->bound = LCQO_REL; c->eb = eb;
     if (!user_bound_ok(eb)) return LCQO_BAD_BOUND;
-    if (dtype == LCQO_F32) {
+    if (dtype != LCQO_F64) { /* float32 and the 16-bit formats (R11) */
         float e = rd_f32(eb);
         if (fpclassify(e) != FP_NORMAL) return LCQO_BAD_BOUND;
         float onep = 1.0f + e;
@@ -263,7 +333,10 @@ void lcqo_range(int dtype, const void* x, uint64_t n, int32_t* any_finite, doubl
     int found = 0;
     double lo = 0.0, hi = 0.0;
     for (uint64_t i = 0; i < n; i++) {
-        double v = (dtype == LCQO_F32) ? (double)((const float*)x)[i] : ((const double*)x)[i];
+        double v;
+        if (dtype == LCQO_F32) v = (double)((const float*)x)[i];
+        else if (dtype == LCQO_F64) v = ((const double*)x)[i];
+        else v = (double)widen16(((const uint16_t*)x)[i], fmt_fb(dtype), fmt_bias(dtype));
         if (!isfinite(v)) continue;
         if (!found) { lo = v; hi = v; found = 1; continue; }
         if (v < lo) lo = v;
@@ -277,7 +350,7 @@ void lcqo_range(int dtype, const void* x, uint64_t n, int32_t* any_finite, doubl
 int lcqo_consts_noa_from_range(int dtype, double eb, int32_t any_finite, double mn, double mx,
                                lcqo_consts* c) {
     memset(c, 0, sizeof(*c));
-    if (dtype != LCQO_F32 && dtype != LCQO_F64) return LCQO_BAD_ARG;
+    if (!dtype_ok(dtype)) return LCQO_BAD_ARG;
     c->dtype = dtype; c->bound = LCQO_NOA; c->eb = eb;
     if (!user_bound_ok(eb)) return LCQO_BAD_BOUND;
     if (!any_finite) { c->all_outliers = 1; return LCQO_OK; }
@@ -295,7 +368,7 @@ int lcqo_consts_noa_from_range(int dtype, double eb, int32_t any_finite, double 
 int lcqo_consts_noa(int dtype, double eb, const void* x, uint64_t n, lcqo_consts* c) {
     int32_t any;
     double mn, mx;
-    if (dtype != LCQO_F32 && dtype != LCQO_F64) { memset(c, 0, sizeof(*c)); return LCQO_BAD_ARG; }
+    if (!dtype_ok(dtype)) { memset(c, 0, sizeof(*c)); return LCQO_BAD_ARG; }
     lcqo_range(dtype, x, n, &any, &mn, &mx);
     return lcqo_consts_noa_from_range(dtype, eb, any, mn, mx, c);
 }
@@ -383,8 +456,58 @@ static int rel_elem_f64(double x, const lcqo_consts* c, int32_t* bin_out) {
     return 1;
 }
 
+/* 16-bit ABS / NOA (reading R11): the float recipe of abs_elem_f32 on the
+ * widened value; the check tests the decoder's 16-bit reconstruction. */
+static int abs_elem_16(uint16_t h, const lcqo_consts* c, int32_t* bin_out) {
+    const float inv = (float)c->inv, eb2 = (float)c->eb2, ebT = (float)c->ebT;
+    float x = widen16(h, fmt_fb(c->dtype), fmt_bias(c->dtype));
+    float q = x * inv;
+    if (!(fabsf(q) < (float)MAXBIN_ABS)) return 0;
+    int32_t bin = (int32_t)rintf(q);
+    if ((bin >= MAXBIN_ABS) || (bin <= -MAXBIN_ABS)) return 0;
+    float recon = (float)bin * eb2;
+    float r = through16(recon, c->dtype);
+    if (!(fabsf(x - r) <= ebT)) return 0;
+    *bin_out = bin;
+    return 1;
+}
+
+/* 16-bit REL (reading R11): rel_elem_f32 on the widened value, accepting the
+ * decoder's 16-bit magnitude RN16(m) in place of m. */
+static int rel_elem_16(uint16_t h, const lcqo_consts* c, int32_t* bin_out) {
+    const float inv_l = (float)c->inv_l, step = (float)c->step, chk = (float)c->chk;
+    float x = widen16(h, fmt_fb(c->dtype), fmt_bias(c->dtype));
+    uint32_t u = f32_bits(x);
+    uint32_t s = u >> 31;
+    uint32_t E = (u >> 23) & 0xFFu;
+    if (E == 0u || E == 0xFFu) return 0; /* zero, float denormal, Inf, NaN */
+    float a = fabsf(x);
+    float L = lcqo_log2approx_f32(a);
+    float q = L * inv_l;
+    if (!(fabsf(q) < (float)MAXBIN_REL)) return 0;
+    int32_t b = (int32_t)rintf(q);
+    if ((b >= MAXBIN_REL) || (b <= -MAXBIN_REL)) return 0;
+    float Lr = (float)b * step;
+    float bb = Lr + 127.0f;
+    if (!(bb >= 1.0f && bb < 255.0f)) return 0;
+    float m = through16(lcqo_pow2approx_f32(Lr), c->dtype);
+    if (!(a <= 2.0f * m && m <= 2.0f * a)) return 0;
+    float d = fabsf(a - m);
+    float lo = (a < m) ? a : m;
+    float sc = (lo < 0x1p-62f) ? 0x1p64f : 1.0f;
+    float t = (lo * sc) * chk;
+    if (!(t >= FLT_MIN)) return 0;
+    if (!(d * sc <= t)) return 0;
+    *bin_out = (int32_t)(((uint32_t)b << 1) | s);
+    return 1;
+}
+
 static int quant_elem(const lcqo_consts* c, const void* x, uint64_t i, int32_t* bin) {
     if (c->all_outliers) return 0;
+    if (is_16bit(c->dtype)) {
+        uint16_t h = ((const uint16_t*)x)[i];
+        return (c->bound == LCQO_REL) ? rel_elem_16(h, c, bin) : abs_elem_16(h, c, bin);
+    }
     if (c->dtype == LCQO_F32) {
         float v = ((const float*)x)[i];
         return (c->bound == LCQO_REL) ? rel_elem_f32(v, c, bin) : abs_elem_f32(v, c, bin);
@@ -421,7 +544,8 @@ static double recon_f64(const lcqo_consts* c, int32_t bin) {
 /* ------------------------------------------------------------------------ */
 
 /* Returns the number of outliers.  bins[n], mask[ceil(n/32)], payload[cap]
- * (uint32 bits for float32 data, uint64 bits for float64 data).  Payload
+ * (uint32 bits for float32 data, uint64 bits for float64 data, uint16 bits
+ * for the 16-bit formats).  Payload
  * writes stop at cap; the count is always complete. */
 uint64_t lcqo_quantize(const lcqo_consts* c, const void* x, uint64_t n, int32_t* bins,
                        uint32_t* mask, void* payload, uint64_t cap) {
@@ -438,8 +562,10 @@ uint64_t lcqo_quantize(const lcqo_consts* c, const void* x, uint64_t n, int32_t*
             if (count < cap) {
                 if (c->dtype == LCQO_F32)
                     ((uint32_t*)payload)[count] = ((const uint32_t*)x)[i];
-                else
+                else if (c->dtype == LCQO_F64)
                     ((uint64_t*)payload)[count] = ((const uint64_t*)x)[i];
+                else
+                    ((uint16_t*)payload)[count] = ((const uint16_t*)x)[i];
             }
             count++;
         }
@@ -452,7 +578,10 @@ void lcqo_dequantize(const lcqo_consts* c, const int32_t* bins, const uint32_t* 
     uint64_t k = 0;
     for (uint64_t i = 0; i < n; i++) {
         int outlier = (mask[i >> 5] >> (i & 31u)) & 1u;
-        if (c->dtype == LCQO_F32) {
+        if (is_16bit(c->dtype)) { /* R11: the float reconstruction, rounded */
+            if (outlier) ((uint16_t*)out)[i] = ((const uint16_t*)payload)[k++];
+            else ((uint16_t*)out)[i] = round16(recon_f32(c, bins[i]), fmt_fb(c->dtype), fmt_bias(c->dtype));
+        } else if (c->dtype == LCQO_F32) {
             if (outlier) ((uint32_t*)out)[i] = ((const uint32_t*)payload)[k++];
             else ((float*)out)[i] = recon_f32(c, bins[i]);
         } else {
@@ -487,6 +616,7 @@ static int abs_elem_unprotected(const lcqo_consts* c, const void* x, uint64_t i,
 
 uint64_t lcqo_quantize_unprotected(const lcqo_consts* c, const void* x, uint64_t n, int32_t* bins,
                                    uint32_t* mask, void* payload, uint64_t cap) {
+    if (c->dtype != LCQO_F32 && c->dtype != LCQO_F64) return UINT64_MAX; /* float / double only */
     uint64_t words = (n + 31u) / 32u;
     for (uint64_t w = 0; w < words; w++) mask[w] = 0u;
     uint64_t count = 0;
@@ -555,11 +685,14 @@ static int abs_diff_le(double x, double y, double e) {
 
 static int same_bits(int dtype, const void* x, const void* y, uint64_t i) {
     if (dtype == LCQO_F32) return ((const uint32_t*)x)[i] == ((const uint32_t*)y)[i];
-    return ((const uint64_t*)x)[i] == ((const uint64_t*)y)[i];
+    if (dtype == LCQO_F64) return ((const uint64_t*)x)[i] == ((const uint64_t*)y)[i];
+    return ((const uint16_t*)x)[i] == ((const uint16_t*)y)[i];
 }
 
 static double load_as_f64(int dtype, const void* p, uint64_t i) {
-    return (dtype == LCQO_F32) ? (double)((const float*)p)[i] : ((const double*)p)[i];
+    if (dtype == LCQO_F32) return (double)((const float*)p)[i];
+    if (dtype == LCQO_F64) return ((const double*)p)[i];
+    return (double)widen16(((const uint16_t*)p)[i], fmt_fb(dtype), fmt_bias(dtype));
 }
 
 /* Number of elements violating |x - x'| <= eb (ABS, Sec. 2.1.1; NOA uses
