@@ -31,7 +31,8 @@
  *     error, re-initialise the workspace.
  *   - n = 0 is legal.
  *
- * Compressed representation of an array of n values of type T (float or double):
+ * Compressed representation of an array of n values of type T (float, double,
+ * or a 16-bit format, see lcq_dtype):
  *   bins     int32[n]      quantization bins; 0 where the value is an outlier.
  *                          ABS/NOA: the bin b; REL: 2*b + signbit(x).
  *   mask     uint32[ceil(n/32)]  bit (i & 31) of word (i >> 5) is 1 iff value i
@@ -52,7 +53,19 @@
 extern "C" {
 #endif
 
-typedef enum { LCQ_F32 = 0, LCQ_F64 = 1 } lcq_dtype;
+/* Data types.  LCQ_F32 and LCQ_F64 are the paper's float and double.  The
+ * 16-bit formats LCQ_F16 (IEEE binary16) and LCQ_BF16 (bfloat16) go beyond
+ * the paper: each value widens exactly to a float and takes the float recipe
+ * with float constants; the check of Sec. 3.1 tests the value the decoder
+ * outputs, i.e. the float reconstruction rounded to nearest-even in the
+ * 16-bit format.  REL treats the widened float's zeros, denormals (so
+ * bfloat16 subnormals), Inf and NaN as outliers.  Outliers are stored as raw
+ * 16-bit patterns.  The 16-bit formats are accepted by lcq_quantize,
+ * lcq_dequantize, lcq_quantize_noalloc, lcq_finite_range,
+ * lcq_quantize_noa_range, lcq_quantize_host(_batch) and the tuning calls
+ * (quantize tile shapes 0 and 1, dequantize shapes 1 and 5); the batched
+ * launch and the ablations take LCQ_F32 / LCQ_F64 only (LCQ_ERR_ARG). */
+typedef enum { LCQ_F32 = 0, LCQ_F64 = 1, LCQ_F16 = 2, LCQ_BF16 = 3 } lcq_dtype;
 
 /* Error-bound types, Sec. 2.1: point-wise absolute (ABS), relative (REL) and
  * normalised absolute (NOA, the ABS bound eb * (max - min)). */

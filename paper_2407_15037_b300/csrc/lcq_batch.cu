@@ -515,9 +515,10 @@ lcq_status lcq_batch_prepare(const lcq_batch_item* h_items, uint32_t count, void
     uint64_t tiles = 0;
     for (uint32_t i = 0; i < count; i++) {
         const lcq_batch_item& it = h_items[i];
-        const lcq_status st = check_quantize_args((lcq_dtype)it.dtype, (lcq_bound_type)it.bound_type, it.eb,
-                                                  it.d_in, it.n, it.d_bins, it.d_mask, it.d_outliers,
-                                                  it.outlier_capacity, it.d_hdr);
+        lcq_status st = check_quantize_args((lcq_dtype)it.dtype, (lcq_bound_type)it.bound_type, it.eb,
+                                            it.d_in, it.n, it.d_bins, it.d_mask, it.d_outliers,
+                                            it.outlier_capacity, it.d_hdr);
+        if (st == LCQ_OK && it.dtype != LCQ_F32 && it.dtype != LCQ_F64) st = LCQ_ERR_ARG;  // float / double only
         if (st != LCQ_OK) {
             h_info->bad_item = i;
             return st;

@@ -21,6 +21,9 @@
 #include <cfloat>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "../../include/lcq.h"
 
 namespace lcq {
@@ -46,6 +49,9 @@ struct Ty;
 template <>
 struct Ty<float> {
     using U = uint32_t;
+    using C = float;  // arithmetic type
+    using K = uint32_t;  // order key of the NOA range
+    static constexpr uint32_t kDtype = LCQ_F32;
     static constexpr int kP = 23;
     static constexpr int kBias = 127;
     static constexpr U kExpAll = 0xFFu;
@@ -67,11 +73,15 @@ struct Ty<float> {
     static __device__ __forceinline__ float rescale() { return 0x1p64f; }
     static __device__ __forceinline__ float top_bb() { return 255.0f; }
     static __device__ __forceinline__ float bias_f() { return 127.0f; }
+    static __device__ __forceinline__ double to_f64(float a) { return (double)a; }
 };
 
 template <>
 struct Ty<double> {
     using U = uint64_t;
+    using C = double;
+    using K = uint64_t;
+    static constexpr uint32_t kDtype = LCQ_F64;
     static constexpr int kP = 52;
     static constexpr int kBias = 1023;
     static constexpr U kExpAll = 0x7FFull;
@@ -93,7 +103,59 @@ struct Ty<double> {
     static __device__ __forceinline__ double rescale() { return 0x1p512; }
     static __device__ __forceinline__ double top_bb() { return 2047.0; }
     static __device__ __forceinline__ double bias_f() { return 1023.0; }
+    static __device__ __forceinline__ double to_f64(double a) { return a; }
 };
+
+// 16-bit storage formats (IEEE binary16 and bfloat16).  The paper works in
+// float and double; here a 16-bit value widens exactly to a float, takes the
+// float recipe, and the check of Sec. 3.1 tests the decoder's output: the
+// float reconstruction rounded to nearest-even in the 16-bit format.  The
+// structs hold raw bit patterns; all arithmetic is float32.
+struct f16s {
+    uint16_t u;
+    __host__ __device__ constexpr f16s(int z = 0) : u((uint16_t)z) {}
+};
+struct bf16s {
+    uint16_t u;
+    __host__ __device__ constexpr bf16s(int z = 0) : u((uint16_t)z) {}
+};
+
+template <typename S, uint32_t DT, int P, uint16_t EALL>
+struct Ty16 {
+    using U = uint16_t;
+    using C = float;
+    using K = uint32_t;  // 16-bit order keys, widened for the warp shuffles
+    static constexpr uint32_t kDtype = DT;
+    static constexpr int kP = P;
+    static constexpr U kExpAll = EALL;
+    static __device__ __forceinline__ U bits(S a) { return a.u; }
+    static __device__ __forceinline__ S from_bits(U u) { return S((int)u); }
+};
+
+template <>
+struct Ty<f16s> : Ty16<f16s, LCQ_F16, 10, 0x1F> {
+    static __device__ __forceinline__ float widen(f16s a) { return __half2float(__ushort_as_half(a.u)); }
+    static __device__ __forceinline__ f16s narrow(float x) {
+        return f16s((int)__half_as_ushort(__float2half_rn(x)));
+    }
+    static __device__ __forceinline__ double to_f64(f16s a) { return (double)widen(a); }
+};
+
+template <>
+struct Ty<bf16s> : Ty16<bf16s, LCQ_BF16, 7, 0xFF> {
+    static __device__ __forceinline__ float widen(bf16s a) { return __uint_as_float((uint32_t)a.u << 16); }
+    static __device__ __forceinline__ bf16s narrow(float x) {
+        return bf16s((int)__bfloat16_as_ushort(__float2bfloat16_rn(x)));
+    }
+    static __device__ __forceinline__ double to_f64(bf16s a) { return (double)widen(a); }
+};
+
+// Arithmetic type of a storage type: float for float and the 16-bit formats.
+template <typename T>
+using CT = typename Ty<T>::C;
+
+template <typename T>
+__host__ __device__ constexpr bool is16() { return sizeof(T) == 2; }
 
 // ---------------------------------------------------------------------------
 // Exact replacements for conversions (the float<->int conversions run on a
@@ -736,10 +798,61 @@ __device__ __forceinline__ double rel_recon_f64(int32_t bin, const Consts<double
     return dfrom(pow2approx_dbits(dbits(bb)) | ((uint64_t)(bin & 1) << 63));
 }
 
-// One value: the float32 recipes above, or the float64 ones with few FP64 ops.
+// 16-bit ABS / NOA: abs_quant's float recipe on the widened value; the check
+// tests the decoder's output, the reconstruction rounded to the 16-bit format.
+// The subtraction is exact wherever the comparison is close (the two values
+// lie within a factor of about 2 of each other and have at most 11
+// significant bits, or the reconstruction is 0).
+template <typename T>
+__device__ __forceinline__ bool abs_quant16(T h, const Consts<float>& c, int32_t& bin) {
+    using F = Ty<T>;
+    const float x = F::widen(h);
+    const float q = __fmul_rn(x, c.inv);
+    if (!(fabsf(q) < (float)kMaxBinAbs)) return false;
+    int32_t b;
+    float bf;
+    Cv<float>::round(q, b, bf);
+    if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
+    const float r = F::widen(F::narrow(__fmul_rn(bf, c.scale)));
+    if (!(fabsf(__fsub_rn(x, r)) <= c.ebT)) return false;
+    bin = b;
+    return true;
+}
+
+// 16-bit REL: rel_quant's float recipe on the widened value, accepting the
+// decoder's magnitude RN16(m) in place of m (an Inf or 0 fails the ratio
+// test).  Float zeros, denormals (bfloat16 subnormals), Inf and NaN are
+// outliers; binary16 subnormals are normal floats and are quantized.
+template <typename T>
+__device__ __forceinline__ bool rel_quant16(T h, const Consts<float>& c, int32_t& bin) {
+    using F = Ty<T>;
+    const uint32_t u = __float_as_uint(F::widen(h));
+    const uint32_t E = (u >> 23) & 0xFFu;
+    if (E == 0u || E == 0xFFu) return false;
+    const float a = __uint_as_float(u & 0x7FFFFFFFu);
+    const float q = __fmul_rn(log2approx<float>(u), c.inv);
+    if (!(fabsf(q) < (float)kMaxBinRel)) return false;
+    int32_t b;
+    float bf;
+    Cv<float>::round(q, b, bf);
+    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
+    const float bb = __fadd_rn(__fmul_rn(bf, c.scale), 127.0f);
+    if (!(bb >= 1.0f && bb < 255.0f)) return false;
+    const float m = F::widen(F::narrow(__uint_as_float(pow2approx_bits<float>(bb))));
+    if (!rel_accept<float>(a, m, c)) return false;
+    bin = (int32_t)(((uint32_t)b << 1) | (u >> 31));
+    return true;
+}
+
+// One value: the float32 recipes above, the float64 ones with few FP64 ops,
+// or the 16-bit ones.
 template <typename T, int MODE>
-__device__ __forceinline__ bool quant1(T x, const Consts<T>& c, int32_t& bin) {
-    if constexpr (MODE == kModeRelLib) {
+__device__ __forceinline__ bool quant1(T x, const Consts<CT<T>>& c, int32_t& bin) {
+    if constexpr (is16<T>()) {
+        static_assert(MODE == LCQ_ABS || MODE == LCQ_REL, "16-bit formats: ABS/NOA and REL only");
+        if constexpr (MODE == LCQ_REL) return rel_quant16<T>(x, c, bin);
+        else return abs_quant16<T>(x, c, bin);
+    } else if constexpr (MODE == kModeRelLib) {
         return rel_quant_lib<T>(x, c, bin);
     } else if constexpr (sizeof(T) == 8) {
         if constexpr (MODE == LCQ_REL) return rel_quant_f64(x, c, bin);
@@ -751,7 +864,7 @@ __device__ __forceinline__ bool quant1(T x, const Consts<T>& c, int32_t& bin) {
 }
 
 template <typename T, int MODE>
-__device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<T>& c, int32_t b[4]) {
+__device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<CT<T>>& c, int32_t b[4]) {
     if constexpr (sizeof(T) == 4 && MODE == LCQ_REL) {
         return rel_quant4_f32(x, c, b);
     } else if constexpr (sizeof(T) == 4 && MODE != kModeRelLib) {
@@ -785,6 +898,14 @@ template <typename T>
 __device__ __forceinline__ T recon1(bool rel, int32_t bin, const Consts<T>& c) {
     if constexpr (sizeof(T) == 8) return rel ? rel_recon_f64(bin, c) : abs_recon_f64(bin, c);
     else return rel ? rel_recon<T>(bin, c) : abs_recon<T>(bin, c);
+}
+
+// The decoder's output value: recon1, rounded to the 16-bit format for the
+// 16-bit formats.
+template <typename T>
+__device__ __forceinline__ T recon_out(bool rel, int32_t bin, const Consts<CT<T>>& c) {
+    if constexpr (is16<T>()) return Ty<T>::narrow(recon1<float>(rel, bin, c));
+    else return recon1<T>(rel, bin, c);
 }
 
 // ---------------------------------------------------------------------------

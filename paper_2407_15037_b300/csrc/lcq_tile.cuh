@@ -67,6 +67,32 @@ struct Vec4<double> {
     }
 };
 
+// 16-bit formats: 4 values = 8 bytes.
+template <typename T>
+struct Vec4x16 {
+    static __device__ __forceinline__ void split(uint2 a, T v[4]) {
+        v[0] = T((int)(a.x & 0xFFFFu)); v[1] = T((int)(a.x >> 16));
+        v[2] = T((int)(a.y & 0xFFFFu)); v[3] = T((int)(a.y >> 16));
+    }
+    static __device__ __forceinline__ void load(const T* p, T v[4]) {
+        split(__ldcs(reinterpret_cast<const uint2*>(p)), v);
+    }
+    static __device__ __forceinline__ void load_shared(const T* p, T v[4]) {
+        split(*reinterpret_cast<const uint2*>(p), v);
+    }
+    static __device__ __forceinline__ void load_cached(const T* p, T v[4]) {
+        split(*reinterpret_cast<const uint2*>(p), v);
+    }
+    static __device__ __forceinline__ void store(T* p, const T v[4]) {
+        __stcs(reinterpret_cast<uint2*>(p), make_uint2((uint32_t)v[0].u | ((uint32_t)v[1].u << 16),
+                                                      (uint32_t)v[2].u | ((uint32_t)v[3].u << 16)));
+    }
+};
+template <>
+struct Vec4<f16s> : Vec4x16<f16s> {};
+template <>
+struct Vec4<bf16s> : Vec4x16<bf16s> {};
+
 template <typename T, int VPT>
 __device__ __forceinline__ void load4(const T* sbuf_tile, const T* gin, bool from_smem, int off,
                                       uint64_t e0, uint64_t n, T x[4]) {
@@ -131,7 +157,7 @@ __device__ __forceinline__ uint32_t scan_mask_words(const uint32_t* s_words, uin
 template <typename T, int MODE, int VPT>
 __device__ __forceinline__ void quantize_subtile(const T* st, const T* gin, bool from_smem,
                                                  uint64_t nvalid, int32_t* gbins, uint32_t* s_words,
-                                                 int word_base, const Consts<T>& c) {
+                                                 int word_base, const Consts<CT<T>>& c) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wbase = word_base + warp * 4 + (lane >> 3);
     // 4-value outlier nibbles of 8 lanes -> one mask word
@@ -274,40 +300,42 @@ __device__ __forceinline__ void write_outliers(const uint32_t* s_words, const ui
 // the bound derived from the range on the device.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ typename Ty<T>::U order_key(typename Ty<T>::U u) {
+__device__ __forceinline__ typename Ty<T>::K order_key(typename Ty<T>::U u) {
     using U = typename Ty<T>::U;
-    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
-    return (u & sign) ? ~u : (u | sign);
+    constexpr U sign = (U)((U)1 << (sizeof(U) * 8 - 1));
+    return (typename Ty<T>::K)((u & sign) ? (U)~u : (U)(u | sign));
 }
 template <typename T>
-__device__ __forceinline__ typename Ty<T>::U key_to_bits(typename Ty<T>::U k) {
+__device__ __forceinline__ typename Ty<T>::U key_to_bits(typename Ty<T>::K key) {
     using U = typename Ty<T>::U;
-    constexpr U sign = (U)1 << (sizeof(U) * 8 - 1);
-    return (k & sign) ? (k & ~sign) : ~k;
+    constexpr U sign = (U)((U)1 << (sizeof(U) * 8 - 1));
+    const U k = (U)key;
+    return (k & sign) ? (U)(k & (U)~sign) : (U)~k;
 }
 
 template <typename T>
-__device__ __forceinline__ void minmax_accum(T x, typename Ty<T>::U& lo, typename Ty<T>::U& hi) {
+__device__ __forceinline__ void minmax_accum(T x, typename Ty<T>::K& lo, typename Ty<T>::K& hi) {
     using F = Ty<T>;
     using U = typename F::U;
     const U u = F::bits(x);
     if (((u >> F::kP) & F::kExpAll) == F::kExpAll) return;  // Inf / NaN
-    const U k = order_key<T>(u);
+    const typename F::K k = order_key<T>(u);
     lo = k < lo ? k : lo;
     hi = k > hi ? k : hi;
 }
 
-template <typename T>
-__device__ __forceinline__ void noa_finalize(lcq_header* h, bool any, T mn, T mx, double eb) {
-    using F = Ty<T>;
+// C: the arithmetic type (float constants for float32 and the 16-bit
+// formats, double constants for float64); mn, mx: the finite range, exact.
+template <typename C>
+__device__ __forceinline__ void noa_finalize(lcq_header* h, bool any, double mn, double mx, double eb) {
     uint32_t mode = 1;
     double R = 0.0, eb_abs = 0.0;
     uint64_t ebT_b = 0, eb2_b = 0, inv_b = 0;
     if (any) {
-        R = __dsub_rd((double)mx, (double)mn);
+        R = __dsub_rd(mx, mn);
         if (R == 0.0) R = 0.0;  // a zero range is +0, whichever signed zeros min and max are
         eb_abs = __dmul_rd(eb, R);
-        if (sizeof(T) == 4) {
+        if (sizeof(C) == 4) {
             const float ebT = __double2float_rd(eb_abs);
             const float eb2 = __fmul_rn(2.0f, ebT);
             const float inv = __fdiv_rn(1.0f, eb2);

@@ -14,7 +14,11 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblcq.so")
 
-F32, F64 = 0, 1
+F32, F64, F16, BF16 = 0, 1, 2, 3
+DTYPE_CODES = {torch.float32: F32, torch.float64: F64, torch.float16: F16, torch.bfloat16: BF16}
+# raw-bit tensor type of the outlier payload per data type
+PAYLOAD_DTYPES = {torch.float32: torch.int32, torch.float64: torch.int64, torch.float16: torch.int16,
+                  torch.bfloat16: torch.int16}
 ABS, REL, NOA = 0, 1, 2
 BOUNDS = {"abs": ABS, "rel": REL, "noa": NOA}
 STATUS_CAPACITY, STATUS_TIMEOUT, STATUS_HEADER = 1, 2, 4
@@ -149,11 +153,11 @@ def _check(code, what):
 
 
 def _dtype_code(t):
-    if t.dtype == torch.float32:
-        return F32
-    if t.dtype == torch.float64:
-        return F64
-    raise TypeError("lcq: float32 or float64 tensor required, got %s" % t.dtype)
+    try:
+        return DTYPE_CODES[t.dtype]
+    except KeyError:
+        raise TypeError("lcq: float32, float64, float16 or bfloat16 tensor required, got %s"
+                        % t.dtype) from None
 
 
 def _bound_code(bound):
@@ -189,7 +193,7 @@ class Quantized:
     """Device-resident compressed form (see include/lcq.h)."""
     bins: torch.Tensor      # int32[n]
     mask: torch.Tensor      # int32[ceil(n/32)] (raw uint32 words)
-    outliers: torch.Tensor  # int32 / int64 [capacity] raw bit patterns
+    outliers: torch.Tensor  # int32 / int64 / int16 [capacity] raw bit patterns
     header: torch.Tensor    # uint8[HEADER_BYTES] (struct lcq_header)
     n: int
     dtype: torch.dtype
@@ -204,7 +208,9 @@ class Quantized:
 
 def alloc_outputs(n, dtype, device, outlier_capacity=None):
     cap = n if outlier_capacity is None else int(outlier_capacity)
-    pay_dtype = torch.int32 if dtype == torch.float32 else torch.int64
+    if dtype not in PAYLOAD_DTYPES:
+        raise TypeError("lcq: float32, float64, float16 or bfloat16 required, got %s" % dtype)
+    pay_dtype = PAYLOAD_DTYPES[dtype]
     return Quantized(
         bins=torch.empty(n, dtype=torch.int32, device=device),
         mask=torch.empty((n + 31) // 32, dtype=torch.int32, device=device),
@@ -226,8 +232,9 @@ def quantize_into(x, bound, eb, q, ws, stream=None):
 
 
 def quantize(x, bound, eb, outlier_capacity=None, ws=None, stream=None):
-    """Quantize a contiguous float32/float64 CUDA tensor with bound type
-    'abs' | 'rel' | 'noa' and bound eb.  Returns the device-resident result."""
+    """Quantize a contiguous float32 / float64 / float16 / bfloat16 CUDA tensor
+    with bound type 'abs' | 'rel' | 'noa' and bound eb.  Returns the
+    device-resident result."""
     _require_cuda(x)
     x = x.contiguous().reshape(-1)
     q = alloc_outputs(x.numel(), x.dtype, x.device, outlier_capacity)

@@ -93,7 +93,12 @@ def test_host_side_argument_errors_need_no_gpu(lib):
     assert nr(0, 1, 0.0, float("nan")) == 1
     assert nr(0, 1, 0.0, 0.1) == 1          # 0.1 is not a float32 value
     assert lib.lcq_quantize_noa_range(0, -1.0, 1, 0.0, 1.0, None, 0, None, None, None, 0, h, p, 4000, None) == 2
-    assert lib.lcq_finite_range(3, None, 0, p, p, 4000, None) == 1
+    assert lib.lcq_finite_range(7, None, 0, p, p, 4000, None) == 1
+    # 16-bit formats: the range values must be values of the format
+    assert nr(2, 1, 0.0, 0.1) == 1               # not a binary16 value
+    assert nr(2, 1, 0.0, 65520.0) == 1           # beyond binary16's largest value
+    assert nr(3, 1, 0.0, 1.0 + 2.0 ** -10) == 1  # not a bfloat16 value (7 fraction bits)
+    assert nr(4, 1, 0.0, 1.0) == 1               # no such data type
     assert lib.lcq_finite_range(0, None, 0, None, p, 4000, None) == 1
     assert lib.lcq_finite_range(0, None, 0, ctypes.c_void_p(p.value + 4), p, 4000, None) == 1
     assert lib.lcq_workspace_size(0, 0, 1 << 31) > lib.lcq_workspace_size(0, 0, 1 << 20)
