@@ -478,6 +478,18 @@ def run_ours(args, world, rank, local):
             extra["f64_256_%s_1e-3" % bound]["variant"] = P.lcq.get_variant(0, P.F64, bound)
         del q64, w64
         del x64
+        # the float32 512^3 field rounded to binary16 / bfloat16
+        for fmt, dt in (("f16", torch.float16), ("bf16", torch.bfloat16)):
+            xh = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device=dev).to(dt)
+            qh = P.alloc_outputs(xh.numel(), dt, dev)
+            wh = P.new_workspace(xh.numel(), dev)
+            code = P.lcq.DTYPE_CODES[dt]
+            for bound in BOUNDS:
+                P.lcq.autotune_quantize(xh, bound, 1e-3, qh, wh, reps=3, stream=stream)
+                key = "%s_512_%s_1e-3" % (fmt, bound)
+                extra[key] = time_calls(xh, bound, 1e-3)
+                extra[key]["variant"] = P.lcq.get_variant(0, code, bound)
+            del qh, wh, xh
         if args.batched:
             extra["batched_4096"] = run_batched(P, synth, dev, stream, args)
         if args.predictor:
@@ -751,14 +763,18 @@ def lsq_reference(train_bins, test_bins, N, m=40000, seed=0):
 def run_profile(args):
     """A short, fixed sequence of calls for ncu captures: three warm-up calls
     and one measured call of the chosen kind on the 512^3 float32 field (or
-    the float64 256^3 field, or the 2^28-value REL stress input)."""
+    the float64 256^3 field, the float32 field rounded to binary16 /
+    bfloat16, or the 2^28-value REL stress input)."""
     import paper_2407_15037_b300 as P
     import synth
     dev = torch.device("cuda", 0)
-    shape = SHAPE if args.profile_dtype == "f32" else (256, 256, 256)
-    dt = torch.float32 if args.profile_dtype == "f32" else torch.float64
+    shape = (256, 256, 256) if args.profile_dtype == "f64" else SHAPE
+    dt = {"f32": torch.float32, "f64": torch.float64, "f16": torch.float16,
+          "bf16": torch.bfloat16}[args.profile_dtype]
     if args.profile_input == "stress":
         x = synth.rel_stress(1 << 28, seed=0, device=dev).to(dt)
+    elif args.profile_dtype in ("f16", "bf16"):
+        x = synth.smooth_field(shape, dtype=torch.float32, seed=0, device=dev).to(dt)
     else:
         x = synth.smooth_field(shape, dtype=dt, seed=0, device=dev)
     q = P.alloc_outputs(x.numel(), x.dtype, dev)
@@ -779,7 +795,7 @@ def run_profile(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq"], default=None)
-    ap.add_argument("--profile-dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--profile-dtype", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--profile-input", choices=["smooth", "stress"], default="smooth")
     ap.add_argument("--profile-eb", type=float, default=1e-3)
     ap.add_argument("--gpus", type=int, default=1)

@@ -139,6 +139,11 @@ struct Ty<f16s> : Ty16<f16s, LCQ_F16, 10, 0x1F> {
         return f16s((int)__half_as_ushort(__float2half_rn(x)));
     }
     static __device__ __forceinline__ double to_f64(f16s a) { return (double)widen(a); }
+    static __device__ __forceinline__ void widen4(const f16s h[4], float v[4]) {
+        const float2 a = __half22float2(__halves2half2(__ushort_as_half(h[0].u), __ushort_as_half(h[1].u)));
+        const float2 b = __half22float2(__halves2half2(__ushort_as_half(h[2].u), __ushort_as_half(h[3].u)));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
 };
 
 template <>
@@ -148,6 +153,9 @@ struct Ty<bf16s> : Ty16<bf16s, LCQ_BF16, 7, 0xFF> {
         return bf16s((int)__bfloat16_as_ushort(__float2bfloat16_rn(x)));
     }
     static __device__ __forceinline__ double to_f64(bf16s a) { return (double)widen(a); }
+    static __device__ __forceinline__ void widen4(const bf16s h[4], float v[4]) {
+        for (int k = 0; k < 4; k++) v[k] = widen(h[k]);
+    }
 };
 
 // Arithmetic type of a storage type: float for float and the 16-bit formats.
@@ -410,6 +418,103 @@ __device__ __forceinline__ T rel_recon_lib(int32_t bin, const Consts<T>& c) {
     return F::from_bits(F::bits(m) | (s << (sizeof(U) * 8 - 1)));
 }
 
+// 16-bit ABS / NOA: abs_quant's float recipe on the widened value x; the
+// check tests the decoder's output, the reconstruction rounded to the 16-bit
+// format T.  The subtraction is exact wherever the comparison is close (the
+// two values lie within a factor of about 2 of each other and have at most
+// 11 significant bits, or the reconstruction is 0).
+template <typename T>
+__device__ __forceinline__ bool abs_quant16(float x, const Consts<float>& c, int32_t& bin) {
+    using F = Ty<T>;
+    const float q = __fmul_rn(x, c.inv);
+    if (!(fabsf(q) < (float)kMaxBinAbs)) return false;
+    int32_t b;
+    float bf;
+    Cv<float>::round(q, b, bf);
+    if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
+    const float r = F::widen(F::narrow(__fmul_rn(bf, c.scale)));
+    if (!(fabsf(__fsub_rn(x, r)) <= c.ebT)) return false;
+    bin = b;
+    return true;
+}
+
+// 16-bit REL: rel_quant's float recipe on the widened value, accepting the
+// decoder's magnitude RN16(m) in place of m (an Inf or 0 fails the ratio
+// test).  Float zeros, denormals (bfloat16 subnormals), Inf and NaN are
+// outliers; binary16 subnormals are normal floats and are quantized.
+template <typename T>
+__device__ __forceinline__ bool rel_quant16(float x, const Consts<float>& c, int32_t& bin) {
+    using F = Ty<T>;
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t E = (u >> 23) & 0xFFu;
+    if (E == 0u || E == 0xFFu) return false;
+    const float a = __uint_as_float(u & 0x7FFFFFFFu);
+    const float q = __fmul_rn(log2approx<float>(u), c.inv);
+    if (!(fabsf(q) < (float)kMaxBinRel)) return false;
+    int32_t b;
+    float bf;
+    Cv<float>::round(q, b, bf);
+    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
+    const float bb = __fadd_rn(__fmul_rn(bf, c.scale), 127.0f);
+    if (!(bb >= 1.0f && bb < 255.0f)) return false;
+    const float m = F::widen(F::narrow(__uint_as_float(pow2approx_bits<float>(bb))));
+    if (!rel_accept<float>(a, m, c)) return false;
+    bin = (int32_t)(((uint32_t)b << 1) | (u >> 31));
+    return true;
+}
+
+// What the four-value fast paths below do with a float reconstruction before
+// checking it: Keep32 (float32 data) leaves it; Round16<T> replaces it by the
+// decoder's 16-bit value, widened back (two packed conversions per four
+// values).  Each also names the per-value recipes of its data type, used
+// where the fast code does not apply.
+struct Keep32 {
+    static __device__ __forceinline__ void apply(float v[4]) {}
+    template <bool CHECK>
+    static __device__ __forceinline__ bool abs1(float x, const Consts<float>& c, int32_t& bin) {
+        return abs_quant<float, CHECK>(x, c, bin);
+    }
+    static __device__ __forceinline__ bool rel1(float x, const Consts<float>& c, int32_t& bin) {
+        return rel_quant<float>(x, c, bin);
+    }
+};
+
+template <typename T>
+struct Round16;
+
+template <typename T>
+struct Round16Base {
+    template <bool CHECK>
+    static __device__ __forceinline__ bool abs1(float x, const Consts<float>& c, int32_t& bin) {
+        static_assert(CHECK, "16-bit formats: the protected quantizer only");
+        return abs_quant16<T>(x, c, bin);
+    }
+    static __device__ __forceinline__ bool rel1(float x, const Consts<float>& c, int32_t& bin) {
+        return rel_quant16<T>(x, c, bin);
+    }
+};
+
+template <>
+struct Round16<f16s> : Round16Base<f16s> {
+    static __device__ __forceinline__ void apply(float v[4]) {
+        const float2 a = __half22float2(__floats2half2_rn(v[0], v[1]));
+        const float2 b = __half22float2(__floats2half2_rn(v[2], v[3]));
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+};
+
+template <>
+struct Round16<bf16s> : Round16Base<bf16s> {
+    static __device__ __forceinline__ void apply(float v[4]) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+        v[0] = __uint_as_float((uint32_t)__bfloat16_as_ushort(a.x) << 16);
+        v[1] = __uint_as_float((uint32_t)__bfloat16_as_ushort(a.y) << 16);
+        v[2] = __uint_as_float((uint32_t)__bfloat16_as_ushort(b.x) << 16);
+        v[3] = __uint_as_float((uint32_t)__bfloat16_as_ushort(b.y) << 16);
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Four values at a time (one 128-bit load), float32.  When every lane of the
 // warp has |q| < 2^22 for all four of its values -- the usual case -- one
@@ -421,7 +526,7 @@ __device__ __forceinline__ T rel_recon_lib(int32_t bin, const Consts<T>& c) {
 // integer overflow, |b| <= 2^22 < maxbin; the REL implications are listed at
 // rel_fast4_f32).  Returns the 4-bit outlier nibble; bins of outliers are 0.
 // ---------------------------------------------------------------------------
-template <bool CHECK = true>
+template <bool CHECK = true, typename R = Keep32>
 __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
     float q[4];
     bool small = true;
@@ -432,23 +537,26 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
     }
     uint32_t nb = 0;
     if (__all_sync(0xFFFFFFFFu, small)) {
+        int32_t bi[4];
+        float recon[4];
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             const float t = __fadd_rn(q[k], 0x1.8p23f);
-            const int32_t bi = __float_as_int(t) - 0x4B400000;
-            bool ok = true;
-            if constexpr (CHECK) {
-                const float recon = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
-                ok = fabsf(__fsub_rn(x[k], recon)) <= c.ebT;
-            }
-            b[k] = ok ? bi : 0;
+            bi[k] = __float_as_int(t) - 0x4B400000;
+            recon[k] = __fmul_rn(__fsub_rn(t, 0x1.8p23f), c.scale);
+        }
+        if constexpr (CHECK) R::apply(recon);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const bool ok = !CHECK || fabsf(__fsub_rn(x[k], recon[k])) <= c.ebT;
+            b[k] = ok ? bi[k] : 0;
             nb |= ok ? 0u : (1u << k);
         }
     } else {
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             int32_t bin = 0;
-            const bool ok = abs_quant<float, CHECK>(x[k], c, bin);
+            const bool ok = R::template abs1<CHECK>(x[k], c, bin);
             b[k] = ok ? bin : 0;
             nb |= ok ? 0u : (1u << k);
         }
@@ -490,7 +598,7 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
 //    or NaN; bb >= 255 makes m +Inf, a NaN, or a negative value (bit 31 set:
 //    then t = RN(lo chk) <= 0 < FLT_MIN); each of these fails d <= t or
 //    t >= FLT_MIN.
-template <bool RATIO, bool WIDE>
+template <bool RATIO, bool WIDE, typename R = Keep32>
 __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float q[4], const Consts<float>& c,
                                                   int32_t b[4]) {
     float a[4], m[4], lo[4], bb[4];
@@ -519,6 +627,10 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
         const float Lr = __fmul_rn(bf, c.scale);
         bb[k] = __fadd_rn(Lr, 127.0f);
         m[k] = __uint_as_float(__float2uint_rz(__fmul_rn(bb[k], 0x1p23f)));
+    }
+    R::apply(m);  // the decoder's magnitudes
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
         lo[k] = fminf(a[k], m[k]);
         tiny |= lo[k] < T;
     }
@@ -568,6 +680,7 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
     return nb;
 }
 
+template <typename R = Keep32>
 __device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Consts<float>& c, int32_t b[4]) {
     float q[4];
     bool small = true;
@@ -579,8 +692,8 @@ __device__ __forceinline__ uint32_t rel_quant4_f32(const float x[4], const Const
     }
     const bool narrow = __all_sync(0xFFFFFFFFu, small);
     if (c.chk <= 0.5f)
-        return narrow ? rel_fast4_f32<false, false>(x, q, c, b) : rel_fast4_f32<false, true>(x, q, c, b);
-    return narrow ? rel_fast4_f32<true, false>(x, q, c, b) : rel_fast4_f32<true, true>(x, q, c, b);
+        return narrow ? rel_fast4_f32<false, false, R>(x, q, c, b) : rel_fast4_f32<false, true, R>(x, q, c, b);
+    return narrow ? rel_fast4_f32<true, false, R>(x, q, c, b) : rel_fast4_f32<true, true, R>(x, q, c, b);
 }
 
 // ---------------------------------------------------------------------------
@@ -798,60 +911,14 @@ __device__ __forceinline__ double rel_recon_f64(int32_t bin, const Consts<double
     return dfrom(pow2approx_dbits(dbits(bb)) | ((uint64_t)(bin & 1) << 63));
 }
 
-// 16-bit ABS / NOA: abs_quant's float recipe on the widened value; the check
-// tests the decoder's output, the reconstruction rounded to the 16-bit format.
-// The subtraction is exact wherever the comparison is close (the two values
-// lie within a factor of about 2 of each other and have at most 11
-// significant bits, or the reconstruction is 0).
-template <typename T>
-__device__ __forceinline__ bool abs_quant16(T h, const Consts<float>& c, int32_t& bin) {
-    using F = Ty<T>;
-    const float x = F::widen(h);
-    const float q = __fmul_rn(x, c.inv);
-    if (!(fabsf(q) < (float)kMaxBinAbs)) return false;
-    int32_t b;
-    float bf;
-    Cv<float>::round(q, b, bf);
-    if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
-    const float r = F::widen(F::narrow(__fmul_rn(bf, c.scale)));
-    if (!(fabsf(__fsub_rn(x, r)) <= c.ebT)) return false;
-    bin = b;
-    return true;
-}
-
-// 16-bit REL: rel_quant's float recipe on the widened value, accepting the
-// decoder's magnitude RN16(m) in place of m (an Inf or 0 fails the ratio
-// test).  Float zeros, denormals (bfloat16 subnormals), Inf and NaN are
-// outliers; binary16 subnormals are normal floats and are quantized.
-template <typename T>
-__device__ __forceinline__ bool rel_quant16(T h, const Consts<float>& c, int32_t& bin) {
-    using F = Ty<T>;
-    const uint32_t u = __float_as_uint(F::widen(h));
-    const uint32_t E = (u >> 23) & 0xFFu;
-    if (E == 0u || E == 0xFFu) return false;
-    const float a = __uint_as_float(u & 0x7FFFFFFFu);
-    const float q = __fmul_rn(log2approx<float>(u), c.inv);
-    if (!(fabsf(q) < (float)kMaxBinRel)) return false;
-    int32_t b;
-    float bf;
-    Cv<float>::round(q, b, bf);
-    if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
-    const float bb = __fadd_rn(__fmul_rn(bf, c.scale), 127.0f);
-    if (!(bb >= 1.0f && bb < 255.0f)) return false;
-    const float m = F::widen(F::narrow(__uint_as_float(pow2approx_bits<float>(bb))));
-    if (!rel_accept<float>(a, m, c)) return false;
-    bin = (int32_t)(((uint32_t)b << 1) | (u >> 31));
-    return true;
-}
-
 // One value: the float32 recipes above, the float64 ones with few FP64 ops,
 // or the 16-bit ones.
 template <typename T, int MODE>
 __device__ __forceinline__ bool quant1(T x, const Consts<CT<T>>& c, int32_t& bin) {
     if constexpr (is16<T>()) {
         static_assert(MODE == LCQ_ABS || MODE == LCQ_REL, "16-bit formats: ABS/NOA and REL only");
-        if constexpr (MODE == LCQ_REL) return rel_quant16<T>(x, c, bin);
-        else return abs_quant16<T>(x, c, bin);
+        if constexpr (MODE == LCQ_REL) return rel_quant16<T>(Ty<T>::widen(x), c, bin);
+        else return abs_quant16<T>(Ty<T>::widen(x), c, bin);
     } else if constexpr (MODE == kModeRelLib) {
         return rel_quant_lib<T>(x, c, bin);
     } else if constexpr (sizeof(T) == 8) {
@@ -865,7 +932,12 @@ __device__ __forceinline__ bool quant1(T x, const Consts<CT<T>>& c, int32_t& bin
 
 template <typename T, int MODE>
 __device__ __forceinline__ uint32_t quant4(const T x[4], const Consts<CT<T>>& c, int32_t b[4]) {
-    if constexpr (sizeof(T) == 4 && MODE == LCQ_REL) {
+    if constexpr (is16<T>()) {
+        float xf[4];
+        Ty<T>::widen4(x, xf);
+        if constexpr (MODE == LCQ_REL) return rel_quant4_f32<Round16<T>>(xf, c, b);
+        else return abs_quant4_f32<true, Round16<T>>(xf, c, b);
+    } else if constexpr (sizeof(T) == 4 && MODE == LCQ_REL) {
         return rel_quant4_f32(x, c, b);
     } else if constexpr (sizeof(T) == 4 && MODE != kModeRelLib) {
         return abs_quant4_f32<MODE != kModeAbsNoCheck>(x, c, b);
