@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstring>
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lcq.h"
@@ -48,6 +49,7 @@ struct Point {
     int level;  // 0 anchor, 1..3
     int s;      // stride
     int cls;    // 1..7
+    int sh;     // log2(2 s): coarse positions are the multiples of 1 << sh
 };
 
 __device__ __forceinline__ Point classify(int i, int j, int k) {
@@ -60,6 +62,7 @@ __device__ __forceinline__ Point classify(int i, int j, int k) {
     p.s = m & (-m);
     p.level = p.s == 4 ? 1 : (p.s == 2 ? 2 : 3);
     p.cls = ((i & p.s) ? 1 : 0) | ((j & p.s) ? 2 : 0) | ((k & p.s) ? 4 : 0);
+    p.sh = __ffs(p.s);  // log2(s) + 1
     return p;
 }
 
@@ -77,7 +80,7 @@ __device__ __forceinline__ int axis_off(int c, int x, int stride) { return (c - 
 
 // Interpolation base of point (i, j, k) (not an anchor); p = &b[i][j][k].
 __device__ __forceinline__ int32_t interp(const int32_t* p, int N, int i, int j, int k, const Point& pt) {
-    const int s = pt.s, last = ((N - 1) / (2 * s)) * (2 * s), NN = N * N;
+    const int s = pt.s, last = ((N - 1) >> pt.sh) << pt.sh, NN = N * N;  // 2 s = 1 << sh
     const int i0 = (pt.cls & 1) ? axis_off(clampc(i - s, last), i, NN) : 0;
     const int i1 = (pt.cls & 1) ? axis_off(clampc(i + s, last), i, NN) : 0;
     const int j0 = (pt.cls & 2) ? axis_off(clampc(j - s, last), j, N) : 0;
@@ -99,8 +102,8 @@ __device__ __forceinline__ int32_t interp(const int32_t* p, int N, int i, int j,
 // p = &b[i][j][k].
 __device__ __forceinline__ void stencil(const int32_t* p, int N, int i, int j, int k, const Point& pt,
                                         int32_t base, int s_in, int32_t xw[7]) {
-    const int s2 = 2 * pt.s, last = ((N - 1) / s2) * s2, NN = N * N;
-    const int fi = (i / s2) * s2, fj = (j / s2) * s2, fk = (k / s2) * s2;
+    const int s2 = 2 * pt.s, last = ((N - 1) >> pt.sh) << pt.sh, NN = N * N;  // s2 = 1 << sh
+    const int fi = (i >> pt.sh) << pt.sh, fj = (j >> pt.sh) << pt.sh, fk = (k >> pt.sh) << pt.sh;
     int oi[3], oj[3], ok[3];
 #pragma unroll
     for (int d = 0; d < 3; d++) {
@@ -177,16 +180,180 @@ __device__ __forceinline__ int32_t predict_point(const int32_t* b, int N, int i,
     return base;
 }
 
-// ---------------------------------------------------------------- kernels --
+// ------------------------------------------------ network on tensor cores --
+//
+// A warp evaluates the network for 32 points of one (level, class) at once:
+// hidden = W1 x as a [32 points x 32 inputs] x [32 inputs x 16 hidden]
+// product on the tensor cores (mma.sync m16n8k16, bf16 operands, float32
+// accumulators), the rest in integers.  This is exact: the inputs and
+// weights are integers in [-128, 127], exact in bf16; every product is an
+// integer of magnitude <= 2^14 and every partial sum of the 27 products an
+// integer below 2^24, exact in float32 whatever the order of the additions.
+// So each accumulator equals the dp4a dot product of the definition.
 
-template <bool NET>
-__global__ void __launch_bounds__(256) k_residuals(const int32_t* __restrict__ bins, int N,
-                                                   const lcq_pred_params* params, int32_t* __restrict__ res) {
-    __shared__ SmemParams sp;
-    if (NET) {
-        load_params(sp, params);
-        __syncthreads();
+struct MmaParams {
+    uint32_t bfrag[kNets][32][8];  // W1 as B fragments: [net][lane][n-tile * 4 + k-step * 2 + reg]
+    int32_t b1[kNets][kNhid];
+    int32_t w2[kNets][kNhid];
+    int32_t b2[kNets];
+    int32_t s_in[3];
+    int32_t s1, s2;
+};
+
+constexpr int kArow = 20;  // words per point row of the A staging tile (16 used; 80 B rows: no bank conflicts)
+
+__device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
+    // exact floats of small integers by the 1.5 * 2^23 magic, then one packed conversion (exact)
+    const float a = __fsub_rn(__int_as_float(0x4B400000 + lo), 12582912.0f);
+    const float b = __fsub_rn(__int_as_float(0x4B400000 + hi), 12582912.0f);
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void load_mma_params(MmaParams& mp, const lcq_pred_params* gp) {
+    for (int x = threadIdx.x; x < kNets * 32 * 8; x += blockDim.x) {
+        const int net = x >> 8, lane = (x >> 3) & 31, slot = x & 7;
+        const int nt = slot >> 2, ks = (slot >> 1) & 1, reg = slot & 1;
+        const int n = 8 * nt + (lane >> 2);                      // hidden unit
+        const int k = 16 * ks + 2 * (lane & 3) + 8 * reg;        // first of two inputs
+        const int8_t* row = &gp->w1[net / 7][net % 7][n][0];
+        const int w0 = k < kNin ? row[k] : 0, w1 = k + 1 < kNin ? row[k + 1] : 0;
+        mp.bfrag[net][lane][slot] = bf16_pair(w0, w1);
     }
+    for (int x = threadIdx.x; x < kNets * kNhid; x += blockDim.x) {
+        (&mp.b1[0][0])[x] = (&gp->b1[0][0][0])[x];
+        (&mp.w2[0][0])[x] = (&gp->w2[0][0][0])[x];
+    }
+    for (int x = threadIdx.x; x < kNets; x += blockDim.x) mp.b2[x] = (&gp->b2[0][0])[x];
+    if (threadIdx.x < 3) mp.s_in[threadIdx.x] = gp->s_in[threadIdx.x];
+    if (threadIdx.x == 0) { mp.s1 = gp->s1; mp.s2 = gp->s2; }
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t a[4], uint32_t saddr) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3])
+                 : "r"(saddr));
+}
+
+// The network output o of the point of this lane (all 32 lanes take part;
+// the stencil inputs of the lane's point are already in its row of the
+// warp's staging tile `arow`, 32 rows of kArow words).
+__device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, const uint32_t* arow) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();
+    uint32_t a[2][2][4];  // [m-tile][k-step]
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(arow);
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+            const int mtx = lane >> 3, r = lane & 7;
+            const int point = 16 * mt + r + 8 * (mtx & 1);
+            const int col = 16 * ks + 8 * (mtx >> 1);  // bf16 column
+            ldmatrix_x4(a[mt][ks], base + (uint32_t)(point * kArow * 4 + col * 2));
+        }
+    float c[2][2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int nt = 0; nt < 2; nt++) {
+#pragma unroll
+            for (int v = 0; v < 4; v++) c[mt][nt][v] = 0.0f;
+#pragma unroll
+            for (int ks = 0; ks < 2; ks++)
+                mma_bf16(c[mt][nt], a[mt][ks], mp.bfrag[net][lane][nt * 4 + ks * 2],
+                         mp.bfrag[net][lane][nt * 4 + ks * 2 + 1]);
+        }
+    // hidden units 8 nt + 2 q + {0, 1} of points 16 mt + 8 hf + g (g = lane / 4, q = lane % 4)
+    const int q = lane & 3, g = lane >> 2;
+    const int s1 = mp.s1, r1 = 1 << (s1 - 1);
+    int32_t o[2][2];
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++)
+#pragma unroll
+        for (int hf = 0; hf < 2; hf++) {
+            int32_t acc = 0;
+#pragma unroll
+            for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+                for (int e = 0; e < 2; e++) {
+                    const int u = 8 * nt + 2 * q + e;
+                    const int32_t z = __float2int_rn(c[mt][nt][2 * hf + e]) + mp.b1[net][u];
+                    int32_t h = (z + r1) >> s1;
+                    h = h < 0 ? 0 : (h > 127 ? 127 : h);
+                    acc += mp.w2[net][u] * h;
+                }
+            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+            o[mt][hf] = acc;
+        }
+    (void)g;
+    // the point of this lane: m-tile lane / 16, half (lane % 16) / 8, row lane % 8 (held by quad lane % 8)
+    const int src = 4 * (lane & 7);
+    const int32_t v00 = __shfl_sync(0xFFFFFFFFu, o[0][0], src), v01 = __shfl_sync(0xFFFFFFFFu, o[0][1], src);
+    const int32_t v10 = __shfl_sync(0xFFFFFFFFu, o[1][0], src), v11 = __shfl_sync(0xFFFFFFFFu, o[1][1], src);
+    const int32_t mine = (lane < 16) ? ((lane & 8) ? v01 : v00) : ((lane & 8) ? v11 : v10);
+    return (mine + mp.b2[net] + (1 << (mp.s2 - 1))) >> mp.s2;
+}
+
+// The 27 stencil inputs of the point (as in `stencil`) written to the lane's
+// row of the staging tile as bf16 pairs; inputs 27..31 are 0.
+__device__ __forceinline__ void stencil_row(const int32_t* p, int N, int i, int j, int k, const Point& pt,
+                                            int32_t base, int s_in, uint32_t* row) {
+    const int s2 = 2 * pt.s, last = ((N - 1) >> pt.sh) << pt.sh, NN = N * N;
+    const int fi = (i >> pt.sh) << pt.sh, fj = (j >> pt.sh) << pt.sh, fk = (k >> pt.sh) << pt.sh;
+    int oi[3], oj[3], ok[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        oi[d] = axis_off(clampc(fi + s2 * (d - 1), last), i, NN);
+        oj[d] = axis_off(clampc(fj + s2 * (d - 1), last), j, N);
+        ok[d] = clampc(fk + s2 * (d - 1), last) - k;
+    }
+    int dv[32];
+#pragma unroll
+    for (int t = 0; t < 32; t++) {
+        if (t < kNin) {
+            const int32_t c = p[oi[t / 9] + oj[(t / 3) % 3] + ok[t % 3]];
+            int32_t d = (c - base) >> s_in;
+            dv[t] = d < -128 ? -128 : (d > 127 ? 127 : d);
+        } else {
+            dv[t] = 0;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 16; w += 4)
+        *reinterpret_cast<uint4*>(row + w) = make_uint4(bf16_pair(dv[2 * w], dv[2 * w + 1]),
+                                                        bf16_pair(dv[2 * w + 2], dv[2 * w + 3]),
+                                                        bf16_pair(dv[2 * w + 4], dv[2 * w + 5]),
+                                                        bf16_pair(dv[2 * w + 6], dv[2 * w + 7]));
+}
+
+// ---------------------------------------------------------------- kernels --
+//
+// Interpolation only: one CTA per grid row (i, j) (or lattice row of one
+// level when reconstructing), the threads along k, so that every load and
+// store of a warp is one coalesced row segment.
+//
+// With the network, residuals and reconstruction walk the grid by point
+// groups instead: the anchors, then for each level (stride s = 4, 2, 1) and
+// class the sub-lattice of its points (on an odd axis of the class the
+// coordinates s, 3s, 5s, ..., on an even axis 0, 2s, 4s, ...; together they
+// partition the grid).  A warp takes 32 consecutive points of one lattice
+// row, so its lanes share the class and the network: the weights are read
+// from shared memory as broadcasts.  A persistent grid of a few CTAs per SM
+// loads the network parameters once per CTA.  (For interpolation alone this
+// order is slower: the strided rows of the sub-lattices waste half of every
+// line they touch.)
+
+__global__ void __launch_bounds__(256) k_interp_residuals(const int32_t* __restrict__ bins, int N,
+                                                          int32_t* __restrict__ res) {
     const int i = blockIdx.z, j = blockIdx.y;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
         const size_t e = ((size_t)i * N + j) * N + k;
@@ -194,22 +361,15 @@ __global__ void __launch_bounds__(256) k_residuals(const int32_t* __restrict__ b
         if (pt.level == 0) {
             res[e] = bins[e];
         } else {
-            const int32_t pr = predict_point(bins, N, i, j, k, pt, NET ? &sp : nullptr);
+            const int32_t pr = predict_point(bins, N, i, j, k, pt, nullptr);
             res[e] = (int32_t)((uint32_t)bins[e] - (uint32_t)pr);
         }
     }
 }
 
-// Reconstruct the points of one level (anchors when s == 8) on the lattice of
-// multiples of s.
-template <bool NET>
-__global__ void __launch_bounds__(256) k_reconstruct(const int32_t* __restrict__ res, int N, int s,
-                                                     const lcq_pred_params* params, int32_t* bins) {
-    __shared__ SmemParams sp;
-    if (NET) {
-        load_params(sp, params);
-        __syncthreads();
-    }
+// The points of one level (anchors when s == 8) on the lattice of multiples of s.
+__global__ void __launch_bounds__(256) k_interp_reconstruct(const int32_t* __restrict__ res, int N, int s,
+                                                            int32_t* bins) {
     const int i = blockIdx.z * s, j = blockIdx.y * s;
     for (int kk = blockIdx.x * blockDim.x + threadIdx.x; kk * s < N; kk += gridDim.x * blockDim.x) {
         const int k = kk * s;
@@ -219,8 +379,92 @@ __global__ void __launch_bounds__(256) k_reconstruct(const int32_t* __restrict__
         if (pt.level == 0) {
             bins[e] = res[e];
         } else {
-            const int32_t pr = predict_point(bins, N, i, j, k, pt, NET ? &sp : nullptr);
+            const int32_t pr = predict_point(bins, N, i, j, k, pt, nullptr);
             bins[e] = (int32_t)((uint32_t)pr + (uint32_t)res[e]);
+        }
+    }
+}
+
+constexpr int kMaxGroups = 22;  // anchors + 3 levels x 7 classes
+
+struct Group {
+    int s, cls, level, step;  // anchors: s = 8, cls = level = 0, step 8; else step 2s
+    int o[3];                 // first coordinate on each axis (s or 0)
+    int n[3];                 // positions on each axis
+    int kchunks;              // ceil(n[2] / 32)
+    uint32_t first_job;       // jobs (lattice rows) of the groups before this one
+};
+
+struct GroupTable {
+    Group g[kMaxGroups];
+    int count;
+    uint32_t total_jobs;
+};
+
+// The groups of `level` (0: anchors only, 1..3: that level's classes, -1:
+// everything), jobs counted from 0.
+static GroupTable group_table(int N, int level) {
+    GroupTable t{};
+    uint32_t jobs = 0;
+    auto add = [&](int s, int cls, int lv, int step) {
+        Group& G = t.g[t.count++];
+        G.s = s; G.cls = cls; G.level = lv; G.step = step;
+        for (int a = 0; a < 3; a++) {
+            G.o[a] = ((cls >> a) & 1) ? s : 0;
+            G.n[a] = G.o[a] < N ? (N - 1 - G.o[a]) / step + 1 : 0;
+        }
+        G.kchunks = (G.n[2] + 31) / 32;
+        G.first_job = jobs;
+        jobs += G.n[2] > 0 ? (uint32_t)G.n[0] * (uint32_t)G.n[1] : 0u;
+    };
+    if (level <= 0) add(8, 0, 0, 8);
+    for (int lv = 1; lv <= 3; lv++)
+        if (level < 0 || level == lv)
+            for (int c = 1; c <= 7; c++) add(8 >> lv, c, lv, 16 >> lv);
+    t.total_jobs = jobs;
+    return t;
+}
+
+// RECON = false: res = bins - prediction (anchors: res = bins).
+// RECON = true: bins = prediction + res for the groups of one level, whose
+// predictions read only coarser levels, already reconstructed.
+template <bool RECON>
+__global__ void __launch_bounds__(256) k_net_groups(const int32_t* __restrict__ in, int N,
+                                                    const lcq_pred_params* params, int32_t* out,
+                                                    const GroupTable gt) {
+    __shared__ MmaParams mp;
+    __shared__ __align__(16) uint32_t s_a[8][32 * kArow];  // per-warp staging tiles
+    load_mma_params(mp, params);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* arow = &s_a[warp][0];
+    const uint32_t wstride = gridDim.x * (blockDim.x / 32);
+    int g = 0;  // jobs only grow, so the group search resumes where it stopped
+    for (uint32_t job = blockIdx.x * (blockDim.x / 32) + (uint32_t)warp; job < gt.total_jobs; job += wstride) {
+        while (g + 1 < gt.count && job >= gt.g[g + 1].first_job) g++;  // the same in every lane
+        const Group& G = gt.g[g];
+        const uint32_t r = job - G.first_job;  // one lattice row (ii, jj)
+        const int jj = (int)(r % (uint32_t)G.n[1]), ii = (int)(r / (uint32_t)G.n[1]);
+        for (int kc = 0; kc < G.kchunks; kc++) {
+        const int kk = kc * 32 + lane;
+        const bool valid = kk < G.n[2];
+        const int i = G.o[0] + ii * G.step, j = G.o[1] + jj * G.step, k = G.o[2] + (valid ? kk : 0) * G.step;
+        const size_t e = ((size_t)i * N + j) * N + k;
+        if (G.level == 0) {  // anchors (uniform in the warp)
+            if (valid) out[e] = in[e];
+            continue;
+        }
+
+        Point pt;
+        pt.level = G.level; pt.s = G.s; pt.cls = G.cls; pt.sh = __ffs(G.s);
+        const int32_t* bins = RECON ? out : in;
+        const int32_t* pp = bins + e;
+        const int32_t base = interp(pp, N, i, j, k, pt);  // k is a valid point of the group in every lane
+        stencil_row(pp, N, i, j, k, pt, base, mp.s_in[pt.level - 1], arow + lane * kArow);
+        const int net = (pt.level - 1) * 7 + (pt.cls - 1);
+        const int32_t pr = (int32_t)((uint32_t)base + (uint32_t)network_mma(mp, net, arow));
+        __syncwarp();  // the staging tile is rewritten by the next chunk
+        if (valid) out[e] = RECON ? (int32_t)((uint32_t)pr + (uint32_t)in[e]) : (int32_t)((uint32_t)in[e] - (uint32_t)pr);
         }
     }
 }
@@ -411,6 +655,20 @@ __global__ void k_freeze(const float* shadow, lcq_pred_params* out) {
 
 static bool n_ok(int N) { return N >= 1 && N <= 2048; }
 
+// Persistent grid for `jobs` warp jobs (lattice rows): the CTAs (8 warps)
+// that fit on the device at once, at most one per 8 jobs.
+template <typename K>
+static unsigned jobs_grid(K kernel, uint32_t jobs) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
+    uint64_t g = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)(sms > 0 ? sms : 148);
+    const uint64_t need = ((uint64_t)jobs + 7) / 8;
+    if (g > need) g = need;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
 }  // namespace pred
 }  // namespace lcq
 
@@ -421,20 +679,31 @@ extern "C" {
 lcq_status lcq_pred_residuals(const int32_t* d_bins, uint32_t N, const lcq_pred_params* d_params, int32_t* d_res,
                               cudaStream_t stream) {
     if (!n_ok((int)N) || !d_bins || !d_res) return LCQ_ERR_ARG;
-    const dim3 grid((N + 255) / 256, N, N);
-    if (d_params) k_residuals<true><<<grid, 256, 0, stream>>>(d_bins, (int)N, d_params, d_res);
-    else k_residuals<false><<<grid, 256, 0, stream>>>(d_bins, (int)N, nullptr, d_res);
+    if (d_params) {
+        const GroupTable gt = group_table((int)N, -1);
+        k_net_groups<false><<<jobs_grid(k_net_groups<false>, gt.total_jobs), 256, 0, stream>>>(d_bins, (int)N,
+                                                                                            d_params, d_res, gt);
+    } else {
+        const dim3 grid((N + 255) / 256, N, N);
+        k_interp_residuals<<<grid, 256, 0, stream>>>(d_bins, (int)N, d_res);
+    }
     return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
 }
 
 lcq_status lcq_pred_reconstruct(const int32_t* d_res, uint32_t N, const lcq_pred_params* d_params, int32_t* d_bins,
                                 cudaStream_t stream) {
     if (!n_ok((int)N) || !d_bins || !d_res) return LCQ_ERR_ARG;
-    for (int s : {8, 4, 2, 1}) {
-        const unsigned m = (N + s - 1) / s;
-        const dim3 grid((m + 255) / 256, m, m);
-        if (d_params) k_reconstruct<true><<<grid, 256, 0, stream>>>(d_res, (int)N, s, d_params, d_bins);
-        else k_reconstruct<false><<<grid, 256, 0, stream>>>(d_res, (int)N, s, nullptr, d_bins);
+    for (int level = 0; level <= 3; level++) {
+        if (d_params) {
+            const GroupTable gt = group_table((int)N, level);
+            k_net_groups<true><<<jobs_grid(k_net_groups<true>, gt.total_jobs), 256, 0, stream>>>(d_res, (int)N,
+                                                                                              d_params, d_bins, gt);
+        } else {
+            const int s = 8 >> level;
+            const unsigned m = (N + s - 1) / s;
+            const dim3 grid((m + 255) / 256, m, m);
+            k_interp_reconstruct<<<grid, 256, 0, stream>>>(d_res, (int)N, s, d_bins);
+        }
         if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
