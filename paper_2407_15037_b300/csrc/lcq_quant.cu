@@ -77,17 +77,14 @@ struct QParams {
     const T* in;          // chunk start
     int32_t* bins;        // chunk start
     uint32_t* mask;       // chunk start (chunk offsets are multiples of 32)
-    typename Ty<T>::U* out;
-    uint64_t cap;
+    uint32_t* counts;     // outliers per scan tile of this chunk
     lcq_header* hdr;
     WsHead* ws;
-    uint64_t* desc;
     uint64_t n;           // values in this chunk
     uint32_t num_tiles;
     uint32_t first_chunk;
     uint32_t consts_from_hdr;  // NOA: constants written by k_minmax
     Consts<CT<T>> c;
-    ScanCfg scan;
     // header fields (written by the CTA that owns tile 0 of the first chunk)
     uint32_t dtype, bound;
     double eb, eb_abs;
@@ -126,10 +123,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
     __shared__ uint32_t s_mask[2][WORDS];
     __shared__ uint32_t s_wpre[2][WORDS];
     __shared__ uint32_t s_jt[2];
-    __shared__ uint64_t s_pbase[2];
     __shared__ uint32_t s_epoch, s_filled;
     __shared__ volatile uint32_t s_abort;
-    __shared__ uint64_t s_base;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t full_sub = p.n / STILE;
@@ -142,7 +137,6 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
         }
         mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
-        s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.hdr->outlier_count);
         s_abort = 0;
         s_filled = 0;
     }
@@ -168,19 +162,17 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                 }
             }
         };
-        // Returns true if the kernel must stop (uniform over the compute warps).
-        auto write_payload = [&](uint32_t jj) -> bool {  // all compute threads
+        // Wait until the scan warp has taken scan tile jj's mask words, so
+        // that its buffer may be reused.  Returns true if the kernel must
+        // stop (uniform over the compute warps).
+        auto release_tile = [&](uint32_t jj) -> bool {  // all compute threads
             const int bb = (int)(jj & 1u);
             bool ok = mbar_wait_or_abort(&s_done[bb], (jj >> 1) & 1u, kMbarLimit, &s_abort);
             if (!ok && !s_abort) {
                 atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
                 s_abort = 1;
             }
-            if (named_barrier_or(1, kComputeThreads, !ok)) return true;
-            write_outliers<T>(s_mask[bb], s_wpre[bb], WORDS, p.in + (uint64_t)s_jt[bb] * TILE, s_pbase[bb],
-                              p.out, p.cap);
-            named_barrier_sync(1, kComputeThreads);  // buffer bb may be reused
-            return false;
+            return named_barrier_or(1, kComputeThreads, !ok);
         };
 
         if (tid == 0) issue();
@@ -212,7 +204,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                     s_jt[b] = t;
                     mbar_arrive(&s_full[b]);  // hand the scan tile to the scan warp
                 }
-                if (j >= 1 && write_payload(j - 1)) {
+                if (j >= 1 && release_tile(j - 1)) {
                     stop = true;
                     break;
                 }
@@ -222,7 +214,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
         // the abort flag by itself
         if (!named_barrier_or(1, kComputeThreads, s_abort != 0)) {
             const uint32_t J = k / SUB;  // scan tiles handled by this CTA
-            if (!(J >= 1 && write_payload(J - 1)) && tid == 0) {
+            if (!(J >= 1 && release_tile(J - 1)) && tid == 0) {
                 s_jt[J & 1u] = kNoTile;
                 mbar_arrive(&s_full[J & 1u]);
             }
@@ -240,15 +232,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             if (t == kNoTile) break;
             const uint32_t agg = scan_mask_words<WPL>(s_mask[b], s_wpre[b], p.mask,
                                                       (uint64_t)t * WORDS + (uint64_t)lane * WPL, nwords, true);
-            if (lane == 0) lookback_publish(p.desc, t, agg, s_epoch, p.scan);
-            const uint32_t excl = lookback_walk(p.desc, t, agg, s_epoch, p.scan, &p.ws->err);
             if (lane == 0) {
-                s_pbase[b] = s_base + excl;
-                if (t == p.num_tiles - 1) {
-                    const uint64_t total = s_base + excl + agg;
-                    st_relaxed_u64(&p.hdr->outlier_count, total);
-                    if (total > p.cap) atomicOr(&p.ws->err, LCQ_STATUS_CAPACITY);
-                }
+                p.counts[t] = agg;
                 if (t == 0 && p.first_chunk) {
                     lcq_header* h = p.hdr;
                     h->magic = LCQ_MAGIC;
@@ -296,6 +281,178 @@ __global__ void k_header_empty(lcq_header* h, uint32_t dtype, uint32_t bound, do
     h->outlier_count = 0;
     h->status = 0;
     h->reserved = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Outlier compaction (after k_quantize): k_tile_offsets turns the per-tile
+// outlier counts of a chunk into payload offsets (exclusive scan, one CTA,
+// continuing the count of the earlier chunks from the header) and writes the
+// header's outlier count; k_compact walks the mask words of every tile that
+// has outliers and writes their raw bits to payload[offset + rank], in index
+// order.  Keeping this out of k_quantize leaves the streaming CTAs without
+// any dependence on one another (an in-kernel lookback made every CTA wait
+// for the slowest ones).
+// ---------------------------------------------------------------------------
+constexpr int kOffsetsThreads = 1024;
+constexpr int kOffsetsPerThread = 8;
+
+__global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t* counts, uint32_t tiles,
+                                                                  uint64_t* offsets, lcq_header* hdr,
+                                                                  uint32_t first_chunk, uint64_t cap) {
+    constexpr uint32_t kPass = kOffsetsThreads * kOffsetsPerThread;
+    __shared__ unsigned long long s_warp[kOffsetsThreads / 32];
+    __shared__ unsigned long long s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = first_chunk ? 0ull : hdr->outlier_count;  // outliers of the earlier chunks
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < tiles; t0 += kPass) {
+        // thread tid takes tiles t0 + tid * 8 .. + 7
+        const uint32_t tb = t0 + (uint32_t)tid * kOffsetsPerThread;
+        uint32_t v[kOffsetsPerThread];
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int u = 0; u < kOffsetsPerThread; u++) {
+            v[u] = tb + u < tiles ? counts[tb + u] : 0u;
+            sum += v[u];
+        }
+        unsigned long long x = sum;  // inclusive scan of the thread sums within the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_warp[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        unsigned long long run = s_carry + (warp ? s_warp[warp - 1] : 0ull) + x - sum;
+#pragma unroll
+        for (int u = 0; u < kOffsetsPerThread; u++) {
+            if (tb + u < tiles) offsets[tb + u] = run;
+            run += v[u];
+        }
+        __syncthreads();
+        if (tid == kOffsetsThreads - 1) s_carry = run;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        hdr->outlier_count = s_carry;
+        if (s_carry > cap) atomicOr(&hdr->status, LCQ_STATUS_CAPACITY);
+    }
+}
+
+// One warp per scan tile of WORDS mask words: tiles without outliers cost
+// one load.  The warp takes the tile in parts of 512 words: lane l takes the
+// words [16 l, 16 l + 16) of a part, and the warp scan of their bit counts
+// gives each lane its first rank.  In a sparse tile each lane walks its own
+// words in index order and issues the loads of up to eight outliers (across
+// words) before their stores, so that the latencies overlap.  In a dense
+// tile (more than 1/8 outliers) the warp takes the words one by one with one
+// lane per bit, so that its loads and stores are coalesced.
+constexpr int kCompactThreads = 256;
+
+template <typename T, int WORDS>
+__global__ void __launch_bounds__(kCompactThreads) k_compact(const T* in, const uint32_t* mask, uint64_t n,
+                                                             const uint32_t* counts, const uint64_t* offsets,
+                                                             uint32_t tiles, typename Ty<T>::U* out, uint64_t cap) {
+    using U = typename Ty<T>::U;
+    constexpr int TILE = WORDS * 32, PART = 512, WPL = PART / 32;  // 16 words per lane and part
+    static_assert(WORDS % PART == 0, "whole parts");
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const uint64_t nwords = (n + 31) / 32;
+    const uint32_t wstride = gridDim.x * (kCompactThreads / 32);
+    for (uint32_t t = blockIdx.x * (kCompactThreads / 32) + (threadIdx.x >> 5); t < tiles; t += wstride) {
+        const uint32_t tcount = counts[t];
+        if (tcount == 0u) continue;  // the same in every lane
+        uint64_t pbase = offsets[t];
+        if (pbase >= cap) continue;
+        const bool dense = tcount > (uint32_t)(TILE / 8);
+        for (int part = 0; part < WORDS / PART; part++) {
+            const uint64_t gw = (uint64_t)t * WORDS + (uint64_t)part * PART + (uint64_t)lane * WPL;
+            uint32_t wv[WPL];
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int j = 0; j < WPL; j += 4) {
+                if (gw + j + 4 <= nwords) {
+                    const uint4 a = *reinterpret_cast<const uint4*>(mask + gw + j);
+                    wv[j] = a.x; wv[j + 1] = a.y; wv[j + 2] = a.z; wv[j + 3] = a.w;
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; i++) wv[j + i] = gw + j + i < nwords ? mask[gw + j + i] : 0u;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; i++) cnt += __popc(wv[j + i]);
+            }
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const T* gp = in + (uint64_t)t * TILE + (uint64_t)part * PART * 32;  // first value of the part
+            if (dense) {
+                for (int L = 0; L < 32; L++) {
+                    uint32_t run = __shfl_sync(0xFFFFFFFFu, incl - cnt, L);
+#pragma unroll
+                    for (int j0 = 0; j0 < WPL; j0 += 4) {
+                        uint32_t w[4], r[4];
+                        U v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            w[u] = __shfl_sync(0xFFFFFFFFu, wv[j0 + u], L);
+                            r[u] = run + __popc(w[u] & below);
+                            run += __popc(w[u]);
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+                            if ((w[u] >> lane) & 1u) v[u] = Ty<T>::bits(gp[(uint32_t)(L * WPL + j0 + u) * 32u + lane]);
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+                            if (((w[u] >> lane) & 1u) && pbase + r[u] < cap) out[pbase + r[u]] = v[u];
+                    }
+                }
+            } else {
+                constexpr int Q = 8;
+                uint64_t rank = pbase + (incl - cnt);
+                const T* gin = gp + (uint64_t)lane * WPL * 32;
+                uint32_t qi[Q] = {0, 0, 0, 0, 0, 0, 0, 0};
+                int qn = 0;
+                auto flush = [&]() {
+                    U v[Q];
+#pragma unroll
+                    for (int u = 0; u < Q; u++)
+                        if (u < qn) v[u] = Ty<T>::bits(gin[qi[u]]);
+#pragma unroll
+                    for (int u = 0; u < Q; u++)
+                        if (u < qn && rank + u < cap) out[rank + u] = v[u];
+                    rank += (uint64_t)qn;
+                    qn = 0;
+                };
+#pragma unroll
+                for (int jw = 0; jw < WPL; jw++) {
+                    uint32_t m = wv[jw];
+                    while (m) {
+                        const uint32_t idx = (uint32_t)jw * 32u + (uint32_t)(__ffs(m) - 1);
+                        m &= m - 1u;
+#pragma unroll
+                        for (int u = 0; u < Q; u++) qi[u] = qn == u ? idx : qi[u];
+                        if (++qn == Q) flush();
+                    }
+                }
+                flush();
+            }
+            pbase += __shfl_sync(0xFFFFFFFFu, incl, 31);  // outliers of this part
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -691,10 +848,22 @@ static size_t desc_bytes(uint64_t n) {
     return (size_t)(tiles_for(per_chunk) * sizeof(uint64_t));
 }
 
+// Tile table of a quantize chunk: outlier counts (uint32) and payload
+// offsets (uint64) per scan tile; every tile shape has at least
+// kTileValuesMin values per scan tile.
+constexpr uint64_t kTileValuesMin = 16384;
+
+static uint64_t table_tiles(uint64_t n) {
+    const uint64_t per_chunk = n < kChunk ? n : kChunk;
+    return (per_chunk + kTileValuesMin - 1) / kTileValuesMin;
+}
+
+static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 static size_t ws_size(uint64_t n) {
-    size_t d = desc_bytes(n);
-    d = (d + 255) & ~(size_t)255;
-    return kWsHeadBytes + d + kMinmaxPartialBytes;
+    const size_t d = up256(desc_bytes(n));
+    const uint64_t tt = table_tiles(n);
+    return kWsHeadBytes + d + kMinmaxPartialBytes + up256(tt * 4) + up256(tt * 8);
 }
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
@@ -815,6 +984,27 @@ template <typename T, int MODE>
 static cudaError_t launch_ablation(const QParams<T>& p, cudaStream_t st) {
     constexpr Variant v = kVariants[ablation_variant<T, MODE>()];
     return launch_quantize<T, MODE, v.vpt, v.stages, v.sub, v.minb>(p, st);
+}
+
+// The compaction kernel for scan tiles of `words` mask words (every tile
+// shape has 512 or 1024).
+template <typename T>
+static cudaError_t launch_compact(int words, const T* in, const uint32_t* mask, uint64_t n, const uint32_t* counts,
+                                  const uint64_t* offsets, uint32_t tiles, typename Ty<T>::U* out, uint64_t cap,
+                                  cudaStream_t st) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const uint32_t warps = kCompactThreads / 32;
+    uint32_t grid = (uint32_t)device_sms(dev) * 8u;
+    if (grid > (tiles + warps - 1) / warps) grid = (tiles + warps - 1) / warps;
+    if (grid < 1) grid = 1;
+    if (words == 1024)
+        k_compact<T, 1024><<<grid, kCompactThreads, 0, st>>>(in, mask, n, counts, offsets, tiles, out, cap);
+    else if (words == 512)
+        k_compact<T, 512><<<grid, kCompactThreads, 0, st>>>(in, mask, n, counts, offsets, tiles, out, cap);
+    else
+        return cudaErrorInvalidValue;
+    return cudaPeekAtLastError();
 }
 
 // Selected variant per kernel kind (0 quantize, 1 dequantize), dtype (float32,
@@ -981,9 +1171,11 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     }
     const uint32_t dtype = Ty<T>::kDtype;
     WsHead* head = reinterpret_cast<WsHead*>(ws);
-    uint64_t* desc = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
-    size_t dsz = (desc_bytes(n) + 255) & ~(size_t)255;
+    const size_t dsz = up256(desc_bytes(n));
     uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz);
+    char* table = reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz + kMinmaxPartialBytes;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(table);
+    uint64_t* offsets = reinterpret_cast<uint64_t*>(table + up256(table_tiles(n) * 4));
 
     if (io) {
         // NOA needs the whole input for its range before any binning
@@ -1023,27 +1215,29 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.in = in + off;
         p.bins = bins + off;
         p.mask = mask + off / 32;
-        p.out = reinterpret_cast<typename Ty<T>::U*>(outl);
-        p.cap = cap;
+        p.counts = counts;
         p.hdr = hdr;
         p.ws = head;
-        p.desc = desc;
         p.n = len;
         p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
         p.consts_from_hdr = noa;
         p.c = c;
-        p.scan = g_scan;
         p.dtype = dtype;
         p.bound = bt;
         p.eb = eb;
         p.eb_abs = eb_abs;
         p.n_total = n;
-        const int var = g_variant[0][dtype][bt];
+        int var = g_variant[0][dtype][bt];
         cudaError_t e = cudaErrorInvalidValue;
         if constexpr (!is16<T>()) {
-            if (ablation == kModeAbsNoCheck) e = launch_ablation<T, kModeAbsNoCheck>(p, st);
-            else if (ablation == kModeRelLib) e = launch_ablation<T, kModeRelLib>(p, st);
+            if (ablation == kModeAbsNoCheck) {
+                var = ablation_variant<T, kModeAbsNoCheck>();
+                e = launch_ablation<T, kModeAbsNoCheck>(p, st);
+            } else if (ablation == kModeRelLib) {
+                var = ablation_variant<T, kModeRelLib>();
+                e = launch_ablation<T, kModeRelLib>(p, st);
+            }
         }
         if (ablation == 0) {
             if (bt == LCQ_REL) e = launch_quantize_variant<T, LCQ_REL>(var, p, st);
@@ -1051,6 +1245,14 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         }
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
         if (io && !host_io_download(*io, off / chunk, off, len, st)) return LCQ_ERR_CUDA;
+        // outlier offsets and payload of this chunk
+        const uint64_t tile = (uint64_t)kComputeThreads * 4 * kVariants[var].vpt * kVariants[var].sub;
+        const uint32_t tiles = (uint32_t)tiles_of(len, (int)tile);
+        k_tile_offsets<<<1, kOffsetsThreads, 0, st>>>(counts, tiles, offsets, hdr, off == 0 ? 1u : 0u, cap);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+        if (launch_compact<T>((int)(tile / 32), p.in, p.mask, len, counts, offsets, tiles,
+                              reinterpret_cast<typename Ty<T>::U*>(outl), cap, st) != cudaSuccess)
+            return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
 }
@@ -1326,8 +1528,6 @@ struct StageSlot {
     void* d_out;
     lcq_header* d_hdr;
 };
-
-size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 StageSlot stage_slot(void* base, size_t es, uint64_t n, uint64_t cap) {
     StageSlot t;

@@ -132,20 +132,30 @@ def test_workspace_reuse_across_calls():
 
 
 def test_scan_timeout_is_reported_without_hang():
-    """A tile that never publishes its scan descriptor: the successor's wait
-    gives up after the spin limit and the header carries LCQ_STATUS_TIMEOUT."""
+    """The decoder's bounded lookback: a tile that never publishes its scan
+    descriptor makes the successor's wait give up after the spin limit, and
+    the status carries LCQ_STATUS_TIMEOUT; the workspace is usable again once
+    zeroed."""
     x = torch.randn(1 << 19, device=DEV)  # several scan tiles of every tile shape
+    x[::1000] = float("nan")               # outliers in every tile
     ws = P.new_workspace(x.numel(), x.device)
-    q = P.alloc_outputs(x.numel(), x.dtype, x.device)
+    q = P.quantize(x, "abs", 1e-3)
+    out = torch.empty_like(x)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
     P.debug_set_scan(spin_limit=200, drop_tile=1)
-    P.quantize_into(x, "abs", 1e-3, q, ws)
-    code, _ = P.sync_status(q)
-    assert code == 4  # LCQ_ERR_TIMEOUT
-    P.debug_set_scan(0)
+    try:
+        P.dequantize_into(q, out, ws, status)
+        torch.cuda.synchronize()
+    finally:
+        P.debug_set_scan(0)
+    assert int(status.item()) & P.lcq.STATUS_TIMEOUT
     ws.zero_()
-    P.quantize_into(x, "abs", 1e-3, q, ws)
-    assert P.sync_status(q)[0] == 0
-    compare(x, "abs", 1e-3, q=q)
+    status.zero_()
+    P.dequantize_into(q, out, ws, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    oq = O.quantize(x.cpu().numpy(), "abs", 1e-3)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), O.dequantize(oq).view(np.uint32))
 
 
 def test_dequantize_rejects_mismatched_header():
