@@ -32,7 +32,6 @@ constexpr int kWords = kScanTile / 32;  // mask words per scan tile
 constexpr int kWpl = kWords / 32;       // per scan-warp lane
 constexpr int kRangeChunk = 16384;      // values per range-reduction chunk
 constexpr int kRangeBlock = 256;
-constexpr uint32_t kSpin = 1u << 20;
 constexpr uint32_t kMbarLimit = 1u << 22;
 
 // One array of the plan (device memory, read-only for the kernels).
@@ -598,7 +597,7 @@ lcq_status lcq_quantize_batched(const lcq_batch_info* h_info, const void* d_plan
     bp.total_tiles = h_info->total_tiles;
     bp.ws = ws;
     bp.desc = reinterpret_cast<uint64_t*>((char*)d_ws + kWsHeadBytes);
-    bp.scan = ScanCfg{kSpin, ~0ull};
+    bp.scan = current_scan_config();
     return launch_batch_variant(g_bvariant, bp, stream) == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
 }
 

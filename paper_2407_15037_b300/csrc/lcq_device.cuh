@@ -1024,6 +1024,9 @@ struct ScanCfg {
     uint64_t drop_tile;   // test hook: this tile never publishes
 };
 
+// Host: the current setting of the test hook lcq_debug_set_scan.
+ScanCfg current_scan_config();
+
 // Publish a tile's aggregate (or, for tile 0, its inclusive prefix).  Lane 0.
 __device__ __forceinline__ void lookback_publish(uint64_t* desc, uint32_t tile, uint32_t agg,
                                                  uint32_t epoch, const ScanCfg& cfg) {

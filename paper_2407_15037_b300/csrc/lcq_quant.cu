@@ -11,13 +11,17 @@
 //       (cp.async.bulk + mbarrier) in a ring; scan tiles (several stages) are
 //       handed out by an atomic ticket.  Compute warps quantize, verify and
 //       store bins per value (Sec. 2.2, 3.1-3.3) and build the outlier mask
-//       words; the scan warp scans each finished tile's mask, publishes its
-//       count and runs a bounded decoupled lookback for the tile's payload
-//       offset; the compute warps then write that tile's outliers (raw bits,
-//       ascending index order) while the next tile streams in.
-// k_dequantize mirrors it: bins and mask words arrive by bulk copies, the same
-// lookback gives each tile's payload offset, and values are reconstructed with
-// the encoder's exact operations (Sec. 3.1; no double-check on decode, Sec. 6).
+//       words; the scan warp stores each finished tile's mask words and its
+//       outlier count.  No CTA waits for another.
+//   k_tile_offsets: the payload offset of every scan tile (exclusive scan of
+//       the counts, one CTA) and the header's outlier count.
+//   k_compact: the outliers' raw bits to payload[offset + rank], ascending
+//       index order (Sec. 3.1), one warp per tile that has outliers.
+// Decoding: k_tile_counts (outliers per tile from the mask) and
+// k_tile_offsets give each tile's payload offset; k_dequantize streams bins
+// and mask words by bulk copies and reconstructs the values with the
+// encoder's exact operations (Sec. 3.1; no double-check on decode, Sec. 6),
+// patching the outliers from the payload.
 //
 // Arrays longer than kChunk values are processed as several launches; the
 // running outlier count carries from one chunk to the next in device memory,
@@ -39,9 +43,8 @@
 namespace lcq {
 
 constexpr int kBlock = 256;
-constexpr int kTileMin = 4096;                  // smallest tile; sizes the scan workspace
 constexpr uint64_t kChunk = 1ull << 31;         // values per launch at most
-constexpr uint32_t kDefaultSpin = 1u << 20;     // lookback polls (~1 s with backoff)
+constexpr uint32_t kDefaultSpin = 1u << 20;     // batched lookback polls (~1 s with backoff)
 constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (seconds)
 
 // Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
@@ -66,11 +69,13 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 static ScanCfg g_scan = {kDefaultSpin, ~0ull};
 
+// The setting of the test hook lcq_debug_set_scan (read by the batched launch).
+ScanCfg current_scan_config() { return g_scan; }
+
 // ---------------------------------------------------------------------------
 // Quantize kernel: persistent CTAs; input tiles stream into a ring of
 // shared-memory stages by bulk asynchronous copies, so that the next tiles
-// are in flight while the current tile is quantized and its outliers are
-// placed by the lookback scan.
+// are in flight while the current tile is quantized.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct QParams {
@@ -93,16 +98,12 @@ struct QParams {
 
 // Warp-specialised streaming kernels.  A CTA has 8 compute warps and one
 // scan warp.  The compute warps stream the CTA's tiles through a ring of
-// shared-memory stages (bulk asynchronous copies, one sub-tile per stage) and
-// never wait on the cross-CTA scan: when a scan tile (SUB sub-tiles) is done
-// they hand its mask words to the scan warp and go on.  The scan warp scans
-// the words, publishes the tile's count, walks back over the predecessors
-// (bounded decoupled lookback) and posts the tile's payload offset; the
-// compute warps write that tile's outliers one scan tile later.
-//
-// Tickets are taken one scan tile at a time as the ring fills, so the global
-// ticket order follows the order in which CTAs reach their tiles, and every
-// CTA handles its tiles in ticket order (needed for the lookback to progress).
+// shared-memory stages (bulk asynchronous copies, one sub-tile per stage):
+// when a scan tile (SUB sub-tiles) is done they hand its mask words to the
+// scan warp and go on.  The scan warp stores the words and the tile's count
+// (quantize) or their in-tile prefix counts and the tile's payload offset
+// (dequantize: the compute warps then patch that tile's outliers one scan
+// tile later).  Tickets are taken one scan tile at a time as the ring fills.
 
 
 template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
@@ -296,14 +297,19 @@ __global__ void k_header_empty(lcq_header* h, uint32_t dtype, uint32_t bound, do
 constexpr int kOffsetsThreads = 1024;
 constexpr int kOffsetsPerThread = 8;
 
+// total: the running outlier count over the chunks of the call (the
+// header's count when quantizing, a workspace word when decoding); hdr_cap:
+// the header that gets LCQ_STATUS_CAPACITY when the total exceeds cap, or
+// null.
 __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t* counts, uint32_t tiles,
-                                                                  uint64_t* offsets, lcq_header* hdr,
-                                                                  uint32_t first_chunk, uint64_t cap) {
+                                                                  uint64_t* offsets, uint64_t* total,
+                                                                  uint32_t first_chunk, lcq_header* hdr_cap,
+                                                                  uint64_t cap) {
     constexpr uint32_t kPass = kOffsetsThreads * kOffsetsPerThread;
     __shared__ unsigned long long s_warp[kOffsetsThreads / 32];
     __shared__ unsigned long long s_carry;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = first_chunk ? 0ull : hdr->outlier_count;  // outliers of the earlier chunks
+    if (tid == 0) s_carry = first_chunk ? 0ull : *total;  // outliers of the earlier chunks
     __syncthreads();
     for (uint32_t t0 = 0; t0 < tiles; t0 += kPass) {
         // thread tid takes tiles t0 + tid * 8 .. + 7
@@ -344,8 +350,35 @@ __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t
         __syncthreads();
     }
     if (tid == 0) {
-        hdr->outlier_count = s_carry;
-        if (s_carry > cap) atomicOr(&hdr->status, LCQ_STATUS_CAPACITY);
+        *total = s_carry;
+        if (hdr_cap && s_carry > cap) atomicOr(&hdr_cap->status, LCQ_STATUS_CAPACITY);
+    }
+}
+
+// Outliers per scan tile of WORDS mask words (the decoder's counts), one
+// warp per tile.
+template <int WORDS>
+__global__ void __launch_bounds__(256) k_tile_counts(const uint32_t* mask, uint64_t n, uint32_t tiles,
+                                                     uint32_t* counts) {
+    constexpr int WPL = WORDS / 32;
+    const int lane = threadIdx.x & 31;
+    const uint64_t nwords = (n + 31) / 32;
+    const uint32_t wstride = gridDim.x * (blockDim.x / 32);
+    for (uint32_t t = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < tiles; t += wstride) {
+        const uint64_t gw = (uint64_t)t * WORDS + (uint64_t)lane * WPL;
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < WPL; j += 4) {
+            if (gw + j + 4 <= nwords) {
+                const uint4 a = *reinterpret_cast<const uint4*>(mask + gw + j);
+                c += __popc(a.x) + __popc(a.y) + __popc(a.z) + __popc(a.w);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++) c += gw + j + i < nwords ? __popc(mask[gw + j + i]) : 0;
+            }
+        }
+        c = __reduce_add_sync(0xFFFFFFFFu, c);
+        if (lane == 0) counts[t] = c;
     }
 }
 
@@ -570,9 +603,9 @@ __global__ void k_noa_given(lcq_header* h, bool any, double mn, double mx, doubl
 
 // ---------------------------------------------------------------------------
 // Dequantize kernel: persistent CTAs; bins and mask words of each tile stream
-// into shared-memory stages.  A tile publishes its outlier count before it
-// reconstructs its values, writes the reconstructions of the quantized values
-// at once, and patches the outliers after the lookback walk.
+// into shared-memory stages.  A tile writes the reconstructions of its
+// quantized values at once and patches its outliers from the payload at the
+// tile's offset (k_tile_counts + k_tile_offsets) one scan tile later.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct DParams {
@@ -582,14 +615,13 @@ struct DParams {
     T* out;
     const lcq_header* hdr;
     WsHead* ws;
-    uint64_t* desc;
+    const uint64_t* offsets;  // payload offset per scan tile of this chunk
     uint32_t* status;
     uint64_t n;           // values in this chunk
     uint64_t n_total;
     uint32_t dtype;
     uint32_t num_tiles;
     uint32_t first_chunk;
-    ScanCfg scan;
 };
 
 template <typename T, int VPT, int STAGES, int SUB, int MINB>
@@ -613,7 +645,6 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
     __shared__ uint64_t s_pbase[2];
     __shared__ uint32_t s_epoch, s_filled, s_ok;
     __shared__ volatile uint32_t s_abort;
-    __shared__ uint64_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t full_sub = p.n / STILE;
     const uint64_t nwords = (p.n + 31) / 32;
@@ -626,7 +657,6 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
         }
         mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
-        s_base = p.first_chunk ? 0ull : ld_relaxed_u64(&p.ws->carry);
         // decode only a complete, error-free encoding of exactly these arrays
         const bool ok = p.hdr->magic == LCQ_MAGIC && p.hdr->dtype == p.dtype &&
                         p.hdr->n == p.n_total && p.hdr->status == 0u && p.hdr->mode <= 1u &&
@@ -787,13 +817,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
             }
             const uint32_t t = s_jt[b];
             if (t == kNoTile) break;
-            const uint32_t agg = scan_mask_words<WPL>(s_mask[b], s_wpre[b], nullptr, 0, 0, false);
-            if (lane == 0) lookback_publish(p.desc, t, agg, s_epoch, p.scan);
-            const uint32_t excl = lookback_walk(p.desc, t, agg, s_epoch, p.scan, &p.ws->err);
-            if (lane == 0) {
-                s_pbase[b] = s_base + excl;
-                if (t == p.num_tiles - 1) st_relaxed_u64(&p.ws->carry, s_base + excl + agg);
-            }
+            scan_mask_words<WPL>(s_mask[b], s_wpre[b], nullptr, 0, 0, false);
+            if (lane == 0) s_pbase[b] = p.offsets[t];
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_done[b]);
         }
@@ -840,13 +865,8 @@ static lcq_status with_dtype(lcq_dtype dtype, Fn&& f) {
     return LCQ_ERR_ARG;
 }
 
-static uint64_t tiles_for(uint64_t n) { return (n + kTileMin - 1) / kTileMin; }
 static uint64_t tiles_of(uint64_t n, int tile) { return (n + tile - 1) / tile; }
 
-static size_t desc_bytes(uint64_t n) {
-    const uint64_t per_chunk = n < kChunk ? n : kChunk;
-    return (size_t)(tiles_for(per_chunk) * sizeof(uint64_t));
-}
 
 // Tile table of a quantize chunk: outlier counts (uint32) and payload
 // offsets (uint64) per scan tile; every tile shape has at least
@@ -860,10 +880,22 @@ static uint64_t table_tiles(uint64_t n) {
 
 static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Workspace of the single-array calls: the head, the range-reduction
+// partials, the tile table.
 static size_t ws_size(uint64_t n) {
-    const size_t d = up256(desc_bytes(n));
     const uint64_t tt = table_tiles(n);
-    return kWsHeadBytes + d + kMinmaxPartialBytes + up256(tt * 4) + up256(tt * 8);
+    return kWsHeadBytes + kMinmaxPartialBytes + up256(tt * 4) + up256(tt * 8);
+}
+
+static uint64_t* ws_partials(void* ws) {
+    return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
+}
+static uint32_t* ws_counts(void* ws) {
+    return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes);
+}
+static uint64_t* ws_offsets(void* ws, uint64_t n) {
+    return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes +
+                                       up256(table_tiles(n) * 4));
 }
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
@@ -1171,11 +1203,9 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     }
     const uint32_t dtype = Ty<T>::kDtype;
     WsHead* head = reinterpret_cast<WsHead*>(ws);
-    const size_t dsz = up256(desc_bytes(n));
-    uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz);
-    char* table = reinterpret_cast<char*>(ws) + kWsHeadBytes + dsz + kMinmaxPartialBytes;
-    uint32_t* counts = reinterpret_cast<uint32_t*>(table);
-    uint64_t* offsets = reinterpret_cast<uint64_t*>(table + up256(table_tiles(n) * 4));
+    uint64_t* partial = ws_partials(ws);
+    uint32_t* counts = ws_counts(ws);
+    uint64_t* offsets = ws_offsets(ws, n);
 
     if (io) {
         // NOA needs the whole input for its range before any binning
@@ -1248,7 +1278,8 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         // outlier offsets and payload of this chunk
         const uint64_t tile = (uint64_t)kComputeThreads * 4 * kVariants[var].vpt * kVariants[var].sub;
         const uint32_t tiles = (uint32_t)tiles_of(len, (int)tile);
-        k_tile_offsets<<<1, kOffsetsThreads, 0, st>>>(counts, tiles, offsets, hdr, off == 0 ? 1u : 0u, cap);
+        k_tile_offsets<<<1, kOffsetsThreads, 0, st>>>(counts, tiles, offsets, &hdr->outlier_count,
+                                                       off == 0 ? 1u : 0u, hdr, cap);
         if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
         if (launch_compact<T>((int)(tile / 32), p.in, p.mask, len, counts, offsets, tiles,
                               reinterpret_cast<typename Ty<T>::U*>(outl), cap, st) != cudaSuccess)
@@ -1262,13 +1293,28 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
                                   const uint32_t* mask, const void* outl, T* out, uint32_t* status,
                                   void* ws, cudaStream_t st) {
     WsHead* head = reinterpret_cast<WsHead*>(ws);
-    uint64_t* desc = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
+    uint32_t* counts = ws_counts(ws);
+    uint64_t* offsets = ws_offsets(ws, n);
     if (n == 0) {
         k_status_only<<<1, 1, 0, st>>>(status, 0u);
         return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
     }
+    int dev = 0;
+    cudaGetDevice(&dev);
     for (uint64_t off = 0; off < n; off += kChunk) {
         const uint64_t len = (n - off) < kChunk ? (n - off) : kChunk;
+        const int var = g_variant[1][Ty<T>::kDtype][0];
+        // payload offset of every scan tile: outlier counts from the mask, then their scan
+        const uint64_t tile = (uint64_t)kComputeThreads * 4 * kVariants[var].vpt * kVariants[var].sub;
+        const uint32_t tiles = (uint32_t)tiles_of(len, (int)tile);
+        uint32_t grid = (uint32_t)device_sms(dev) * 8u;
+        if (grid > (tiles + 7) / 8) grid = (tiles + 7) / 8;
+        if (tile == 32768) k_tile_counts<1024><<<grid, 256, 0, st>>>(mask + off / 32, len, tiles, counts);
+        else if (tile == 16384) k_tile_counts<512><<<grid, 256, 0, st>>>(mask + off / 32, len, tiles, counts);
+        else return LCQ_ERR_ARG;
+        k_tile_offsets<<<1, kOffsetsThreads, 0, st>>>(counts, tiles, offsets, &head->carry, off == 0 ? 1u : 0u,
+                                                       nullptr, 0);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
         DParams<T> p;
         p.bins = bins + off;
         p.mask = mask + off / 32;
@@ -1276,15 +1322,14 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         p.out = out + off;
         p.hdr = hdr;
         p.ws = head;
-        p.desc = desc;
+        p.offsets = offsets;
         p.status = status;
         p.n = len;
         p.n_total = n;
         p.dtype = Ty<T>::kDtype;
         p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
-        p.scan = g_scan;
-        const cudaError_t e = launch_dequantize_variant<T>(g_variant[1][p.dtype][0], p, st);
+        const cudaError_t e = launch_dequantize_variant<T>(var, p, st);
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
@@ -1448,8 +1493,7 @@ lcq_status lcq_finite_range(lcq_dtype dtype, const void* d_in, uint64_t n, doubl
     if (n >= (1ull << 40)) return LCQ_ERR_ARG;
     if (ws_bytes < ws_size(n)) return LCQ_ERR_WORKSPACE;
     WsHead* head = reinterpret_cast<WsHead*>(d_ws);
-    const size_t dsz = (desc_bytes(n) + 255) & ~(size_t)255;
-    uint64_t* partial = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(d_ws) + kWsHeadBytes + dsz);
+    uint64_t* partial = ws_partials(d_ws);
     uint64_t blocks = (n / 4 + kBlock - 1) / kBlock;
     if (blocks < 1) blocks = 1;
     if (blocks > (uint64_t)kMinmaxMaxBlocks) blocks = kMinmaxMaxBlocks;

@@ -132,30 +132,25 @@ def test_workspace_reuse_across_calls():
 
 
 def test_scan_timeout_is_reported_without_hang():
-    """The decoder's bounded lookback: a tile that never publishes its scan
-    descriptor makes the successor's wait give up after the spin limit, and
-    the status carries LCQ_STATUS_TIMEOUT; the workspace is usable again once
-    zeroed."""
-    x = torch.randn(1 << 19, device=DEV)  # several scan tiles of every tile shape
+    """The batched launch's bounded lookback: a tile that never publishes its
+    scan descriptor makes the successor's wait give up after the spin limit,
+    and the array's header carries LCQ_STATUS_TIMEOUT; a new plan with a new
+    workspace then quantizes the same array exactly."""
+    x = torch.randn(1 << 19, device=DEV)  # 32 scan tiles of 16K values
     x[::1000] = float("nan")               # outliers in every tile
-    ws = P.new_workspace(x.numel(), x.device)
-    q = P.quantize(x, "abs", 1e-3)
-    out = torch.empty_like(x)
-    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    items = [(x, "abs", 1e-3, P.alloc_outputs(x.numel(), x.dtype, DEV))]
     P.debug_set_scan(spin_limit=200, drop_tile=1)
     try:
-        P.dequantize_into(q, out, ws, status)
+        P.Batch(items, DEV).run()
         torch.cuda.synchronize()
     finally:
         P.debug_set_scan(0)
-    assert int(status.item()) & P.lcq.STATUS_TIMEOUT
-    ws.zero_()
-    status.zero_()
-    P.dequantize_into(q, out, ws, status)
+    assert items[0][3].read_header().status & P.lcq.STATUS_TIMEOUT
+    again = [(x, "abs", 1e-3, P.alloc_outputs(x.numel(), x.dtype, DEV))]
+    P.Batch(again, DEV).run()
     torch.cuda.synchronize()
-    assert int(status.item()) == 0
-    oq = O.quantize(x.cpu().numpy(), "abs", 1e-3)
-    assert np.array_equal(out.cpu().numpy().view(np.uint32), O.dequantize(oq).view(np.uint32))
+    assert again[0][3].read_header().status == 0
+    compare(x, "abs", 1e-3, q=again[0][3])
 
 
 def test_dequantize_rejects_mismatched_header():
