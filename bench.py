@@ -374,7 +374,8 @@ def run_ours(args, world, rank, local):
                             "ms_per_variant": [round(m, 4) for m in ms]}
     del out_t
 
-    launches_per_step = len(BOUNDS) * len(EBS) + len(EBS)  # + NOA range kernels
+    # each call: k_quantize, k_tile_offsets, k_compact; NOA calls also k_minmax
+    launches_per_step = 3 * len(BOUNDS) * len(EBS) + len(EBS)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -577,11 +578,13 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": step_config(world),
             "pct_hbm_peak_in": 100 * value / world / hbm_peak,
-            "roofline": {"bound": "hbm", "kernel": "k_quantize<float,ABS> (ABS/NOA calls)",
+            "roofline": {"bound": "hbm",
+                         "kernel": "k_quantize<float,ABS> with its compaction (k_tile_offsets, k_compact): "
+                                   "CUDA events bracket each ABS call of the timed steps",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_source": peak_kind,
                          "alg_bytes_per_launch": alg_bytes, "traffic": traffic,
-                         "avg_launch_ms": t_abs * 1e3,
+                         "avg_launch_ms": t_abs * 1e3, "launches_per_call": 3,
                          "launches_timed": len(abs_events)},
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,
