@@ -489,14 +489,13 @@ lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, doub
                                 cudaStream_t stream);
 
 /*
- * Test hook for the bounded waits of the outlier scan of the batched launch
- * (lcq_quantize_batched; no counterpart in the paper).  spin_limit: maximum
- * polls of one predecessor's scan descriptor before the wait gives up with
- * LCQ_STATUS_TIMEOUT (0 restores the default, about one second).
- * drop_tile: index of a tile that does not publish its descriptor, so that
- * its successor's wait runs out (UINT64_MAX: none).  Affects subsequent
- * lcq_quantize_batched launches of this process (a captured graph keeps the
- * setting of its capture).
+ * Test hook for the bounded waits inside the quantize kernel (no counterpart
+ * in the paper).  drop_tile: index of a scan tile, within a launch, whose
+ * buffers the kernel's scan warp never hands back to the compute warps, so
+ * that their wait for it runs out after spin_limit polls and the call
+ * reports LCQ_STATUS_TIMEOUT (UINT64_MAX: none; spin_limit 0 restores the
+ * default).  Affects subsequent lcq_quantize calls of this process; after a
+ * timeout, re-initialise the workspace.
  */
 void lcq_debug_set_scan(uint32_t spin_limit, uint64_t drop_tile);
 

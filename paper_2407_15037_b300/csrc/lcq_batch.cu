@@ -1,17 +1,18 @@
 // lcq_batch.cu -- batched quantization: many arrays of different sizes, data
-// types, bound types and bounds in one header/range pass plus ONE persistent
-// quantize launch (the method per array is that of lcq_quant.cu, Fallin &
-// Burtscher, arXiv 2407.15037, Sec. 2.1-3.3; the batching itself has no
-// counterpart in the paper).
+// types, bound types and bounds in one header/range pass, ONE persistent
+// quantize launch and two compaction launches (the method per array is that
+// of lcq_quant.cu, Fallin & Burtscher, arXiv 2407.15037, Sec. 2.1-3.3; the
+// batching itself has no counterpart in the paper).
 //
 // Every array is cut into scan tiles of 16384 values.  A global ticket hands
 // out scan tiles of all arrays in array order; a CTA maps its ticket to the
 // array by binary search over the plan's tile prefix, streams the tile's
 // stages through its shared-memory ring (16 KB stages by default: 4096
 // float32 or 2048 float64 values each), quantizes them with the same
-// per-value code as the single-array kernel, and its scan warp runs the
-// array's own bounded decoupled lookback (descriptors are per array, so the
-// chains of different arrays never wait on each other).
+// per-value code as the single-array kernel, and its scan warp stores the
+// tile's mask words and outlier count; no CTA waits for another.  Then
+// k_batch_offsets scans each array's tile counts into payload offsets (one
+// CTA per array) and k_batch_compact writes the outliers, one warp per tile.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -90,7 +91,7 @@ __host__ __device__ inline PlanView plan_view(const void* plan, uint32_t count, 
     return v;
 }
 
-// Workspace: WsHead (256 B) | scan descriptors[total_tiles] | keys: min[count], max[count]
+// Workspace: WsHead (256 B) | per-tile count / offset[total_tiles] | keys: min[count], max[count]
 static size_t ws_bytes_for(uint64_t total_tiles, uint32_t count) {
     size_t d = (size_t)total_tiles * 8;
     d = (d + 255) & ~(size_t)255;
@@ -224,8 +225,7 @@ struct BParams {
     uint32_t count;
     uint64_t total_tiles;
     WsHead* ws;
-    uint64_t* desc;
-    ScanCfg scan;
+    uint64_t* tiles;  // per global scan tile: outlier count, then (k_batch_offsets) payload offset
 };
 
 template <typename T, int MODE, int VPT>
@@ -265,7 +265,6 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
     __shared__ uint32_t s_mask[2][kWords];
     __shared__ uint32_t s_wpre[2][kWords];
     __shared__ uint32_t s_jt[2], s_ja[2];
-    __shared__ uint64_t s_pbase[2];
     __shared__ uint32_t s_epoch, s_filled, s_cur_tile, s_cur_arr, s_cur_sub, s_cur_subs;
     __shared__ volatile uint32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -325,25 +324,16 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
                 }
             }
         };
-        // Outliers of local scan tile jj; true if the kernel must stop.
-        auto write_payload = [&](uint32_t jj) -> bool {
+        // Wait until the scan warp has taken local scan tile jj's mask words
+        // (their buffer may then be reused); true if the kernel must stop.
+        auto release_tile = [&](uint32_t jj) -> bool {
             const int bb = (int)(jj & 1u);
             bool ok = mbar_wait_or_abort(&s_done[bb], (jj >> 1) & 1u, kMbarLimit, &s_abort);
-            const Array& A = p.v.arr[s_ja[bb]];
             if (!ok && !s_abort) {
-                atomicOr(&A.hdr->status, LCQ_STATUS_TIMEOUT);
+                atomicOr(&p.v.arr[s_ja[bb]].hdr->status, LCQ_STATUS_TIMEOUT);
                 s_abort = 1;
             }
-            if (named_barrier_or(1, kComputeThreads, !ok)) return true;
-            const uint64_t t0 = (uint64_t)(s_jt[bb] - A.tile_begin) * kScanTile;
-            if (A.dtype == LCQ_F32)
-                write_outliers<float, 2>(s_mask[bb], s_wpre[bb], kWords, reinterpret_cast<const float*>(A.in) + t0,
-                                      s_pbase[bb], reinterpret_cast<uint32_t*>(A.out), A.cap);
-            else
-                write_outliers<double, 2>(s_mask[bb], s_wpre[bb], kWords, reinterpret_cast<const double*>(A.in) + t0,
-                                       s_pbase[bb], reinterpret_cast<uint64_t*>(A.out), A.cap);
-            named_barrier_sync(1, kComputeThreads);
-            return false;
+            return named_barrier_or(1, kComputeThreads, !ok);
         };
 
         if (tid == 0) issue();
@@ -382,12 +372,12 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
                     s_ja[b] = a;
                     mbar_arrive(&s_full[b]);
                 }
-                if (j >= 1 && write_payload(j - 1)) break;
+                if (j >= 1 && release_tile(j - 1)) break;
                 j++;
             }
         }
         if (!named_barrier_or(1, kComputeThreads, s_abort != 0)) {
-            if (!(j >= 1 && write_payload(j - 1)) && tid == 0) {
+            if (!(j >= 1 && release_tile(j - 1)) && tid == 0) {
                 s_jt[j & 1u] = kNoTile;
                 mbar_arrive(&s_full[j & 1u]);
             }
@@ -407,23 +397,84 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
             const uint64_t nwords = (A.n + 31) / 32;
             const uint32_t agg = scan_mask_words<kWpl>(s_mask[b], s_wpre[b], A.mask,
                                                        (uint64_t)lt * kWords + (uint64_t)lane * kWpl, nwords, true);
-            uint64_t* desc = p.desc + A.tile_begin;
-            if (lane == 0) lookback_publish(desc, lt, agg, s_epoch, p.scan);
-            const uint32_t excl = lookback_walk(desc, lt, agg, s_epoch, p.scan, &A.hdr->status);
-            if (lane == 0) {
-                s_pbase[b] = excl;
-                if (lt == A.num_tiles - 1) {
-                    const uint64_t total = (uint64_t)excl + agg;
-                    st_relaxed_u64(&A.hdr->outlier_count, total);
-                    if (total > A.cap) atomicOr(&A.hdr->status, LCQ_STATUS_CAPACITY);
-                }
-            }
+            if (lane == 0) p.tiles[t] = agg;
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_done[b]);
         }
     }
     __syncthreads();
     if (tid == 0) finish_launch(p.ws, s_epoch, nullptr, false);
+}
+
+// ---------------------------------------------------------------------------
+// Pass 3: payload offsets per array (one CTA per array: exclusive scan of its
+// tiles' counts in place, the header's outlier count and capacity status).
+// Pass 4: the outliers' raw bits, one warp per tile (compact_tile).
+// ---------------------------------------------------------------------------
+constexpr int kOffThreads = 256;
+
+__global__ void __launch_bounds__(kOffThreads) k_batch_offsets(PlanView v, uint64_t* tiles) {
+    __shared__ unsigned long long s_warp[kOffThreads / 32];
+    __shared__ unsigned long long s_carry;
+    const Array& A = v.arr[blockIdx.x];
+    uint64_t* c = tiles + A.tile_begin;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (uint32_t t0 = 0; t0 < A.num_tiles; t0 += kOffThreads) {
+        const uint32_t t = t0 + (uint32_t)tid;
+        const unsigned long long x0 = t < A.num_tiles ? c[t] : 0ull;
+        unsigned long long x = x0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = lane < kOffThreads / 32 ? s_warp[lane] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < kOffThreads / 32) s_warp[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long excl = s_carry + (warp ? s_warp[warp - 1] : 0ull) + x - x0;
+        if (t < A.num_tiles) c[t] = excl;  // every count of this pass was read above
+        __syncthreads();
+        if (tid == kOffThreads - 1) s_carry = excl + x0;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        A.hdr->outlier_count = s_carry;
+        if (s_carry > A.cap) atomicOr(&A.hdr->status, LCQ_STATUS_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_batch_compact(PlanView v, uint32_t count, uint64_t total_tiles,
+                                                       const uint64_t* tiles) {
+    const uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x / 32);
+    for (uint64_t t = (uint64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); t < total_tiles; t += wstride) {
+        const uint32_t a = find_slot(v.tile_begin, count, t);
+        const Array& A = v.arr[a];
+        const uint32_t lt = (uint32_t)(t - A.tile_begin);
+        const uint64_t off = tiles[t];
+        const uint64_t next = lt + 1 < A.num_tiles ? tiles[t + 1] : A.hdr->outlier_count;
+        const uint32_t tcount = (uint32_t)(next - off);
+        if (tcount == 0u || off >= A.cap) continue;  // the same in every lane
+        const uint64_t nwords = (A.n + 31) / 32;
+        const uint64_t w0 = (uint64_t)lt * kWords;
+        if (A.dtype == LCQ_F32)
+            compact_tile<float, kWords>(reinterpret_cast<const float*>(A.in) + (uint64_t)lt * kScanTile, A.mask + w0,
+                                        nwords - w0, tcount, off, reinterpret_cast<uint32_t*>(A.out), A.cap);
+        else
+            compact_tile<double, kWords>(reinterpret_cast<const double*>(A.in) + (uint64_t)lt * kScanTile,
+                                         A.mask + w0, nwords - w0, tcount, off, reinterpret_cast<uint64_t*>(A.out),
+                                         A.cap);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -596,9 +647,18 @@ lcq_status lcq_quantize_batched(const lcq_batch_info* h_info, const void* d_plan
     bp.count = h_info->count;
     bp.total_tiles = h_info->total_tiles;
     bp.ws = ws;
-    bp.desc = reinterpret_cast<uint64_t*>((char*)d_ws + kWsHeadBytes);
-    bp.scan = current_scan_config();
-    return launch_batch_variant(g_bvariant, bp, stream) == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
+    bp.tiles = reinterpret_cast<uint64_t*>((char*)d_ws + kWsHeadBytes);
+    if (launch_batch_variant(g_bvariant, bp, stream) != cudaSuccess) return LCQ_ERR_CUDA;
+    if (h_info->count > 0) {
+        k_batch_offsets<<<h_info->count, kOffThreads, 0, stream>>>(v, bp.tiles);
+        uint64_t cgrid = (uint64_t)device_sm_count() * 8;
+        const uint64_t need = (h_info->total_tiles + 7) / 8;
+        if (cgrid > need) cgrid = need;
+        if (cgrid < 1) cgrid = 1;
+        k_batch_compact<<<(unsigned)cgrid, 256, 0, stream>>>(v, h_info->count, h_info->total_tiles, bp.tiles);
+        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+    }
+    return LCQ_OK;
 }
 
 int lcq_batch_tune_variant_count(void) { return kNumBVariants; }

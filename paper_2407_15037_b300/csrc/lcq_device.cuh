@@ -1,8 +1,7 @@
 // lcq_device.cuh -- device-side building blocks of liblcq: per-value quantize /
 // verify / reconstruct recipes (one IEEE operation per step, explicit
 // round-to-nearest intrinsics, so nothing can be contracted into an FMA), the
-// workspace layout, and the bounded decoupled-lookback scan used to compact
-// outliers in index order.
+// workspace head and the end-of-launch bookkeeping.
 //
 // Method: Fallin & Burtscher, arXiv 2407.15037.  ABS bin (Sec. 2.2), the
 // reconstruct-and-check step (Sec. 3.1), IEEE-only arithmetic (Sec. 3.2), the
@@ -981,15 +980,15 @@ __device__ __forceinline__ T recon_out(bool rel, int32_t bin, const Consts<CT<T>
 }
 
 // ---------------------------------------------------------------------------
-// Workspace and bounded decoupled lookback
+// Workspace head and launch bookkeeping
 // ---------------------------------------------------------------------------
 
-// Workspace layout: a 256-byte head, then one 64-bit scan descriptor per tile
-// of the largest chunk, then per-block partials of the range reduction.
+// The 256-byte head of every workspace (what follows it is laid out by each
+// entry point).
 struct WsHead {
-    uint32_t ticket;  // next tile index (dynamic, so predecessors are resident)
+    uint32_t ticket;  // next scan tile index (handed out dynamically)
     uint32_t done;    // CTAs finished; the last one resets ticket/done
-    uint32_t epoch;   // launch counter; descriptors of older launches are stale
+    uint32_t epoch;   // launch counter
     uint32_t err;     // LCQ_STATUS_* bits gathered during one launch
     uint64_t carry;   // running outlier count across chunks (decoder)
 };
@@ -997,12 +996,6 @@ struct WsHead {
 constexpr size_t kWsHeadBytes = 256;
 constexpr int kMinmaxMaxBlocks = 1184;  // 8 x 148
 constexpr size_t kMinmaxPartialBytes = (size_t)kMinmaxMaxBlocks * 2 * sizeof(uint64_t);
-
-// Descriptor: [63:62] state (1 aggregate, 2 inclusive prefix), [61:32] epoch,
-// [31:0] count.  A chunk holds at most 2^31 values, so counts fit 32 bits.
-constexpr uint32_t kEpochMask = 0x3FFFFFFFu;
-constexpr uint64_t kStAgg = 1ull << 62;
-constexpr uint64_t kStPre = 2ull << 62;
 
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
     uint64_t v;
@@ -1018,95 +1011,13 @@ __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
     return v;
 }
 
-// Scan parameters shared by the kernels that compact in index order.
+// Test hook of the bounded waits (lcq_debug_set_scan): in a quantize launch
+// the scan warp never hands scan tile drop_tile back to its compute warps,
+// whose wait for it gives up after spin_limit polls with LCQ_STATUS_TIMEOUT.
 struct ScanCfg {
-    uint32_t spin_limit;  // polls before a wait gives up
-    uint64_t drop_tile;   // test hook: this tile never publishes
+    uint32_t spin_limit;
+    uint64_t drop_tile;  // UINT64_MAX: none
 };
-
-// Host: the current setting of the test hook lcq_debug_set_scan.
-ScanCfg current_scan_config();
-
-// Publish a tile's aggregate (or, for tile 0, its inclusive prefix).  Lane 0.
-__device__ __forceinline__ void lookback_publish(uint64_t* desc, uint32_t tile, uint32_t agg,
-                                                 uint32_t epoch, const ScanCfg& cfg) {
-    if ((uint64_t)tile == cfg.drop_tile) return;
-    const uint64_t tag = (uint64_t)(epoch & kEpochMask) << 32;
-    st_relaxed_u64(&desc[tile], (tile == 0 ? kStPre : kStAgg) | tag | agg);
-}
-
-// Called by all 32 lanes of one warp after lookback_publish.  Walks back over
-// the predecessors, kLbPerLane x 32 descriptors per round trip (lane j reads
-// the descriptors j*kLbPerLane .. j*kLbPerLane+kLbPerLane-1 places back,
-// closest first), until an inclusive prefix is found; publishes the tile's
-// inclusive prefix and returns its exclusive prefix.  Every wait is bounded:
-// after cfg.spin_limit polls a missing predecessor is counted as 0 and
-// LCQ_STATUS_TIMEOUT is raised, so the scan always ends.
-constexpr int kLbPerLane = 4;
-
-__device__ __forceinline__ uint32_t lookback_walk(uint64_t* desc, uint32_t tile, uint32_t agg,
-                                                  uint32_t epoch, const ScanCfg& cfg, uint32_t* err) {
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    if (tile == 0) return 0;
-    const uint32_t ep = epoch & kEpochMask;
-    const uint64_t tag = (uint64_t)ep << 32;
-    uint32_t excl = 0;
-    int64_t pos0 = (int64_t)tile - 1 - (int64_t)lane * kLbPerLane;  // closest descriptor of this lane
-    bool timed_out = false;
-    while (true) {
-        uint32_t spins = 0;
-        unsigned ns = 32;
-        uint32_t lane_sum, first_p, invalid_before;
-        while (true) {
-            uint64_t d[kLbPerLane];
-#pragma unroll
-            for (int i = 0; i < kLbPerLane; i++) {
-                const int64_t pos = pos0 - i;
-                d[i] = pos >= 0 ? ld_relaxed_u64(&desc[pos]) : (kStPre | tag);  // before tile 0: empty prefix
-            }
-            lane_sum = 0;
-            first_p = kLbPerLane;
-            invalid_before = 0;
-#pragma unroll
-            for (int i = 0; i < kLbPerLane; i++) {
-                const bool fresh = (uint32_t)((d[i] >> 32) & kEpochMask) == ep;
-                const uint32_t st = fresh ? (uint32_t)(d[i] >> 62) : 0u;
-                if (first_p == kLbPerLane) {
-                    if (st == 0u) {
-                        if (timed_out) first_p = i;  // give up on it: count 0, stop here
-                        else invalid_before = 1;
-                    } else {
-                        lane_sum += (uint32_t)d[i];
-                        if (st == 2u) first_p = i;
-                    }
-                }
-            }
-            const uint32_t pm = __ballot_sync(FULL, first_p < kLbPerLane);
-            const uint32_t need = pm ? ((pm & (0u - pm)) << 1) - 1u : FULL;  // lanes up to the first prefix
-            if ((__ballot_sync(FULL, invalid_before != 0u) & need) == 0u) break;
-            if (++spins > cfg.spin_limit) {
-                timed_out = true;
-                continue;  // re-evaluate once with missing predecessors counted as 0
-            }
-            __nanosleep(ns);
-            ns = ns < 256u ? ns * 2u : 256u;
-        }
-        const uint32_t pmask = __ballot_sync(FULL, first_p < kLbPerLane);
-        if (pmask) {
-            const int first = __ffs(pmask) - 1;
-            excl += __reduce_add_sync(FULL, lane <= first ? lane_sum : 0u);
-            break;
-        }
-        excl += __reduce_add_sync(FULL, lane_sum);
-        pos0 -= 32 * kLbPerLane;
-    }
-    if (lane == 0) {
-        if ((uint64_t)tile != cfg.drop_tile) st_relaxed_u64(&desc[tile], kStPre | tag | (uint32_t)(excl + agg));
-        if (timed_out) atomicOr(err, LCQ_STATUS_TIMEOUT);
-    }
-    return excl;
-}
 
 // End-of-launch bookkeeping, called by thread 0 of every CTA after its last
 // global write: the last CTA to finish hands the gathered error bits to

@@ -44,7 +44,7 @@ namespace lcq {
 
 constexpr int kBlock = 256;
 constexpr uint64_t kChunk = 1ull << 31;         // values per launch at most
-constexpr uint32_t kDefaultSpin = 1u << 20;     // batched lookback polls (~1 s with backoff)
+constexpr uint32_t kDefaultSpin = 1u << 20;     // default of the test hook's poll limit
 constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (seconds)
 
 // Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
@@ -67,10 +67,7 @@ constexpr Variant kVariants[] = {
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
-static ScanCfg g_scan = {kDefaultSpin, ~0ull};
-
-// The setting of the test hook lcq_debug_set_scan (read by the batched launch).
-ScanCfg current_scan_config() { return g_scan; }
+static ScanCfg g_scan = {kDefaultSpin, ~0ull};  // the test hook (lcq_debug_set_scan)
 
 // ---------------------------------------------------------------------------
 // Quantize kernel: persistent CTAs; input tiles stream into a ring of
@@ -90,6 +87,7 @@ struct QParams {
     uint32_t first_chunk;
     uint32_t consts_from_hdr;  // NOA: constants written by k_minmax
     Consts<CT<T>> c;
+    ScanCfg hook;              // test hook of the bounded tile handoff
     // header fields (written by the CTA that owns tile 0 of the first chunk)
     uint32_t dtype, bound;
     double eb, eb_abs;
@@ -168,7 +166,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
         // stop (uniform over the compute warps).
         auto release_tile = [&](uint32_t jj) -> bool {  // all compute threads
             const int bb = (int)(jj & 1u);
-            bool ok = mbar_wait_or_abort(&s_done[bb], (jj >> 1) & 1u, kMbarLimit, &s_abort);
+            const uint32_t limit = (uint64_t)s_jt[bb] == p.hook.drop_tile ? p.hook.spin_limit : kMbarLimit;
+            bool ok = mbar_wait_or_abort(&s_done[bb], (jj >> 1) & 1u, limit, &s_abort);
             if (!ok && !s_abort) {
                 atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
                 s_abort = 1;
@@ -256,7 +255,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&s_done[b]);
+            if (lane == 0 && (uint64_t)t != p.hook.drop_tile) mbar_arrive(&s_done[b]);  // test hook: never handed back
         }
     }
     __syncthreads();
@@ -382,109 +381,23 @@ __global__ void __launch_bounds__(256) k_tile_counts(const uint32_t* mask, uint6
     }
 }
 
-// One warp per scan tile of WORDS mask words: tiles without outliers cost
-// one load.  The warp takes the tile in parts of 512 words: lane l takes the
-// words [16 l, 16 l + 16) of a part, and the warp scan of their bit counts
-// gives each lane its first rank.  In a sparse tile each lane walks its own
-// words in index order and issues the loads of up to eight outliers (across
-// words) before their stores, so that the latencies overlap.  In a dense
-// tile (more than 1/8 outliers) the warp takes the words one by one with one
-// lane per bit, so that its loads and stores are coalesced.
 constexpr int kCompactThreads = 256;
 
+// One warp per scan tile (compact_tile); tiles without outliers cost one load.
 template <typename T, int WORDS>
 __global__ void __launch_bounds__(kCompactThreads) k_compact(const T* in, const uint32_t* mask, uint64_t n,
                                                              const uint32_t* counts, const uint64_t* offsets,
                                                              uint32_t tiles, typename Ty<T>::U* out, uint64_t cap) {
-    using U = typename Ty<T>::U;
-    constexpr int TILE = WORDS * 32, PART = 512, WPL = PART / 32;  // 16 words per lane and part
-    static_assert(WORDS % PART == 0, "whole parts");
-    const int lane = threadIdx.x & 31;
-    const uint32_t below = (1u << lane) - 1u;
+    constexpr int TILE = WORDS * 32;
     const uint64_t nwords = (n + 31) / 32;
     const uint32_t wstride = gridDim.x * (kCompactThreads / 32);
     for (uint32_t t = blockIdx.x * (kCompactThreads / 32) + (threadIdx.x >> 5); t < tiles; t += wstride) {
         const uint32_t tcount = counts[t];
         if (tcount == 0u) continue;  // the same in every lane
-        uint64_t pbase = offsets[t];
+        const uint64_t pbase = offsets[t];
         if (pbase >= cap) continue;
-        const bool dense = tcount > (uint32_t)(TILE / 8);
-        for (int part = 0; part < WORDS / PART; part++) {
-            const uint64_t gw = (uint64_t)t * WORDS + (uint64_t)part * PART + (uint64_t)lane * WPL;
-            uint32_t wv[WPL];
-            uint32_t cnt = 0;
-#pragma unroll
-            for (int j = 0; j < WPL; j += 4) {
-                if (gw + j + 4 <= nwords) {
-                    const uint4 a = *reinterpret_cast<const uint4*>(mask + gw + j);
-                    wv[j] = a.x; wv[j + 1] = a.y; wv[j + 2] = a.z; wv[j + 3] = a.w;
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; i++) wv[j + i] = gw + j + i < nwords ? mask[gw + j + i] : 0u;
-                }
-#pragma unroll
-                for (int i = 0; i < 4; i++) cnt += __popc(wv[j + i]);
-            }
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o) incl += y;
-            }
-            const T* gp = in + (uint64_t)t * TILE + (uint64_t)part * PART * 32;  // first value of the part
-            if (dense) {
-                for (int L = 0; L < 32; L++) {
-                    uint32_t run = __shfl_sync(0xFFFFFFFFu, incl - cnt, L);
-#pragma unroll
-                    for (int j0 = 0; j0 < WPL; j0 += 4) {
-                        uint32_t w[4], r[4];
-                        U v[4];
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            w[u] = __shfl_sync(0xFFFFFFFFu, wv[j0 + u], L);
-                            r[u] = run + __popc(w[u] & below);
-                            run += __popc(w[u]);
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; u++)
-                            if ((w[u] >> lane) & 1u) v[u] = Ty<T>::bits(gp[(uint32_t)(L * WPL + j0 + u) * 32u + lane]);
-#pragma unroll
-                        for (int u = 0; u < 4; u++)
-                            if (((w[u] >> lane) & 1u) && pbase + r[u] < cap) out[pbase + r[u]] = v[u];
-                    }
-                }
-            } else {
-                constexpr int Q = 8;
-                uint64_t rank = pbase + (incl - cnt);
-                const T* gin = gp + (uint64_t)lane * WPL * 32;
-                uint32_t qi[Q] = {0, 0, 0, 0, 0, 0, 0, 0};
-                int qn = 0;
-                auto flush = [&]() {
-                    U v[Q];
-#pragma unroll
-                    for (int u = 0; u < Q; u++)
-                        if (u < qn) v[u] = Ty<T>::bits(gin[qi[u]]);
-#pragma unroll
-                    for (int u = 0; u < Q; u++)
-                        if (u < qn && rank + u < cap) out[rank + u] = v[u];
-                    rank += (uint64_t)qn;
-                    qn = 0;
-                };
-#pragma unroll
-                for (int jw = 0; jw < WPL; jw++) {
-                    uint32_t m = wv[jw];
-                    while (m) {
-                        const uint32_t idx = (uint32_t)jw * 32u + (uint32_t)(__ffs(m) - 1);
-                        m &= m - 1u;
-#pragma unroll
-                        for (int u = 0; u < Q; u++) qi[u] = qn == u ? idx : qi[u];
-                        if (++qn == Q) flush();
-                    }
-                }
-                flush();
-            }
-            pbase += __shfl_sync(0xFFFFFFFFu, incl, 31);  // outliers of this part
-        }
+        compact_tile<T, WORDS>(in + (uint64_t)t * TILE, mask + (uint64_t)t * WORDS, nwords - (uint64_t)t * WORDS,
+                               tcount, pbase, out, cap);
     }
 }
 
@@ -1253,6 +1166,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.first_chunk = off == 0;
         p.consts_from_hdr = noa;
         p.c = c;
+        p.hook = g_scan;
         p.dtype = dtype;
         p.bound = bt;
         p.eb = eb;

@@ -1,7 +1,8 @@
 // lcq_tile.cuh -- per-tile building blocks shared by the single-array and the
 // batched streaming kernels: vector access, the 4-value quantize of one ring
 // stage ("sub-tile") into bins and shared-memory mask words, the warp scan of
-// a scan tile's mask words, and the outlier writer.
+// a scan tile's mask words, the decoder's outlier walk, the per-tile
+// compaction after quantization, and the NOA range helpers.
 #pragma once
 
 #include <cstdint>
@@ -279,20 +280,105 @@ __device__ __forceinline__ void for_each_outlier(const uint32_t* s_words, const 
     }
 }
 
-// Outliers of one scan tile of `words` mask words: the raw bits of input
-// value i (read again from global memory; the tile was read moments ago, so
-// this hits L2) go to out[pbase + rank], ranks in index order.
-template <typename T, int UNROLL = 4>
-__device__ __forceinline__ void write_outliers(const uint32_t* s_words, const uint32_t* s_wpre, int words,
-                                               const T* gin, uint64_t pbase,
-                                               typename Ty<T>::U* out, uint64_t cap) {
+// ---------------------------------------------------------------------------
+// Outlier payload of one scan tile after quantization, by one warp (all 32
+// lanes): the raw bits of the tile's outliers (tcount of them, tcount > 0) to
+// out[pbase + rank], ranks in index order, writes stopping at cap.  tin: the
+// tile's first value; tmask: its first mask word, of which words_left are
+// valid (the rest count as 0).  The warp reads the mask in parts of 512
+// words, 16 per lane, and a warp scan of the lanes' bit counts gives each
+// lane its first rank.  In a sparse tile each lane walks its own words in
+// index order and issues the loads of up to eight outliers (across words)
+// before their stores, so that the latencies overlap.  In a dense tile (more
+// than 1/8 outliers) the warp takes the words one by one with one lane per
+// bit, so that its loads and stores are coalesced.
+// ---------------------------------------------------------------------------
+template <typename T, int WORDS>
+__device__ __forceinline__ void compact_tile(const T* tin, const uint32_t* tmask, uint64_t words_left,
+                                             uint32_t tcount, uint64_t pbase, typename Ty<T>::U* out,
+                                             uint64_t cap) {
     using U = typename Ty<T>::U;
-    for_each_outlier<U, UNROLL>(
-        s_words, s_wpre, words, [&](uint32_t i, uint32_t) { return Ty<T>::bits(gin[i]); },
-        [&](uint32_t, uint32_t r, U v) {
-            const uint64_t rank = pbase + r;
-            if (rank < cap) out[rank] = v;
-        });
+    constexpr int TILE = WORDS * 32, PART = 512, WPL = PART / 32;  // 16 words per lane and part
+    static_assert(WORDS % PART == 0, "whole parts");
+    const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
+    const bool dense = tcount > (uint32_t)(TILE / 8);
+    for (int part = 0; part < WORDS / PART; part++) {
+        const uint64_t lw = (uint64_t)part * PART + (uint64_t)lane * WPL;  // the lane's first word
+        uint32_t wv[WPL];
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int j = 0; j < WPL; j += 4) {
+            if (lw + j + 4 <= words_left) {
+                const uint4 a = *reinterpret_cast<const uint4*>(tmask + lw + j);
+                wv[j] = a.x; wv[j + 1] = a.y; wv[j + 2] = a.z; wv[j + 3] = a.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++) wv[j + i] = lw + j + i < words_left ? tmask[lw + j + i] : 0u;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; i++) cnt += __popc(wv[j + i]);
+        }
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const T* gp = tin + (uint64_t)part * PART * 32;  // first value of the part
+        if (dense) {
+            for (int L = 0; L < 32; L++) {
+                uint32_t run = __shfl_sync(0xFFFFFFFFu, incl - cnt, L);
+#pragma unroll
+                for (int j0 = 0; j0 < WPL; j0 += 4) {
+                    uint32_t w[4], r[4];
+                    U v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        w[u] = __shfl_sync(0xFFFFFFFFu, wv[j0 + u], L);
+                        r[u] = run + __popc(w[u] & below);
+                        run += __popc(w[u]);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if ((w[u] >> lane) & 1u) v[u] = Ty<T>::bits(gp[(uint32_t)(L * WPL + j0 + u) * 32u + lane]);
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (((w[u] >> lane) & 1u) && pbase + r[u] < cap) out[pbase + r[u]] = v[u];
+                }
+            }
+        } else {
+            constexpr int Q = 8;
+            uint64_t rank = pbase + (incl - cnt);
+            const T* gin = gp + (uint64_t)lane * WPL * 32;
+            uint32_t qi[Q] = {0, 0, 0, 0, 0, 0, 0, 0};
+            int qn = 0;
+            auto flush = [&]() {
+                U v[Q];
+#pragma unroll
+                for (int u = 0; u < Q; u++)
+                    if (u < qn) v[u] = Ty<T>::bits(gin[qi[u]]);
+#pragma unroll
+                for (int u = 0; u < Q; u++)
+                    if (u < qn && rank + u < cap) out[rank + u] = v[u];
+                rank += (uint64_t)qn;
+                qn = 0;
+            };
+#pragma unroll
+            for (int jw = 0; jw < WPL; jw++) {
+                uint32_t m = wv[jw];
+                while (m) {
+                    const uint32_t idx = (uint32_t)jw * 32u + (uint32_t)(__ffs(m) - 1);
+                    m &= m - 1u;
+#pragma unroll
+                    for (int u = 0; u < Q; u++) qi[u] = qn == u ? idx : qi[u];
+                    if (++qn == Q) flush();
+                }
+            }
+            flush();
+        }
+        pbase += __shfl_sync(0xFFFFFFFFu, incl, 31);  // outliers of this part
+    }
 }
 
 // ---------------------------------------------------------------------------
