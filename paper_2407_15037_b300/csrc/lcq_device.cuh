@@ -742,23 +742,53 @@ __device__ __forceinline__ int32_t rint_d_small(uint64_t u) {
     return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
 }
 
-// rint_d_small, and whether q lies at least 2^-20 away from the midpoint
-// between two integers: |q - rint(q)| <= 1/2 - 2^-20.  With q = m 2^-sh,
-// 1/2 - |q - rint(q)| = |rem - half| 2^-sh; for |q| < 1/2 it is 1/2 - |q|.
-__device__ __forceinline__ int32_t rint_d_small_clear(uint64_t u, bool& clear) {
-    const int e = (int)((u >> 52) & 0x7FF);
-    const int sh = 1075 - e;  // q = m 2^-sh, m = 1.M 2^52
-    const uint64_t m = (u & kD_MANT) | (1ull << 52);
-    if (sh > 53) {  // |q| < 1/2
-        clear = sh > 54 || m <= (1ull << 53) - (1ull << 34);
+// The integer part and the top 32 bits of the fraction of a double q with
+// |q| < 2^30 (caller checks), by two funnel shifts of its significand: q =
+// ip + f 2^-32 + delta, 0 <= delta < 2^-32 (sign apart).  For |q| < 1/2 it
+// returns ip = 0, f = 0 and sets small.
+__device__ __forceinline__ uint32_t d_int_frac(uint64_t u, uint32_t& f, bool& small) {
+    const uint32_t hi = (uint32_t)(u >> 32);
+    const int sh = 1075 - (int)((hi >> 20) & 0x7FFu);  // q = m 2^-sh, 23 <= sh when |q| < 2^30
+    small = sh > 53;
+    if (small) {
+        f = 0;
         return 0;
     }
-    const uint64_t ip = m >> sh;
-    const uint64_t rem = m & ((1ull << sh) - 1);
-    const uint64_t half = 1ull << (sh - 1);
-    const uint64_t gap = rem > half ? rem - half : half - rem;
-    clear = gap >= (1ull << (sh - 20));  // sh >= 23 here since |q| < 2^30
-    const uint64_t r = ip + ((rem > half || (rem == half && (ip & 1))) ? 1 : 0);
+    const uint64_t m = (u & kD_MANT) | (1ull << 52);
+    f = (uint32_t)((m << (64 - sh)) >> 32);
+    return (uint32_t)(m >> sh);
+}
+
+// rint(q), round half to even, for |q| < 2^30 (caller checks): the fraction's
+// top 32 bits decide unless they are exactly 1/2, where rint_d_small does.
+__device__ __forceinline__ int32_t rint_d_fast(uint64_t u) {
+    uint32_t f;
+    bool small;
+    const uint32_t ip = d_int_frac(u, f, small);
+    if (small) return 0;  // |q| < 1/2
+    if (f == 0x80000000u) return rint_d_small(u);
+    const uint32_t r = ip + (f > 0x80000000u ? 1u : 0u);
+    return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
+}
+
+// rint(q) as rint_d_fast, and whether q lies at least 2^-20 away from the
+// midpoint between two integers (clear).  With q = ip + F 2^-32 + delta:
+// |F - 2^31| > 2^12 gives |frac - 1/2| >= 2^-20 + 2^-32 - delta > 2^-20 and
+// fixes the rounding direction; |q| <= 1/2 - 2^-20 is clear as well (its
+// high word below that of 0x3FDFFFFC00000000, a conservative test).  Where
+// clear is false the returned bin is exact but the caller checks anyway.
+__device__ __forceinline__ int32_t rint_d_fast_clear(uint64_t u, bool& clear) {
+    uint32_t f;
+    bool small;
+    const uint32_t ip = d_int_frac(u, f, small);
+    if (small) {
+        clear = ((uint32_t)(u >> 32) & 0x7FFFFFFFu) < 0x3FDFFFFCu;
+        return 0;
+    }
+    const uint32_t d = f > 0x80000000u ? f - 0x80000000u : 0x80000000u - f;
+    clear = d > 0x1000u;
+    if (!clear) return rint_d_small(u);
+    const uint32_t r = ip + (f > 0x80000000u ? 1u : 0u);
     return (u & kD_SIGN) ? -(int32_t)r : (int32_t)r;
 }
 
@@ -831,10 +861,10 @@ __device__ __forceinline__ bool abs_quant_f64(double x, const Consts<double>& c,
     const uint64_t uq = clear_sign(dbits(q));
     if (!(uq < 0x41D0000000000000ull)) return false;  // !(|q| < 2^30): also NaN
     bool clear;
-    const int32_t b = rint_d_small_clear(dbits(q), clear);
+    const int32_t b = rint_d_fast_clear(dbits(q), clear);
     if ((uint32_t)(b + (kMaxBinAbs - 1)) > (uint32_t)(2 * (kMaxBinAbs - 1))) return false;  // Sec. 3.3
     if constexpr (CHECK) {
-        clear = clear && clear_sign(dbits(x)) < 0x7FD0000000000000ull;  // |x| < 2^1022
+        clear = clear && ((uint32_t)(dbits(x) >> 32) & 0x7FFFFFFFu) < 0x7FD00000u;  // |x| < 2^1022
         if (!clear && !abs_check_f64(x, b, c.scale, c.ebT)) return false;
     }
     bin = b;
@@ -891,7 +921,7 @@ __device__ __forceinline__ bool rel_quant_f64(double x, const Consts<double>& c,
     const double q = __dmul_rn(L, c.inv);
     const uint64_t uq = clear_sign(dbits(q));
     if (!(uq < 0x41C0000000000000ull)) return false;  // !(|q| < 2^29)
-    const int32_t b = rint_d_small(dbits(q));
+    const int32_t b = rint_d_fast(dbits(q));
     if ((uint32_t)(b + (kMaxBinRel - 1)) > (uint32_t)(2 * (kMaxBinRel - 1))) return false;  // Sec. 3.3
     const uint64_t M = u & kD_MANT;
     const bool sure = c.cert_w != 0 && E >= c.cert_emin && M >= c.cert_w && M < (1ull << 52) - c.cert_w;
