@@ -311,15 +311,21 @@ __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t
     if (tid == 0) s_carry = first_chunk ? 0ull : *total;  // outliers of the earlier chunks
     __syncthreads();
     for (uint32_t t0 = 0; t0 < tiles; t0 += kPass) {
-        // thread tid takes tiles t0 + tid * 8 .. + 7
+        // thread tid takes tiles t0 + tid * 8 .. + 7 (two 16-byte loads where whole)
         const uint32_t tb = t0 + (uint32_t)tid * kOffsetsPerThread;
+        const bool whole = tb + kOffsetsPerThread <= tiles;
         uint32_t v[kOffsetsPerThread];
+        if (whole) {
+            const uint4 a = *reinterpret_cast<const uint4*>(counts + tb);
+            const uint4 b = *reinterpret_cast<const uint4*>(counts + tb + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int u = 0; u < kOffsetsPerThread; u++) v[u] = tb + u < tiles ? counts[tb + u] : 0u;
+        }
         unsigned long long sum = 0;
 #pragma unroll
-        for (int u = 0; u < kOffsetsPerThread; u++) {
-            v[u] = tb + u < tiles ? counts[tb + u] : 0u;
-            sum += v[u];
-        }
+        for (int u = 0; u < kOffsetsPerThread; u++) sum += v[u];
         unsigned long long x = sum;  // inclusive scan of the thread sums within the warp
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -339,10 +345,20 @@ __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t
         }
         __syncthreads();
         unsigned long long run = s_carry + (warp ? s_warp[warp - 1] : 0ull) + x - sum;
+        unsigned long long o[kOffsetsPerThread];
 #pragma unroll
         for (int u = 0; u < kOffsetsPerThread; u++) {
-            if (tb + u < tiles) offsets[tb + u] = run;
+            o[u] = run;
             run += v[u];
+        }
+        if (whole) {
+#pragma unroll
+            for (int u = 0; u < kOffsetsPerThread; u += 2)
+                *reinterpret_cast<ulonglong2*>(offsets + tb + u) = make_ulonglong2(o[u], o[u + 1]);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kOffsetsPerThread; u++)
+                if (tb + u < tiles) offsets[tb + u] = o[u];
         }
         __syncthreads();
         if (tid == kOffsetsThreads - 1) s_carry = run;
