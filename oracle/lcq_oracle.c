@@ -6,7 +6,7 @@
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
  * baseline leg of the benchmark may load this library.  It shares no code,
  * header, table or constant with the CUDA library; the two are written
- * independently from the same paper and the same numbered readings (R1..R10
+ * independently from the same paper and the same numbered readings (R1..R11
  * below), and the tests compare them element by element.
  *
  * Build (done by oracle/build.py):
