@@ -772,6 +772,30 @@ def run_profile(args):
     import paper_2407_15037_b300 as P
     import synth
     dev = torch.device("cuda", 0)
+    if args.profile == "pred":
+        # the predictor's residual kernels on a 256^3 k^-3 field (ABS 1e-3 bins):
+        # interpolation, then the network with seeded int8 weights
+        from paper_2407_15037_b300 import predictor as PD
+        N = 256
+        qp = P.quantize(synth.grf(N, seed=1000, device=dev).reshape(-1), "abs", 1e-3)
+        rng = np.random.default_rng(0)
+        pp = PD.PredParams()
+        w1 = rng.integers(-20, 21, 3 * 7 * 16 * 28)
+        for k in range(len(w1)):
+            pp.w1[k] = int(w1[k]) if k % 28 != 27 else 0
+        for k in range(3 * 7 * 16):
+            pp.b1[k] = int(rng.integers(-500, 500))
+            pp.w2[k] = int(rng.integers(-20, 21))
+        for k in range(21):
+            pp.b2[k] = int(rng.integers(-100, 100))
+        pp.s_in[0], pp.s_in[1], pp.s_in[2], pp.s1, pp.s2 = 3, 3, 2, 8, 6
+        params = PD.params_to_device(pp, dev)
+        for prm in (None, params):
+            for _ in range(2):
+                PD.residuals(qp.bins, N, prm)
+        torch.cuda.synchronize()
+        print("profile run done pred")
+        return
     shape = (256, 256, 256) if args.profile_dtype == "f64" else SHAPE
     dt = {"f32": torch.float32, "f64": torch.float64, "f16": torch.float16,
           "bf16": torch.bfloat16}[args.profile_dtype]
@@ -798,7 +822,7 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq"], default=None)
+    ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq", "pred"], default=None)
     ap.add_argument("--profile-dtype", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--profile-input", choices=["smooth", "stress"], default="smooth")
     ap.add_argument("--profile-eb", type=float, default=1e-3)
