@@ -796,6 +796,16 @@ def run_profile(args):
         torch.cuda.synchronize()
         print("profile run done pred")
         return
+    if args.profile == "compact":
+        # two REL 1e-3, two REL 1e-5 and two ABS 1e-5 calls on the float32 512^3 field
+        x = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device=dev)
+        q = P.alloc_outputs(x.numel(), x.dtype, dev)
+        ws = P.new_workspace(x.numel(), dev)
+        for bound, eb in (("rel", 1e-3),) * 2 + (("rel", 1e-5),) * 2 + (("abs", 1e-5),) * 2:
+            P.quantize_into(x, bound, eb, q, ws)
+        torch.cuda.synchronize()
+        print("profile run done compact")
+        return
     shape = (256, 256, 256) if args.profile_dtype == "f64" else SHAPE
     dt = {"f32": torch.float32, "f64": torch.float64, "f16": torch.float16,
           "bf16": torch.bfloat16}[args.profile_dtype]
@@ -822,7 +832,7 @@ def run_profile(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq", "pred"], default=None)
+    ap.add_argument("--profile", choices=["abs", "rel", "noa", "deq", "pred", "compact"], default=None)
     ap.add_argument("--profile-dtype", choices=["f32", "f64", "f16", "bf16"], default="f32")
     ap.add_argument("--profile-input", choices=["smooth", "stress"], default="smooth")
     ap.add_argument("--profile-eb", type=float, default=1e-3)
