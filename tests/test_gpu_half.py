@@ -5,9 +5,9 @@ The oracle's 16-bit recipe (the float recipe on the widened value, checked
 against the decoder's 16-bit rounding) is pinned in test_oracle_half.py.
 Cases: every 16-bit pattern at several bounds of each type (also shuffled and
 repeated over many tiles with a ragged tail, in both tile shapes), smooth
-fields with a ragged length, the NOA range entry points, the host-buffer
-entry point over several pipelined chunks, and the calls that refuse 16-bit
-data."""
+fields with a ragged length, the benchmark's 512^3 workload over every
+value, the NOA range entry points, the host-buffer entry point over several
+pipelined chunks, and the calls that refuse 16-bit data."""
 import numpy as np
 import pytest
 import torch
@@ -181,3 +181,18 @@ def test_calls_that_take_float_and_double_only():
     status = torch.zeros(1, dtype=torch.int32, device=DEV)
     P.lcq.dequantize_into(q, out, ws, status)
     assert int(status.item()) & P.lcq.STATUS_HEADER
+
+
+@pytest.mark.parametrize("fmt", ["f16", "bf16"])
+@pytest.mark.parametrize("bound", ["abs", "rel", "noa"])
+def test_full_field_512(fmt, bound):
+    """The benchmark's 16-bit workload (the float32 512^3 field rounded to the
+    format) at 1e-3, in the launch configuration the benchmark times,
+    compared with the oracle over every value."""
+    x = synth.smooth_field((512, 512, 512), dtype=torch.float32, seed=0, device=DEV).to(FMTS[fmt]).reshape(-1)
+    q = P.quantize(x, bound, 1e-3)
+    torch.cuda.synchronize()
+    bits = _bits(x)
+    xo = bits.view(np.float16) if fmt == "f16" else bits
+    c = O.consts(bound, fmt, 1e-3, x=xo if bound == "noa" else None)
+    _compare(q, O.quantize_parallel(c, xo), fmt)
