@@ -16,8 +16,9 @@
 //     x_t = clamp((bin of coarse stencil point t - base) >> s_in, -128, 127)
 //     over the 3x3x3 coarse points f + 2s (di, dj, dk) around the floor-aligned
 //     coarse point f; h_u = clamp((W1 x + b1 + 2^(s1-1)) >> s1, 0, 127);
-//     o = (W2 h + b2 + 2^(s2-1)) >> s2; pred = base + o.  Dot products use
-//     __dp4a (4 int8 products into an int32 accumulator, exact).
+//     o = (W2 h + b2 + 2^(s2-1)) >> s2; pred = base + o.  The W1 x products
+//     run on the tensor cores (bf16 operands, float32 accumulators, exact
+//     for these integers), the rest in integers.
 //   * Residual = bin - pred modulo 2^32; reconstruction adds it back level by
 //     level.
 //   * Training: shadow parameters in float32 (integer units), forward pass =
@@ -122,62 +123,9 @@ __device__ __forceinline__ void stencil(const int32_t* p, int N, int i, int j, i
     }
 }
 
-// Parameters in shared memory, W1 rows as 7 packed int32 words and a zero
-// eighth, so that a row is two 16-byte loads.
-struct SmemParams {
-    int4 w1[kNets][kNhid][2];
-    int32_t b1[kNets][kNhid];
-    int32_t w2[kNets][4];
-    int32_t b2[kNets];
-    int32_t s_in[3];
-    int32_t s1, s2;
-};
-
-__device__ __forceinline__ void load_params(SmemParams& sp, const lcq_pred_params* gp) {
-    const int32_t* w1 = reinterpret_cast<const int32_t*>(gp->w1);
-    const int32_t* w2 = reinterpret_cast<const int32_t*>(gp->w2);
-    int32_t* sw1 = reinterpret_cast<int32_t*>(&sp.w1[0][0][0]);
-    for (int x = threadIdx.x; x < kNets * kNhid * 8; x += blockDim.x) sw1[x] = (x & 7) < 7 ? w1[(x >> 3) * 7 + (x & 7)] : 0;
-    for (int x = threadIdx.x; x < kNets * kNhid; x += blockDim.x) (&sp.b1[0][0])[x] = (&gp->b1[0][0][0])[x];
-    for (int x = threadIdx.x; x < kNets * 4; x += blockDim.x) (&sp.w2[0][0])[x] = w2[x];
-    for (int x = threadIdx.x; x < kNets; x += blockDim.x) sp.b2[x] = (&gp->b2[0][0])[x];
-    if (threadIdx.x < 3) sp.s_in[threadIdx.x] = gp->s_in[threadIdx.x];
-    if (threadIdx.x == 0) { sp.s1 = gp->s1; sp.s2 = gp->s2; }
-}
-
-__device__ __forceinline__ int32_t network(const SmemParams& sp, int net, const int32_t xw[7]) {
-    int32_t hw[4] = {0, 0, 0, 0};
-#pragma unroll
-    for (int u = 0; u < kNhid; u++) {
-        int32_t z = sp.b1[net][u];
-        const int4 a = sp.w1[net][u][0], c = sp.w1[net][u][1];
-        z = __dp4a(xw[0], a.x, z);
-        z = __dp4a(xw[1], a.y, z);
-        z = __dp4a(xw[2], a.z, z);
-        z = __dp4a(xw[3], a.w, z);
-        z = __dp4a(xw[4], c.x, z);
-        z = __dp4a(xw[5], c.y, z);
-        z = __dp4a(xw[6], c.z, z);
-        int32_t h = (z + (1 << (sp.s1 - 1))) >> sp.s1;
-        h = h < 0 ? 0 : (h > 127 ? 127 : h);
-        hw[u >> 2] |= h << (8 * (u & 3));
-    }
-    int32_t o = sp.b2[net];
-#pragma unroll
-    for (int w = 0; w < 4; w++) o = __dp4a(hw[w], sp.w2[net][w], o);
-    return (o + (1 << (sp.s2 - 1))) >> sp.s2;
-}
-
-__device__ __forceinline__ int32_t predict_point(const int32_t* b, int N, int i, int j, int k, const Point& pt,
-                                                 const SmemParams* sp) {
-    const int32_t* p = b + (((size_t)i * N + j) * N + k);
-    int32_t base = interp(p, N, i, j, k, pt);
-    if (sp) {
-        int32_t xw[7];
-        stencil(p, N, i, j, k, pt, base, sp->s_in[pt.level - 1], xw);
-        base = (int32_t)((uint32_t)base + (uint32_t)network(*sp, (pt.level - 1) * 7 + (pt.cls - 1), xw));
-    }
-    return base;
+// Interpolation prediction of point (i, j, k) (not an anchor) from bins b.
+__device__ __forceinline__ int32_t interp_point(const int32_t* b, int N, int i, int j, int k, const Point& pt) {
+    return interp(b + (((size_t)i * N + j) * N + k), N, i, j, k, pt);
 }
 
 // ------------------------------------------------ network on tensor cores --
@@ -189,7 +137,7 @@ __device__ __forceinline__ int32_t predict_point(const int32_t* b, int N, int i,
 // weights are integers in [-128, 127], exact in bf16; every product is an
 // integer of magnitude <= 2^14 and every partial sum of the 27 products an
 // integer below 2^24, exact in float32 whatever the order of the additions.
-// So each accumulator equals the dp4a dot product of the definition.
+// So each accumulator equals the integer dot product of the definition.
 
 struct MmaParams {
     uint32_t bfrag[kNets][32][8];  // W1 as B fragments: [net][lane][n-tile * 4 + k-step * 2 + reg]
@@ -361,7 +309,7 @@ __global__ void __launch_bounds__(256) k_interp_residuals(const int32_t* __restr
         if (pt.level == 0) {
             res[e] = bins[e];
         } else {
-            const int32_t pr = predict_point(bins, N, i, j, k, pt, nullptr);
+            const int32_t pr = interp_point(bins, N, i, j, k, pt);
             res[e] = (int32_t)((uint32_t)bins[e] - (uint32_t)pr);
         }
     }
@@ -379,7 +327,7 @@ __global__ void __launch_bounds__(256) k_interp_reconstruct(const int32_t* __res
         if (pt.level == 0) {
             bins[e] = res[e];
         } else {
-            const int32_t pr = predict_point(bins, N, i, j, k, pt, nullptr);
+            const int32_t pr = interp_point(bins, N, i, j, k, pt);
             bins[e] = (int32_t)((uint32_t)pr + (uint32_t)res[e]);
         }
     }
