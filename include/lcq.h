@@ -62,9 +62,10 @@ extern "C" {
  * bfloat16 subnormals), Inf and NaN as outliers.  Outliers are stored as raw
  * 16-bit patterns.  The 16-bit formats are accepted by lcq_quantize,
  * lcq_dequantize, lcq_quantize_noalloc, lcq_finite_range,
- * lcq_quantize_noa_range, lcq_quantize_host(_batch) and the tuning calls
- * (quantize tile shapes 0 and 1, dequantize shapes 1 and 5); the batched
- * launch and the ablations take LCQ_F32 / LCQ_F64 only (LCQ_ERR_ARG). */
+ * lcq_quantize_noa_range, lcq_quantize_host(_batch), the batched launch
+ * (any mix of the four types) and the tuning calls (quantize tile shapes 0
+ * and 1, dequantize shapes 1 and 5); the ablations take LCQ_F32 / LCQ_F64
+ * only (LCQ_ERR_ARG). */
 typedef enum { LCQ_F32 = 0, LCQ_F64 = 1, LCQ_F16 = 2, LCQ_BF16 = 3 } lcq_dtype;
 
 /* Error-bound types, Sec. 2.1: point-wise absolute (ABS), relative (REL) and
@@ -320,10 +321,13 @@ lcq_status lcq_quantize_host_batch(lcq_host_item* items, uint32_t count, void* d
  *       prefix) to d_plan, initialises the workspace, and fills *h_info.  It
  *       synchronises `stream`.  Errors: LCQ_ERR_ARG / LCQ_ERR_BOUND for the
  *       first bad item (its index in h_info->bad_item).
- *   lcq_quantize_batched(info, plan, ws, stream)  enqueues two kernels: a
+ *   lcq_quantize_batched(info, plan, ws, stream)  enqueues four kernels: a
  *       header / NOA range pass over all arrays (min/max over finite values
- *       of every NOA array, its bound derived on the device) and one
- *       persistent quantize launch over every array's tiles.  No host work,
+ *       of every NOA array, its bound derived on the device), one persistent
+ *       quantize launch over every array's tiles (bins, mask words and each
+ *       tile's outlier count), the payload offsets of every array (an
+ *       exclusive scan of its tiles' counts, the header's outlier count) and
+ *       the outliers' raw bits in index order.  No host work,
  *       no synchronisation, no allocation: it can be captured in a CUDA graph
  *       and replayed; each replay re-reads the inputs and rewrites every
  *       output.  Per-array device errors go to that array's header status.

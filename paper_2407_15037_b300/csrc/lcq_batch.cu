@@ -8,7 +8,8 @@
 // out scan tiles of all arrays in array order; a CTA maps its ticket to the
 // array by binary search over the plan's tile prefix, streams the tile's
 // stages through its shared-memory ring (16 KB stages by default: 4096
-// float32 or 2048 float64 values each), quantizes them with the same
+// float32 or 2048 float64 values each; a 16-bit stage holds 4096 values in
+// 8 KB), quantizes them with the same
 // per-value code as the single-array kernel, and its scan warp stores the
 // tile's mask words and outlier count; no CTA waits for another.  Then
 // k_batch_offsets scans each array's tile counts into payload offsets (one
@@ -123,17 +124,17 @@ struct RParams {
 
 template <typename T>
 __device__ void range_chunk(const Array& A, uint64_t lc, uint64_t* kmin, uint64_t* kmax, uint32_t a) {
-    using U = typename Ty<T>::U;
-    __shared__ U s_lo[kRangeBlock / 32], s_hi[kRangeBlock / 32];
+    using K = typename Ty<T>::K;  // order keys (32-bit for the 16-bit formats)
+    __shared__ K s_lo[kRangeBlock / 32], s_hi[kRangeBlock / 32];
     const T* in = reinterpret_cast<const T*>(A.in);
     const uint64_t b0 = lc * kRangeChunk;
     const uint64_t e = A.n < b0 + kRangeChunk ? A.n : b0 + kRangeChunk;
-    U lo = ~(U)0, hi = (U)0;
+    K lo = ~(K)0, hi = (K)0;
     for (uint64_t i = b0 + threadIdx.x; i < e; i += kRangeBlock) minmax_accum<T>(in[i], lo, hi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const U x = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
-        const U y = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+        const K x = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        const K y = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
         lo = x < lo ? x : lo;
         hi = y > hi ? y : hi;
     }
@@ -151,6 +152,17 @@ __device__ void range_chunk(const Array& A, uint64_t lc, uint64_t* kmin, uint64_
         }
     }
     __syncthreads();
+}
+
+// The NOA bound of one array from its range keys (Sec. 2.1.3).
+template <typename T>
+__device__ void range_finalize(const Array& A, uint64_t lo, uint64_t hi) {
+    using F = Ty<T>;
+    using K = typename F::K;
+    const bool any = lo <= hi;
+    const double mn = any ? F::to_f64(F::from_bits(key_to_bits<T>((K)lo))) : 0.0;
+    const double mx = any ? F::to_f64(F::from_bits(key_to_bits<T>((K)hi))) : 0.0;
+    noa_finalize<CT<T>>(A.hdr, any, mn, mx, A.eb);
 }
 
 __global__ void __launch_bounds__(kRangeBlock) k_batch_range(RParams p) {
@@ -182,8 +194,13 @@ __global__ void __launch_bounds__(kRangeBlock) k_batch_range(RParams p) {
         const uint32_t i = find_slot(p.v.noa_begin, p.noa_count, c);
         const uint32_t a = p.v.noa_index[i];
         const Array& A = p.v.arr[a];
-        if (A.dtype == LCQ_F32) range_chunk<float>(A, c - p.v.noa_begin[i], p.kmin, p.kmax, a);
-        else range_chunk<double>(A, c - p.v.noa_begin[i], p.kmin, p.kmax, a);
+        const uint64_t lc = c - p.v.noa_begin[i];
+        switch (A.dtype) {
+            case LCQ_F32: range_chunk<float>(A, lc, p.kmin, p.kmax, a); break;
+            case LCQ_F64: range_chunk<double>(A, lc, p.kmin, p.kmax, a); break;
+            case LCQ_F16: range_chunk<f16s>(A, lc, p.kmin, p.kmax, a); break;
+            default: range_chunk<bf16s>(A, lc, p.kmin, p.kmax, a); break;
+        }
     }
     __shared__ bool s_last;
     __syncthreads();
@@ -200,15 +217,11 @@ __global__ void __launch_bounds__(kRangeBlock) k_batch_range(RParams p) {
         const Array& A = p.v.arr[a];
         const uint64_t lo = ld_relaxed_u64(&p.kmin[a]);
         const uint64_t hi = ld_relaxed_u64(&p.kmax[a]);
-        const bool any = lo <= hi;
-        if (A.dtype == LCQ_F32) {
-            const float mn = __uint_as_float(key_to_bits<float>((uint32_t)lo));
-            const float mx = __uint_as_float(key_to_bits<float>((uint32_t)hi));
-            noa_finalize<float>(A.hdr, any, mn, mx, A.eb);
-        } else {
-            const double mn = __longlong_as_double((long long)key_to_bits<double>(lo));
-            const double mx = __longlong_as_double((long long)key_to_bits<double>(hi));
-            noa_finalize<double>(A.hdr, any, mn, mx, A.eb);
+        switch (A.dtype) {
+            case LCQ_F32: range_finalize<float>(A, lo, hi); break;
+            case LCQ_F64: range_finalize<double>(A, lo, hi); break;
+            case LCQ_F16: range_finalize<f16s>(A, lo, hi); break;
+            default: range_finalize<bf16s>(A, lo, hi); break;
         }
         p.kmin[a] = ~0ull;
         p.kmax[a] = 0ull;
@@ -232,15 +245,16 @@ template <typename T, int MODE, int VPT>
 __device__ __forceinline__ void batch_subtile(const Array& A, const void* stage, uint64_t first,
                                               uint32_t* s_words, int word_base) {
     constexpr int STILE = kComputeThreads * 4 * VPT;
-    Consts<T> c;
+    using C = CT<T>;  // float constants for float32 and the 16-bit formats
+    Consts<C> c;
     if (A.bound == LCQ_NOA) {
-        c = consts_from_header<T>(A.hdr);
+        c = consts_from_header<C>(A.hdr);
     } else {
-        using U = typename Ty<T>::U;
-        c.ebT = Ty<T>::from_bits((U)A.bits[0]);
-        c.scale = Ty<T>::from_bits((U)A.bits[1]);
-        c.inv = Ty<T>::from_bits((U)A.bits[2]);
-        c.chk = Ty<T>::from_bits((U)A.bits[3]);
+        using U = typename Ty<C>::U;
+        c.ebT = Ty<C>::from_bits((U)A.bits[0]);
+        c.scale = Ty<C>::from_bits((U)A.bits[1]);
+        c.inv = Ty<C>::from_bits((U)A.bits[2]);
+        c.chk = Ty<C>::from_bits((U)A.bits[3]);
         c.all_outliers = 0;
         c.cert_w = A.cert_w;
         c.cert_emin = A.cert_emin;
@@ -256,6 +270,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
     constexpr int VF = SB / 4 / (kComputeThreads * 4);  // float32 vectors per thread per stage
     constexpr int VD = SB / 8 / (kComputeThreads * 4);  // float64
     constexpr int STILE_F = SB / 4, STILE_D = SB / 8;   // values per stage
+    // a 16-bit stage holds as many values as a float32 stage (half its bytes),
+    // so its per-thread work is the float32 one
     static_assert(VD >= 1, "a stage must hold at least one float64 vector per thread");
     extern __shared__ __align__(128) unsigned char dsmem[];
     __shared__ __align__(8) uint64_t s_stage_bar[STAGES];
@@ -297,7 +313,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
                     const uint32_t a = find_slot(p.v.tile_begin, p.count, t);
                     s_cur_tile = t;
                     s_cur_arr = a;
-                    s_cur_subs = p.v.arr[a].dtype == LCQ_F32 ? kScanTile / STILE_F : kScanTile / STILE_D;
+                    s_cur_subs = p.v.arr[a].dtype == LCQ_F64 ? kScanTile / STILE_D : kScanTile / STILE_F;
                 } else {
                     s_cur_tile = kNoTile;
                     s_cur_subs = 1;
@@ -312,13 +328,15 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
             s_filled = f + 1;
             if (t != kNoTile) {
                 const Array& A = p.v.arr[a];
-                const uint32_t es = A.dtype == LCQ_F32 ? 4u : 8u;
-                const uint64_t stile = SB / es;
+                const bool f64 = A.dtype == LCQ_F64;
+                const uint32_t es = f64 ? 8u : A.dtype == LCQ_F32 ? 4u : 2u;
+                const uint64_t stile = f64 ? STILE_D : STILE_F;
+                const uint32_t bytes = (uint32_t)(stile * es);
                 const uint64_t first = (t - A.tile_begin) * (uint64_t)kScanTile + (uint64_t)sub * stile;
                 void* dst = dsmem + (size_t)s * SB;
                 if (first + stile <= A.n) {
-                    mbar_arrive_expect_tx(&s_stage_bar[s], SB);
-                    bulk_g2s(dst, reinterpret_cast<const char*>(A.in) + first * es, SB, &s_stage_bar[s]);
+                    mbar_arrive_expect_tx(&s_stage_bar[s], bytes);
+                    bulk_g2s(dst, reinterpret_cast<const char*>(A.in) + first * es, bytes, &s_stage_bar[s]);
                 } else {
                     mbar_arrive(&s_stage_bar[s]);  // ragged or empty stage: global reads
                 }
@@ -352,16 +370,28 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
             }
             const void* stage = dsmem + (size_t)s * SB;
             const uint64_t tfirst = (t - A.tile_begin) * (uint64_t)kScanTile;
-            const bool f32 = A.dtype == LCQ_F32;
-            const uint32_t subs = f32 ? kScanTile / STILE_F : kScanTile / STILE_D;
-            if (f32) {
-                const uint64_t first = tfirst + (uint64_t)sub * STILE_F;
-                if (A.bound == LCQ_REL) batch_subtile<float, LCQ_REL, VF>(A, stage, first, s_mask[b], sub * (STILE_F / 32));
-                else batch_subtile<float, LCQ_ABS, VF>(A, stage, first, s_mask[b], sub * (STILE_F / 32));
-            } else {
-                const uint64_t first = tfirst + (uint64_t)sub * STILE_D;
-                if (A.bound == LCQ_REL) batch_subtile<double, LCQ_REL, VD>(A, stage, first, s_mask[b], sub * (STILE_D / 32));
-                else batch_subtile<double, LCQ_ABS, VD>(A, stage, first, s_mask[b], sub * (STILE_D / 32));
+            const bool f64 = A.dtype == LCQ_F64;
+            const uint32_t subs = f64 ? kScanTile / STILE_D : kScanTile / STILE_F;
+            const uint64_t first = tfirst + (uint64_t)sub * (f64 ? STILE_D : STILE_F);
+            const int wb = (int)sub * ((f64 ? STILE_D : STILE_F) / 32);
+            const bool rel = A.bound == LCQ_REL;
+            switch (A.dtype) {
+                case LCQ_F32:
+                    if (rel) batch_subtile<float, LCQ_REL, VF>(A, stage, first, s_mask[b], wb);
+                    else batch_subtile<float, LCQ_ABS, VF>(A, stage, first, s_mask[b], wb);
+                    break;
+                case LCQ_F64:
+                    if (rel) batch_subtile<double, LCQ_REL, VD>(A, stage, first, s_mask[b], wb);
+                    else batch_subtile<double, LCQ_ABS, VD>(A, stage, first, s_mask[b], wb);
+                    break;
+                case LCQ_F16:
+                    if (rel) batch_subtile<f16s, LCQ_REL, VF>(A, stage, first, s_mask[b], wb);
+                    else batch_subtile<f16s, LCQ_ABS, VF>(A, stage, first, s_mask[b], wb);
+                    break;
+                default:
+                    if (rel) batch_subtile<bf16s, LCQ_REL, VF>(A, stage, first, s_mask[b], wb);
+                    else batch_subtile<bf16s, LCQ_ABS, VF>(A, stage, first, s_mask[b], wb);
+                    break;
             }
             fence_proxy_async_smem();
             if (named_barrier_or(1, kComputeThreads, s_abort != 0)) break;  // stage s consumed
@@ -454,6 +484,13 @@ __global__ void __launch_bounds__(kOffThreads) k_batch_offsets(PlanView v, uint6
     }
 }
 
+template <typename T>
+__device__ __forceinline__ void batch_compact_tile(const Array& A, uint32_t lt, uint64_t w0, uint64_t nwords,
+                                                   uint32_t tcount, uint64_t off) {
+    compact_tile<T, kWords>(reinterpret_cast<const T*>(A.in) + (uint64_t)lt * kScanTile, A.mask + w0, nwords - w0,
+                            tcount, off, reinterpret_cast<typename Ty<T>::U*>(A.out), A.cap);
+}
+
 __global__ void __launch_bounds__(256) k_batch_compact(PlanView v, uint32_t count, uint64_t total_tiles,
                                                        const uint64_t* tiles) {
     const uint64_t wstride = (uint64_t)gridDim.x * (blockDim.x / 32);
@@ -467,13 +504,12 @@ __global__ void __launch_bounds__(256) k_batch_compact(PlanView v, uint32_t coun
         if (tcount == 0u || off >= A.cap) continue;  // the same in every lane
         const uint64_t nwords = (A.n + 31) / 32;
         const uint64_t w0 = (uint64_t)lt * kWords;
-        if (A.dtype == LCQ_F32)
-            compact_tile<float, kWords>(reinterpret_cast<const float*>(A.in) + (uint64_t)lt * kScanTile, A.mask + w0,
-                                        nwords - w0, tcount, off, reinterpret_cast<uint32_t*>(A.out), A.cap);
-        else
-            compact_tile<double, kWords>(reinterpret_cast<const double*>(A.in) + (uint64_t)lt * kScanTile,
-                                         A.mask + w0, nwords - w0, tcount, off, reinterpret_cast<uint64_t*>(A.out),
-                                         A.cap);
+        switch (A.dtype) {
+            case LCQ_F32: batch_compact_tile<float>(A, lt, w0, nwords, tcount, off); break;
+            case LCQ_F64: batch_compact_tile<double>(A, lt, w0, nwords, tcount, off); break;
+            case LCQ_F16: batch_compact_tile<f16s>(A, lt, w0, nwords, tcount, off); break;
+            default: batch_compact_tile<bf16s>(A, lt, w0, nwords, tcount, off); break;
+        }
     }
 }
 
@@ -568,7 +604,6 @@ lcq_status lcq_batch_prepare(const lcq_batch_item* h_items, uint32_t count, void
         lcq_status st = check_quantize_args((lcq_dtype)it.dtype, (lcq_bound_type)it.bound_type, it.eb,
                                             it.d_in, it.n, it.d_bins, it.d_mask, it.d_outliers,
                                             it.outlier_capacity, it.d_hdr);
-        if (st == LCQ_OK && it.dtype != LCQ_F32 && it.dtype != LCQ_F64) st = LCQ_ERR_ARG;  // float / double only
         if (st != LCQ_OK) {
             h_info->bad_item = i;
             return st;
@@ -599,7 +634,7 @@ lcq_status lcq_batch_prepare(const lcq_batch_item* h_items, uint32_t count, void
         tile_begin[i] = tiles;
         tiles += A.num_tiles;
         h_info->total_values += it.n;
-        h_info->total_bytes_in += it.n * (it.dtype == LCQ_F32 ? 4 : 8);
+        h_info->total_bytes_in += it.n * (it.dtype == LCQ_F64 ? 8 : it.dtype == LCQ_F32 ? 4 : 2);
     }
     tile_begin[count] = tiles;
     if (tiles >= 0xFFFFFFFFull) return LCQ_ERR_ARG;  // tickets are 32-bit

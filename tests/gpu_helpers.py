@@ -54,3 +54,31 @@ def compare(x, bound, eb, q=None, capacity=None, check_decode=True, oq=None):
         oxr = O.dequantize(oq)
         assert np.array_equal(xr.view(u), oxr.view(u))
     return q, oq
+
+
+CODES16 = {torch.float16: 2, torch.bfloat16: 3}
+
+
+def bits16(t):
+    return t.contiguous().view(torch.int16).cpu().numpy().view(np.uint16)
+
+
+def compare16(x, bound, eb, q):
+    """The 16-bit counterpart of compare: q (the CUDA path's result for the
+    binary16 / bfloat16 tensor x) against the oracle's 16-bit recipe, bins,
+    mask, payload, count and decoded values bit for bit."""
+    torch.cuda.synchronize()
+    bits = bits16(x).reshape(-1)
+    xo = bits.view(np.float16) if x.dtype == torch.float16 else bits
+    fmt = None if x.dtype == torch.float16 else "bf16"
+    oq = O.quantize(xo, bound, eb, fmt=fmt)
+    h = q.read_header()
+    assert h.status == 0 and h.dtype == CODES16[x.dtype]
+    assert h.outlier_count == oq.count
+    assert np.array_equal(q.bins.cpu().numpy(), oq.bins)
+    assert np.array_equal(q.mask.cpu().numpy().view(np.uint32), oq.mask)
+    assert np.array_equal(bits16(q.outliers[:oq.count]), oq.payload)
+    xr = P.dequantize(q)
+    assert xr.dtype == x.dtype
+    assert np.array_equal(bits16(xr), O.dequantize(oq).view(np.uint16))
+    return q, oq

@@ -3,7 +3,8 @@ many arrays of mixed size, dtype, bound type and bound): every array must
 get exactly what lcq_quantize gives it alone, bit for bit, also when the
 batch is captured in a CUDA graph and replayed, and for every tile-shape
 variant; a sample of a batch shaped like the 4096-array workload is checked
-against the oracle as well."""
+against the oracle as well, and so is every array of a batch of binary16
+and bfloat16 arrays."""
 import numpy as np
 import pytest
 import torch
@@ -11,23 +12,27 @@ import torch
 import oracle as O
 import paper_2407_15037_b300 as P
 import synth
-from gpu_helpers import compare
+from gpu_helpers import compare, compare16
 
 pytestmark = pytest.mark.gpu
 
 DEV = "cuda"
 
 
-def _mixed_arrays(seed=0, count=48):
+ALL_DTYPES = (torch.float32, torch.float64, torch.float16, torch.bfloat16)
+
+
+def _mixed_arrays(seed=0, count=48, dtypes=ALL_DTYPES):
     rng = np.random.default_rng(seed)
     out = []
     sizes = [0, 1, 5, 33, 4095, 16384, 16385, 40000, 100003, 250000]
     for i in range(count):
         n = sizes[i % len(sizes)] if i < len(sizes) else int(rng.integers(1, 300000))
-        dtype = torch.float32 if rng.random() < 0.5 else torch.float64
+        dtype = dtypes[int(rng.integers(len(dtypes)))]
         bound = ("abs", "rel", "noa")[i % 3]
         eb = float(10 ** rng.uniform(-5, -2))
-        x = synth.smooth_field((max(n, 1),), dtype=dtype, seed=seed * 1000 + i, device=DEV)[:n].contiguous()
+        src = dtype if dtype == torch.float64 else torch.float32
+        x = synth.smooth_field((max(n, 1),), dtype=src, seed=seed * 1000 + i, device=DEV)[:n].to(dtype).contiguous()
         if n > 10 and i % 4 == 0:
             x[:: 9] = float("nan")
         if i == 11:
@@ -108,6 +113,22 @@ def test_workload_shaped_batch_against_oracle():
         compare(x, bound, eb, q=q)
     # and every array against its single-array call
     _check_against_single(items[::16])
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_16_bit_batch_against_oracle(dtype):
+    """Ragged 16-bit arrays of every bound type, a whole 2^16-pattern sweep
+    and an all-Inf/NaN NOA array among them, each against the oracle."""
+    arrays = _mixed_arrays(seed=5, count=30, dtypes=(dtype,))
+    pats = torch.from_numpy(np.arange(1 << 16, dtype=np.uint32).astype(np.uint16).view(np.int16).copy())
+    sweep = pats.view(dtype).to(DEV)
+    arrays += [(sweep, b, 1e-3) for b in ("abs", "rel", "noa")]
+    arrays.append((torch.full((1000,), float("inf"), dtype=dtype, device=DEV), "noa", 1e-3))
+    batch, items = _prepare(arrays)
+    batch.run()
+    for x, bound, eb, q in items:
+        compare16(x, bound, eb, q)
+    _check_against_single(items)
 
 
 def test_batch_rejects_bad_items():
