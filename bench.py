@@ -374,8 +374,8 @@ def run_ours(args, world, rank, local):
                             "ms_per_variant": [round(m, 4) for m in ms]}
     del out_t
 
-    # each call: k_quantize, k_tile_offsets, k_compact; NOA calls also k_minmax
-    launches_per_step = 3 * len(BOUNDS) * len(EBS) + len(EBS)
+    # each call: k_quantize, k_compact; NOA calls also k_minmax
+    launches_per_step = 2 * len(BOUNDS) * len(EBS) + len(EBS)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize(dev)
@@ -579,12 +579,12 @@ def run_ours(args, world, rank, local):
             "config": step_config(world),
             "pct_hbm_peak_in": 100 * value / world / hbm_peak,
             "roofline": {"bound": "hbm",
-                         "kernel": "k_quantize<float,ABS> with its compaction (k_tile_offsets, k_compact): "
+                         "kernel": "k_quantize<float,ABS> with its compaction (k_compact): "
                                    "CUDA events bracket each ABS call of the timed steps",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "peak_source": peak_kind,
                          "alg_bytes_per_launch": alg_bytes, "traffic": traffic,
-                         "avg_launch_ms": t_abs * 1e3, "launches_per_call": 3,
+                         "avg_launch_ms": t_abs * 1e3, "launches_per_call": 2,
                          "launches_timed": len(abs_events)},
             "clocks": clocks,
             "gpu_launches": launches_per_step * args.steps,

@@ -28,7 +28,8 @@
  *     (lcq_workspace_init or cudaMemsetAsync); the kernels leave it ready for
  *     the next call.  One workspace must not be used by two calls that can run
  *     concurrently.  After a call that reported LCQ_STATUS_TIMEOUT, or a CUDA
- *     error, re-initialise the workspace.
+ *     error, re-initialise the workspace; also before a single-array call
+ *     uses a workspace that the batched calls used (their layout differs).
  *   - n = 0 is legal.
  *
  * Compressed representation of an array of n values of type T (float, double,

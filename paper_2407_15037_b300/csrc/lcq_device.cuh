@@ -1021,7 +1021,21 @@ struct WsHead {
     uint32_t epoch;   // launch counter
     uint32_t err;     // LCQ_STATUS_* bits gathered during one launch
     uint64_t carry;   // running outlier count across chunks (decoder)
+    uint32_t cdone;   // compaction CTAs finished; the last one resets it
 };
+
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  A
+// kernel launched with the programmatic stream serialisation attribute may
+// be scheduled while the kernel before it in the stream is still running:
+// pdl_wait() blocks until that kernel has completed and its memory writes
+// are visible (for a plain launch it returns at once), and pdl_trigger()
+// lets the next kernel be scheduled before this one ends.  Every kernel of
+// the single-array path calls pdl_wait() before it touches global memory,
+// so the overlap only hides launch latency.  The quantize kernel triggers
+// when a CTA has finished its tiles, not at its start: CTAs of the
+// compaction that were let in early made outlier-heavy calls 9% slower.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 constexpr size_t kWsHeadBytes = 256;
 constexpr int kMinmaxMaxBlocks = 1184;  // 8 x 148

@@ -12,11 +12,14 @@
 //       handed out by an atomic ticket.  Compute warps quantize, verify and
 //       store bins per value (Sec. 2.2, 3.1-3.3) and build the outlier mask
 //       words; the scan warp stores each finished tile's mask words and its
-//       outlier count.  No CTA waits for another.
-//   k_tile_offsets: the payload offset of every scan tile (exclusive scan of
-//       the counts, one CTA) and the header's outlier count.
+//       outlier count, and adds the count into its group of 64 tiles.  No
+//       CTA waits for another.
 //   k_compact: the outliers' raw bits to payload[offset + rank], ascending
-//       index order (Sec. 3.1), one warp per tile that has outliers.
+//       index order (Sec. 3.1), one warp per tile that has outliers; each
+//       CTA takes its first offset from the group and tile counts, the last
+//       CTA writes the header's outlier count.
+// The kernels are launched with programmatic stream serialisation, so each
+// one is scheduled while the one before it drains.
 // Decoding: k_tile_counts (outliers per tile from the mask) and
 // k_tile_offsets give each tile's payload offset; k_dequantize streams bins
 // and mask words by bulk copies and reconstructs the values with the
@@ -46,6 +49,7 @@ constexpr int kBlock = 256;
 constexpr uint64_t kChunk = 1ull << 31;         // values per launch at most
 constexpr uint32_t kDefaultSpin = 1u << 20;     // default of the test hook's poll limit
 constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (seconds)
+constexpr uint32_t kGroupTiles = 64;            // scan tiles per group count of the compaction
 
 // Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
 // the depth of the shared-memory stage ring.
@@ -80,6 +84,7 @@ struct QParams {
     int32_t* bins;        // chunk start
     uint32_t* mask;       // chunk start (chunk offsets are multiples of 32)
     uint32_t* counts;     // outliers per scan tile of this chunk
+    uint32_t* groups;     // outliers per kGroupTiles scan tiles (added up; zero on entry)
     lcq_header* hdr;
     WsHead* ws;
     uint64_t n;           // values in this chunk
@@ -127,6 +132,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t full_sub = p.n / STILE;
+    pdl_wait();  // the compaction is let in only when this CTA's tiles are done (below)
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) mbar_init(&s_stage_bar[s], 1);
@@ -234,6 +240,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                                                       (uint64_t)t * WORDS + (uint64_t)lane * WPL, nwords, true);
             if (lane == 0) {
                 p.counts[t] = agg;
+                if (agg) atomicAdd(&p.groups[t / kGroupTiles], agg);
                 if (t == 0 && p.first_chunk) {
                     lcq_header* h = p.hdr;
                     h->magic = LCQ_MAGIC;
@@ -258,6 +265,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             if (lane == 0 && (uint64_t)t != p.hook.drop_tile) mbar_arrive(&s_done[b]);  // test hook: never handed back
         }
     }
+    pdl_trigger();
     __syncthreads();
     if (tid == 0) finish_launch(p.ws, s_epoch, &p.hdr->status, p.first_chunk != 0);
 }
@@ -284,26 +292,33 @@ __global__ void k_header_empty(lcq_header* h, uint32_t dtype, uint32_t bound, do
 }
 
 // ---------------------------------------------------------------------------
-// Outlier compaction (after k_quantize): k_tile_offsets turns the per-tile
-// outlier counts of a chunk into payload offsets (exclusive scan, one CTA,
-// continuing the count of the earlier chunks from the header) and writes the
-// header's outlier count; k_compact walks the mask words of every tile that
-// has outliers and writes their raw bits to payload[offset + rank], in index
-// order.  Keeping this out of k_quantize leaves the streaming CTAs without
-// any dependence on one another (an in-kernel lookback made every CTA wait
-// for the slowest ones).
+// Outlier compaction (after k_quantize): k_compact places the outliers of a
+// chunk.  Each CTA takes a run of consecutive scan tiles; its first payload
+// offset is the count of the earlier chunks plus the outliers of all tiles
+// before the run, which it adds up from the group counts (k_quantize's scan
+// warps add every tile's count into the count of its group of kGroupTiles
+// tiles) and the tile counts of the group it starts in.  It scans its own
+// tiles' counts, and each warp walks the mask words of one tile with
+// outliers and writes their raw bits to payload[offset + rank], in index
+// order.  The last CTA to finish writes the header's outlier count and
+// zeroes the group counts for the next call.  Keeping this out of
+// k_quantize leaves the streaming CTAs without any dependence on one another
+// (an in-kernel lookback made every CTA wait for the slowest ones).
+//
+// The decoder turns the tile counts it takes from the mask (k_tile_counts)
+// into payload offsets with k_tile_offsets (exclusive scan, one CTA).
 // ---------------------------------------------------------------------------
 constexpr int kOffsetsThreads = 1024;
 constexpr int kOffsetsPerThread = 8;
 
-// total: the running outlier count over the chunks of the call (the
-// header's count when quantizing, a workspace word when decoding); hdr_cap:
-// the header that gets LCQ_STATUS_CAPACITY when the total exceeds cap, or
-// null.
+// The decoder's payload offsets: exclusive scan of the tile counts of a
+// chunk; total: the running outlier count over the chunks of the call (a
+// workspace word).
 __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t* counts, uint32_t tiles,
                                                                   uint64_t* offsets, uint64_t* total,
-                                                                  uint32_t first_chunk, lcq_header* hdr_cap,
-                                                                  uint64_t cap) {
+                                                                  uint32_t first_chunk) {
+    pdl_wait();
+    pdl_trigger();
     constexpr uint32_t kPass = kOffsetsThreads * kOffsetsPerThread;
     __shared__ unsigned long long s_warp[kOffsetsThreads / 32];
     __shared__ unsigned long long s_carry;
@@ -364,10 +379,7 @@ __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t
         if (tid == kOffsetsThreads - 1) s_carry = run;
         __syncthreads();
     }
-    if (tid == 0) {
-        *total = s_carry;
-        if (hdr_cap && s_carry > cap) atomicOr(&hdr_cap->status, LCQ_STATUS_CAPACITY);
-    }
+    if (tid == 0) *total = s_carry;
 }
 
 // Outliers per scan tile of WORDS mask words (the decoder's counts), one
@@ -375,6 +387,8 @@ __global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t
 template <int WORDS>
 __global__ void __launch_bounds__(256) k_tile_counts(const uint32_t* mask, uint64_t n, uint32_t tiles,
                                                      uint32_t* counts) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int WPL = WORDS / 32;
     const int lane = threadIdx.x & 31;
     const uint64_t nwords = (n + 31) / 32;
@@ -398,22 +412,113 @@ __global__ void __launch_bounds__(256) k_tile_counts(const uint32_t* mask, uint6
 }
 
 constexpr int kCompactThreads = 256;
+constexpr int kCompactWarps = kCompactThreads / 32;
 
-// One warp per scan tile (compact_tile); tiles without outliers cost one load.
+template <typename T>
+struct CParams {
+    const T* in;               // chunk start
+    const uint32_t* mask;      // chunk start
+    uint64_t n;                // values in this chunk
+    const uint32_t* counts;    // outliers per scan tile
+    uint32_t* groups;          // outliers per kGroupTiles scan tiles
+    uint32_t tiles, per;       // scan tiles of the chunk; consecutive tiles per CTA
+    typename Ty<T>::U* out;    // payload
+    uint64_t cap;              // payload capacity
+    lcq_header* hdr;
+    WsHead* ws;
+    uint32_t first_chunk;
+};
+
+// Sum over the CTA's threads (every thread gets it); s_red: kCompactWarps words.
+__device__ __forceinline__ uint32_t cta_sum(uint32_t v, uint32_t* s_red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    v = __reduce_add_sync(0xFFFFFFFFu, v);
+    __syncthreads();  // s_red may still be read from the previous call
+    if (lane == 0) s_red[warp] = v;
+    __syncthreads();
+    uint32_t t = 0;
+#pragma unroll
+    for (int w = 0; w < kCompactWarps; w++) t += s_red[w];
+    return t;
+}
+
 template <typename T, int WORDS>
-__global__ void __launch_bounds__(kCompactThreads) k_compact(const T* in, const uint32_t* mask, uint64_t n,
-                                                             const uint32_t* counts, const uint64_t* offsets,
-                                                             uint32_t tiles, typename Ty<T>::U* out, uint64_t cap) {
+__global__ void __launch_bounds__(kCompactThreads, sizeof(T) == 8 ? 3 : 4) k_compact(CParams<T> p) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int TILE = WORDS * 32;
-    const uint64_t nwords = (n + 31) / 32;
-    const uint32_t wstride = gridDim.x * (kCompactThreads / 32);
-    for (uint32_t t = blockIdx.x * (kCompactThreads / 32) + (threadIdx.x >> 5); t < tiles; t += wstride) {
-        const uint32_t tcount = counts[t];
-        if (tcount == 0u) continue;  // the same in every lane
-        const uint64_t pbase = offsets[t];
-        if (pbase >= cap) continue;
-        compact_tile<T, WORDS>(in + (uint64_t)t * TILE, mask + (uint64_t)t * WORDS, nwords - (uint64_t)t * WORDS,
-                               tcount, pbase, out, cap);
+    __shared__ uint32_t s_red[kCompactWarps];
+    __shared__ uint32_t s_wsum[kCompactWarps];
+    __shared__ uint32_t s_cnt[kCompactThreads];
+    __shared__ uint64_t s_off[kCompactThreads];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t nwords = (p.n + 31) / 32;
+    // outliers of the earlier chunks (the header's count, written by the
+    // last CTA of the previous chunk's compaction)
+    const uint64_t carry = p.first_chunk ? 0ull : p.hdr->outlier_count;
+    const uint32_t t0 = blockIdx.x * p.per < p.tiles ? blockIdx.x * p.per : p.tiles;
+    const uint32_t t1 = t0 + p.per < p.tiles ? t0 + p.per : p.tiles;
+    // outliers of the tiles before t0: whole groups, then single tiles
+    const uint32_t g0 = t0 / kGroupTiles;
+    uint32_t before = 0;
+    for (uint32_t g = tid; g < g0; g += kCompactThreads) before += p.groups[g];
+    for (uint32_t t = g0 * kGroupTiles + tid; t < t0; t += kCompactThreads) before += p.counts[t];
+    uint64_t base = carry + cta_sum(before, s_red);
+    for (uint32_t b = t0; b < t1; b += kCompactThreads) {
+        // exclusive scan of up to kCompactThreads tile counts
+        const uint32_t c = b + tid < t1 ? p.counts[b + tid] : 0u;
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_wsum[warp] = x;
+        __syncthreads();
+        uint32_t wpre = 0, pass = 0;
+#pragma unroll
+        for (int w = 0; w < kCompactWarps; w++) {
+            const uint32_t v = s_wsum[w];
+            wpre += w < warp ? v : 0u;
+            pass += v;
+        }
+        s_cnt[tid] = c;
+        s_off[tid] = base + wpre + x - c;
+        __syncthreads();
+        const uint32_t m = t1 - b < (uint32_t)kCompactThreads ? t1 - b : (uint32_t)kCompactThreads;
+        for (uint32_t i = (uint32_t)warp; i < m; i += kCompactWarps) {
+            const uint32_t tcount = s_cnt[i];
+            const uint64_t pbase = s_off[i];
+            if (tcount == 0u || pbase >= p.cap) continue;  // the same in every lane
+            const uint64_t t = b + i;
+            compact_tile<T, WORDS>(p.in + t * TILE, p.mask + t * WORDS, nwords - t * WORDS, tcount, pbase, p.out,
+                                   p.cap);
+        }
+        base += pass;
+        __syncthreads();  // s_wsum, s_cnt and s_off are rewritten by the next pass
+    }
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&p.ws->cdone, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    // last CTA: every other CTA has read the group counts
+    __threadfence();
+    const uint32_t ng = (p.tiles + kGroupTiles - 1) / kGroupTiles;
+    uint32_t total = 0;
+    for (uint32_t g = tid; g < ng; g += kCompactThreads) {
+        total += p.groups[g];
+        p.groups[g] = 0u;
+    }
+    total = cta_sum(total, s_red);
+    if (tid == 0) {
+        const uint64_t all = carry + total;
+        p.hdr->outlier_count = all;
+        if (all > p.cap) atomicOr(&p.hdr->status, LCQ_STATUS_CAPACITY);
+        p.ws->cdone = 0u;
+        __threadfence();
     }
 }
 
@@ -435,6 +540,8 @@ struct MParams {
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_minmax(MParams<T> p) {
+    pdl_wait();
+    pdl_trigger();
     using F = Ty<T>;
     using U = typename F::K;  // order keys
     __shared__ U s_lo[kBlock / 32], s_hi[kBlock / 32];
@@ -577,6 +684,8 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t full_sub = p.n / STILE;
     const uint64_t nwords = (p.n + 31) / 32;
+    pdl_wait();
+    pdl_trigger();
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; s++) mbar_init(&s_stage_bar[s], 1);
@@ -810,21 +919,32 @@ static uint64_t table_tiles(uint64_t n) {
 static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Workspace of the single-array calls: the head, the range-reduction
-// partials, the tile table.
+// partials, the compaction's group counts, and the tile table (counts, the
+// decoder's offsets).  The group counts must be zero when a quantize call
+// starts, so they sit at a fixed place, sized for the largest chunk: the
+// table's place depends on n, and a call on a larger array writes offsets
+// where a smaller array's table would end.
+constexpr size_t kGroupBytes = (kChunk / kTileValuesMin + kGroupTiles - 1) / kGroupTiles * 4;  // 8 KB
+static_assert(kGroupBytes % 256 == 0, "256-byte aligned regions");
+
 static size_t ws_size(uint64_t n) {
     const uint64_t tt = table_tiles(n);
-    return kWsHeadBytes + kMinmaxPartialBytes + up256(tt * 4) + up256(tt * 8);
+    return kWsHeadBytes + kMinmaxPartialBytes + kGroupBytes + up256(tt * 4) + up256(tt * 8);
 }
 
 static uint64_t* ws_partials(void* ws) {
     return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
 }
-static uint32_t* ws_counts(void* ws) {
+static uint32_t* ws_groups(void* ws) {
     return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes);
+}
+static uint32_t* ws_counts(void* ws) {
+    return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes +
+                                       kGroupBytes);
 }
 static uint64_t* ws_offsets(void* ws, uint64_t n) {
     return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes +
-                                       up256(table_tiles(n) * 4));
+                                       kGroupBytes + up256(table_tiles(n) * 4));
 }
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
@@ -856,6 +976,26 @@ static int persistent_blocks(K kernel, size_t dyn_smem, int threads, GridCache& 
     return cache.blocks_per_sm[slot] * device_sms(dev);
 }
 
+// Launch with programmatic stream serialisation (the kernel starts with
+// pdl_wait / pdl_trigger): its CTAs may be scheduled while the previous
+// kernel of the stream drains.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    return e != cudaSuccess ? e : cudaPeekAtLastError();
+}
+
 template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
 static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
     static GridCache cache{};
@@ -866,8 +1006,7 @@ static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
     q.num_tiles = (uint32_t)tiles_of(p.n, STILE * SUB);
     uint64_t grid = (uint64_t)persistent_blocks(kern, smem, kSpecThreads, cache);
     if (grid > q.num_tiles) grid = q.num_tiles;
-    kern<<<(unsigned)grid, kSpecThreads, smem, st>>>(q);
-    return cudaPeekAtLastError();
+    return launch_pdl(kern, (unsigned)grid, kSpecThreads, smem, st, q);
 }
 
 template <typename T, int VPT, int STAGES, int SUB, int MINB>
@@ -880,8 +1019,7 @@ static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
     q.num_tiles = (uint32_t)tiles_of(p.n, STILE * SUB);
     uint64_t grid = (uint64_t)persistent_blocks(kern, smem, kSpecThreads, cache);
     if (grid > q.num_tiles) grid = q.num_tiles;
-    kern<<<(unsigned)grid, kSpecThreads, smem, st>>>(q);
-    return cudaPeekAtLastError();
+    return launch_pdl(kern, (unsigned)grid, kSpecThreads, smem, st, q);
 }
 
 // Variant dispatch (the template arguments must be compile-time constants).
@@ -948,24 +1086,20 @@ static cudaError_t launch_ablation(const QParams<T>& p, cudaStream_t st) {
 }
 
 // The compaction kernel for scan tiles of `words` mask words (every tile
-// shape has 512 or 1024).
+// shape has 512 or 1024): runs of about kCompactWarps tiles per CTA, at most
+// 8 CTAs per SM.
 template <typename T>
-static cudaError_t launch_compact(int words, const T* in, const uint32_t* mask, uint64_t n, const uint32_t* counts,
-                                  const uint64_t* offsets, uint32_t tiles, typename Ty<T>::U* out, uint64_t cap,
-                                  cudaStream_t st) {
+static cudaError_t launch_compact(int words, CParams<T> p, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const uint32_t warps = kCompactThreads / 32;
     uint32_t grid = (uint32_t)device_sms(dev) * 8u;
-    if (grid > (tiles + warps - 1) / warps) grid = (tiles + warps - 1) / warps;
+    if (grid > (p.tiles + kCompactWarps - 1) / kCompactWarps) grid = (p.tiles + kCompactWarps - 1) / kCompactWarps;
     if (grid < 1) grid = 1;
-    if (words == 1024)
-        k_compact<T, 1024><<<grid, kCompactThreads, 0, st>>>(in, mask, n, counts, offsets, tiles, out, cap);
-    else if (words == 512)
-        k_compact<T, 512><<<grid, kCompactThreads, 0, st>>>(in, mask, n, counts, offsets, tiles, out, cap);
-    else
-        return cudaErrorInvalidValue;
-    return cudaPeekAtLastError();
+    p.per = (p.tiles + grid - 1) / grid;
+    grid = (p.tiles + p.per - 1) / p.per;
+    if (words == 1024) return launch_pdl(k_compact<T, 1024>, grid, kCompactThreads, 0, st, p);
+    if (words == 512) return launch_pdl(k_compact<T, 512>, grid, kCompactThreads, 0, st, p);
+    return cudaErrorInvalidValue;
 }
 
 // Selected variant per kernel kind (0 quantize, 1 dequantize), dtype (float32,
@@ -1134,7 +1268,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     WsHead* head = reinterpret_cast<WsHead*>(ws);
     uint64_t* partial = ws_partials(ws);
     uint32_t* counts = ws_counts(ws);
-    uint64_t* offsets = ws_offsets(ws, n);
+    uint32_t* groups = ws_groups(ws);
 
     if (io) {
         // NOA needs the whole input for its range before any binning
@@ -1151,8 +1285,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         uint64_t blocks = (n / 4 + kBlock - 1) / kBlock;
         if (blocks < 1) blocks = 1;
         if (blocks > (uint64_t)kMinmaxMaxBlocks) blocks = kMinmaxMaxBlocks;
-        k_minmax<T><<<(unsigned)blocks, kBlock, 0, st>>>(mp);
-        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+        if (launch_pdl(k_minmax<T>, (unsigned)blocks, kBlock, 0, st, mp) != cudaSuccess) return LCQ_ERR_CUDA;
     }
     const double eb_abs = bt == LCQ_ABS ? eb : 0.0;
     if (n == 0) {
@@ -1175,6 +1308,7 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.bins = bins + off;
         p.mask = mask + off / 32;
         p.counts = counts;
+        p.groups = groups;
         p.hdr = hdr;
         p.ws = head;
         p.n = len;
@@ -1208,12 +1342,20 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         // outlier offsets and payload of this chunk
         const uint64_t tile = (uint64_t)kComputeThreads * 4 * kVariants[var].vpt * kVariants[var].sub;
         const uint32_t tiles = (uint32_t)tiles_of(len, (int)tile);
-        k_tile_offsets<<<1, kOffsetsThreads, 0, st>>>(counts, tiles, offsets, &hdr->outlier_count,
-                                                       off == 0 ? 1u : 0u, hdr, cap);
-        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
-        if (launch_compact<T>((int)(tile / 32), p.in, p.mask, len, counts, offsets, tiles,
-                              reinterpret_cast<typename Ty<T>::U*>(outl), cap, st) != cudaSuccess)
-            return LCQ_ERR_CUDA;
+        CParams<T> cp;
+        cp.in = p.in;
+        cp.mask = p.mask;
+        cp.n = len;
+        cp.counts = counts;
+        cp.groups = groups;
+        cp.tiles = tiles;
+        cp.per = 0;  // set at launch
+        cp.out = reinterpret_cast<typename Ty<T>::U*>(outl);
+        cp.cap = cap;
+        cp.hdr = hdr;
+        cp.ws = head;
+        cp.first_chunk = off == 0 ? 1u : 0u;
+        if (launch_compact<T>((int)(tile / 32), cp, st) != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
 }
@@ -1239,12 +1381,15 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         const uint32_t tiles = (uint32_t)tiles_of(len, (int)tile);
         uint32_t grid = (uint32_t)device_sms(dev) * 8u;
         if (grid > (tiles + 7) / 8) grid = (tiles + 7) / 8;
-        if (tile == 32768) k_tile_counts<1024><<<grid, 256, 0, st>>>(mask + off / 32, len, tiles, counts);
-        else if (tile == 16384) k_tile_counts<512><<<grid, 256, 0, st>>>(mask + off / 32, len, tiles, counts);
+        const uint32_t* cmask = mask + off / 32;
+        cudaError_t e;
+        if (tile == 32768) e = launch_pdl(k_tile_counts<1024>, grid, 256, 0, st, cmask, len, tiles, counts);
+        else if (tile == 16384) e = launch_pdl(k_tile_counts<512>, grid, 256, 0, st, cmask, len, tiles, counts);
         else return LCQ_ERR_ARG;
-        k_tile_offsets<<<1, kOffsetsThreads, 0, st>>>(counts, tiles, offsets, &head->carry, off == 0 ? 1u : 0u,
-                                                       nullptr, 0);
-        if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
+        if (e != cudaSuccess) return LCQ_ERR_CUDA;
+        if (launch_pdl(k_tile_offsets, 1, kOffsetsThreads, 0, st, (const uint32_t*)counts, tiles, offsets,
+                       &head->carry, off == 0 ? 1u : 0u) != cudaSuccess)
+            return LCQ_ERR_CUDA;
         DParams<T> p;
         p.bins = bins + off;
         p.mask = mask + off / 32;
@@ -1259,8 +1404,7 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         p.dtype = Ty<T>::kDtype;
         p.num_tiles = 0;  // set per tile shape at launch
         p.first_chunk = off == 0;
-        const cudaError_t e = launch_dequantize_variant<T>(var, p, st);
-        if (e != cudaSuccess) return LCQ_ERR_CUDA;
+        if (launch_dequantize_variant<T>(var, p, st) != cudaSuccess) return LCQ_ERR_CUDA;
     }
     return LCQ_OK;
 }

@@ -131,6 +131,25 @@ def test_workspace_reuse_across_calls():
         compare(x, bound, 1e-4, q=q)
 
 
+def test_workspace_shared_by_arrays_of_different_sizes():
+    """One workspace sized for the largest array serves quantize and
+    dequantize calls on arrays of several sizes in turn (a large array's
+    tile table covers the place where a small array's would lie): every
+    result, encoded and decoded with that workspace, equals the oracle's."""
+    sizes = [1 << 24, 300007, 1 << 24, 5000, (1 << 22) + 3]
+    ws = P.new_workspace(1 << 24, DEV)
+    for i, n in enumerate(sizes):
+        x = synth.smooth_field((n,), dtype=torch.float32, seed=40 + i, device=DEV)
+        for bound, eb in (("abs", 1e-5), ("rel", 1e-4), ("noa", 1e-5)):
+            q = P.alloc_outputs(n, x.dtype, x.device)
+            P.quantize_into(x, bound, eb, q, ws)
+            xr = torch.empty_like(x)
+            P.lcq.dequantize_into(q, xr, ws)
+            _, oq = compare(x, bound, eb, q=q, check_decode=False)
+            assert oq.count > 0
+            assert np.array_equal(xr.cpu().numpy().view(np.uint32), O.dequantize(oq).view(np.uint32))
+
+
 def test_scan_timeout_is_reported_without_hang():
     """A bounded wait that runs out: with the test hook, the quantize kernel's
     scan warp never hands scan tile 1 back to its compute warps; their wait
