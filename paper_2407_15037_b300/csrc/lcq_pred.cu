@@ -141,7 +141,7 @@ __device__ __forceinline__ int32_t interp_point(const int32_t* b, int N, int i, 
 
 struct MmaParams {
     uint32_t bfrag[kNets][32][8];  // W1 as B fragments: [net][lane][n-tile * 4 + k-step * 2 + reg]
-    int32_t b1[kNets][kNhid];
+    uint32_t zk[kNets][kNhid];     // b1 + 2^(s1-1) - bits(1.5 2^23), mod 2^32 (see network_mma)
     int32_t w2[kNets][kNhid];
     int32_t b2[kNets];
     int32_t s_in[3];
@@ -168,8 +168,9 @@ __device__ __forceinline__ void load_mma_params(MmaParams& mp, const lcq_pred_pa
         const int w0 = k < kNin ? row[k] : 0, w1 = k + 1 < kNin ? row[k + 1] : 0;
         mp.bfrag[net][lane][slot] = bf16_pair(w0, w1);
     }
+    const uint32_t r1 = 1u << (gp->s1 - 1);
     for (int x = threadIdx.x; x < kNets * kNhid; x += blockDim.x) {
-        (&mp.b1[0][0])[x] = (&gp->b1[0][0][0])[x];
+        (&mp.zk[0][0])[x] = (uint32_t)(&gp->b1[0][0][0])[x] + r1 - 0x4B400000u;
         (&mp.w2[0][0])[x] = (&gp->w2[0][0][0])[x];
     }
     for (int x = threadIdx.x; x < kNets; x += blockDim.x) mp.b2[x] = (&gp->b2[0][0])[x];
@@ -219,9 +220,12 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
                 mma_bf16(c[mt][nt], a[mt][ks], mp.bfrag[net][lane][nt * 4 + ks * 2],
                          mp.bfrag[net][lane][nt * 4 + ks * 2 + 1]);
         }
-    // hidden units 8 nt + 2 q + {0, 1} of points 16 mt + 8 hf + g (g = lane / 4, q = lane % 4)
+    // hidden units 8 nt + 2 q + {0, 1} of points 16 mt + 8 hf + g (g = lane / 4, q = lane % 4).
+    // Each accumulator is an integer v with |v| <= 27 * 128 * 128 < 2^22, so
+    // RN(v + 1.5 2^23) = 1.5 2^23 + v exactly and its bit pattern minus that
+    // of 1.5 2^23 is v: z + 2^(s1-1) = bits(v + 1.5 2^23) + zk[u] (mod 2^32).
     const int q = lane & 3, g = lane >> 2;
-    const int s1 = mp.s1, r1 = 1 << (s1 - 1);
+    const int s1 = mp.s1;
     int32_t o[2][2];
 #pragma unroll
     for (int mt = 0; mt < 2; mt++)
@@ -233,8 +237,8 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
 #pragma unroll
                 for (int e = 0; e < 2; e++) {
                     const int u = 8 * nt + 2 * q + e;
-                    const int32_t z = __float2int_rn(c[mt][nt][2 * hf + e]) + mp.b1[net][u];
-                    int32_t h = (z + r1) >> s1;
+                    const uint32_t zb = __float_as_uint(__fadd_rn(c[mt][nt][2 * hf + e], 12582912.0f));
+                    int32_t h = (int32_t)(zb + mp.zk[net][u]) >> s1;
                     h = h < 0 ? 0 : (h > 127 ? 127 : h);
                     acc += mp.w2[net][u] * h;
                 }
@@ -252,9 +256,17 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
 }
 
 // The 27 stencil inputs of the point (as in `stencil`) written to the lane's
-// row of the staging tile as bf16 pairs; inputs 27..31 are 0.
-__device__ __forceinline__ void stencil_row(const int32_t* p, int N, int i, int j, int k, const Point& pt,
-                                            int32_t base, int s_in, uint32_t* row) {
+// row of the staging tile as bf16 pairs (inputs 27..31 are 0); returns the
+// point's interpolation base (as `interp`) without loads of its own.  The
+// interpolation corners are stencil positions: along an axis where the
+// point's coordinate x is an odd multiple of s, the floor of x to a multiple
+// of 2s is x - s, so positions 1 and 2 are x - s and clamp(x + s), its two
+// corners; along an even axis position 1 is x itself.  Summing positions
+// {1, 2} of the odd axes and position 1 twice on the even ones adds every
+// distinct corner 2^(3 - c) times (c odd axes), so with that sum A the base
+// (sum + 2^(c-1)) >> c is (A + 4) >> 3.
+__device__ __forceinline__ int32_t stencil_row(const int32_t* p, int N, int i, int j, int k, const Point& pt,
+                                               int s_in, uint32_t* row) {
     const int s2 = 2 * pt.s, last = ((N - 1) >> pt.sh) << pt.sh, NN = N * N;
     const int fi = (i >> pt.sh) << pt.sh, fj = (j >> pt.sh) << pt.sh, fk = (k >> pt.sh) << pt.sh;
     int oi[3], oj[3], ok[3];
@@ -264,12 +276,29 @@ __device__ __forceinline__ void stencil_row(const int32_t* p, int N, int i, int 
         oj[d] = axis_off(clampc(fj + s2 * (d - 1), last), j, N);
         ok[d] = clampc(fk + s2 * (d - 1), last) - k;
     }
+    int32_t c[kNin];
+#pragma unroll
+    for (int t = 0; t < kNin; t++) c[t] = p[oi[t / 9] + oj[(t / 3) % 3] + ok[t % 3]];
+    // interpolation base from positions 1 and 2 (|bins| < 2^30: pairs fit in int32)
+    const bool odd_i = pt.cls & 1, odd_j = pt.cls & 2, odd_k = pt.cls & 4;
+    long long rj[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        long long rk[2];
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int32_t v1 = c[(a + 1) * 9 + (b + 1) * 3 + 1], v2 = c[(a + 1) * 9 + (b + 1) * 3 + 2];
+            rk[b] = (long long)(v1 + (odd_k ? v2 : v1));
+        }
+        rj[a] = rk[0] + (odd_j ? rk[1] : rk[0]);
+    }
+    const long long acc = rj[0] + (odd_i ? rj[1] : rj[0]);
+    const int32_t base = (int32_t)((acc + 4) >> 3);
     int dv[32];
 #pragma unroll
     for (int t = 0; t < 32; t++) {
         if (t < kNin) {
-            const int32_t c = p[oi[t / 9] + oj[(t / 3) % 3] + ok[t % 3]];
-            int32_t d = (c - base) >> s_in;
+            int32_t d = (c[t] - base) >> s_in;
             dv[t] = d < -128 ? -128 : (d > 127 ? 127 : d);
         } else {
             dv[t] = 0;
@@ -281,6 +310,7 @@ __device__ __forceinline__ void stencil_row(const int32_t* p, int N, int i, int 
                                                         bf16_pair(dv[2 * w + 2], dv[2 * w + 3]),
                                                         bf16_pair(dv[2 * w + 4], dv[2 * w + 5]),
                                                         bf16_pair(dv[2 * w + 6], dv[2 * w + 7]));
+    return base;
 }
 
 // ---------------------------------------------------------------- kernels --
@@ -407,8 +437,8 @@ __global__ void __launch_bounds__(256) k_net_groups(const int32_t* __restrict__ 
         pt.level = G.level; pt.s = G.s; pt.cls = G.cls; pt.sh = __ffs(G.s);
         const int32_t* bins = RECON ? out : in;
         const int32_t* pp = bins + e;
-        const int32_t base = interp(pp, N, i, j, k, pt);  // k is a valid point of the group in every lane
-        stencil_row(pp, N, i, j, k, pt, base, mp.s_in[pt.level - 1], arow + lane * kArow);
+        // k is a valid point of the group in every lane
+        const int32_t base = stencil_row(pp, N, i, j, k, pt, mp.s_in[pt.level - 1], arow + lane * kArow);
         const int net = (pt.level - 1) * 7 + (pt.cls - 1);
         const int32_t pr = (int32_t)((uint32_t)base + (uint32_t)network_mma(mp, net, arow));
         __syncwarp();  // the staging tile is rewritten by the next chunk
