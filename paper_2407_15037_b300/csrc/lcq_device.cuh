@@ -1066,12 +1066,14 @@ struct ScanCfg {
 // End-of-launch bookkeeping, called by thread 0 of every CTA after its last
 // global write: the last CTA to finish hands the gathered error bits to
 // *status_out (assigning on the first chunk of a call, OR-ing later) and
-// resets the ticket for the next launch on this workspace.
-__device__ __forceinline__ void finish_launch(WsHead* ws, uint32_t epoch, uint32_t* status_out,
+// resets the ticket for the next launch on this workspace.  Returns true in
+// the last CTA.
+__device__ __forceinline__ bool finish_launch(WsHead* ws, uint32_t epoch, uint32_t* status_out,
                                               bool assign) {
     __threadfence();
     const uint32_t prev = atomicAdd(&ws->done, 1u);
-    if (prev == gridDim.x - 1) {
+    const bool last = prev == gridDim.x - 1;
+    if (last) {
         __threadfence();
         const uint32_t e = atomicExch(&ws->err, 0u);
         if (status_out) {
@@ -1083,6 +1085,7 @@ __device__ __forceinline__ void finish_launch(WsHead* ws, uint32_t epoch, uint32
         atomicExch(&ws->epoch, epoch + 1u);
         __threadfence();
     }
+    return last;
 }
 
 }  // namespace lcq

@@ -20,11 +20,11 @@
 //       CTA writes the header's outlier count.
 // The kernels are launched with programmatic stream serialisation, so each
 // one is scheduled while the one before it drains.
-// Decoding: k_tile_counts (outliers per tile from the mask) and
-// k_tile_offsets give each tile's payload offset; k_dequantize streams bins
-// and mask words by bulk copies and reconstructs the values with the
-// encoder's exact operations (Sec. 3.1; no double-check on decode, Sec. 6),
-// patching the outliers from the payload.
+// Decoding: k_tile_counts (outliers per tile and per group of 64 tiles,
+// from the mask); k_dequantize streams bins and mask words by bulk copies,
+// reconstructs the values with the encoder's exact operations (Sec. 3.1; no
+// double-check on decode, Sec. 6), and patches the outliers from the payload
+// at offsets its scan warp adds up from those counts.
 //
 // Arrays longer than kChunk values are processed as several launches; the
 // running outlier count carries from one chunk to the next in device memory,
@@ -305,88 +305,16 @@ __global__ void k_header_empty(lcq_header* h, uint32_t dtype, uint32_t bound, do
 // k_quantize leaves the streaming CTAs without any dependence on one another
 // (an in-kernel lookback made every CTA wait for the slowest ones).
 //
-// The decoder turns the tile counts it takes from the mask (k_tile_counts)
-// into payload offsets with k_tile_offsets (exclusive scan, one CTA).
+// The decoder takes each tile's outlier count from the mask (k_tile_counts,
+// which adds the group counts too), and its scan warp adds up a tile's
+// payload offset the same way.
 // ---------------------------------------------------------------------------
-constexpr int kOffsetsThreads = 1024;
-constexpr int kOffsetsPerThread = 8;
-
-// The decoder's payload offsets: exclusive scan of the tile counts of a
-// chunk; total: the running outlier count over the chunks of the call (a
-// workspace word).
-__global__ void __launch_bounds__(kOffsetsThreads) k_tile_offsets(const uint32_t* counts, uint32_t tiles,
-                                                                  uint64_t* offsets, uint64_t* total,
-                                                                  uint32_t first_chunk) {
-    pdl_wait();
-    pdl_trigger();
-    constexpr uint32_t kPass = kOffsetsThreads * kOffsetsPerThread;
-    __shared__ unsigned long long s_warp[kOffsetsThreads / 32];
-    __shared__ unsigned long long s_carry;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) s_carry = first_chunk ? 0ull : *total;  // outliers of the earlier chunks
-    __syncthreads();
-    for (uint32_t t0 = 0; t0 < tiles; t0 += kPass) {
-        // thread tid takes tiles t0 + tid * 8 .. + 7 (two 16-byte loads where whole)
-        const uint32_t tb = t0 + (uint32_t)tid * kOffsetsPerThread;
-        const bool whole = tb + kOffsetsPerThread <= tiles;
-        uint32_t v[kOffsetsPerThread];
-        if (whole) {
-            const uint4 a = *reinterpret_cast<const uint4*>(counts + tb);
-            const uint4 b = *reinterpret_cast<const uint4*>(counts + tb + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-        } else {
-#pragma unroll
-            for (int u = 0; u < kOffsetsPerThread; u++) v[u] = tb + u < tiles ? counts[tb + u] : 0u;
-        }
-        unsigned long long sum = 0;
-#pragma unroll
-        for (int u = 0; u < kOffsetsPerThread; u++) sum += v[u];
-        unsigned long long x = sum;  // inclusive scan of the thread sums within the warp
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long w = s_warp[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, o);
-                if (lane >= o) w += y;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        unsigned long long run = s_carry + (warp ? s_warp[warp - 1] : 0ull) + x - sum;
-        unsigned long long o[kOffsetsPerThread];
-#pragma unroll
-        for (int u = 0; u < kOffsetsPerThread; u++) {
-            o[u] = run;
-            run += v[u];
-        }
-        if (whole) {
-#pragma unroll
-            for (int u = 0; u < kOffsetsPerThread; u += 2)
-                *reinterpret_cast<ulonglong2*>(offsets + tb + u) = make_ulonglong2(o[u], o[u + 1]);
-        } else {
-#pragma unroll
-            for (int u = 0; u < kOffsetsPerThread; u++)
-                if (tb + u < tiles) offsets[tb + u] = o[u];
-        }
-        __syncthreads();
-        if (tid == kOffsetsThreads - 1) s_carry = run;
-        __syncthreads();
-    }
-    if (tid == 0) *total = s_carry;
-}
 
 // Outliers per scan tile of WORDS mask words (the decoder's counts), one
-// warp per tile.
+// warp per tile; each count is also added into its group count.
 template <int WORDS>
 __global__ void __launch_bounds__(256) k_tile_counts(const uint32_t* mask, uint64_t n, uint32_t tiles,
-                                                     uint32_t* counts) {
+                                                     uint32_t* counts, uint32_t* groups) {
     pdl_wait();
     pdl_trigger();
     constexpr int WPL = WORDS / 32;
@@ -407,7 +335,10 @@ __global__ void __launch_bounds__(256) k_tile_counts(const uint32_t* mask, uint6
             }
         }
         c = __reduce_add_sync(0xFFFFFFFFu, c);
-        if (lane == 0) counts[t] = c;
+        if (lane == 0) {
+            counts[t] = c;
+            if (c) atomicAdd(&groups[t / kGroupTiles], c);
+        }
     }
 }
 
@@ -641,7 +572,10 @@ __global__ void k_noa_given(lcq_header* h, bool any, double mn, double mx, doubl
 // Dequantize kernel: persistent CTAs; bins and mask words of each tile stream
 // into shared-memory stages.  A tile writes the reconstructions of its
 // quantized values at once and patches its outliers from the payload at the
-// tile's offset (k_tile_counts + k_tile_offsets) one scan tile later.
+// tile's offset one scan tile later.  The scan warp adds up that offset from
+// the counts of k_tile_counts: the earlier chunks' total (a workspace word),
+// the group counts of the whole groups before the tile and the tile counts
+// of its own group; the last CTA updates the total and zeroes the groups.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct DParams {
@@ -651,7 +585,8 @@ struct DParams {
     T* out;
     const lcq_header* hdr;
     WsHead* ws;
-    const uint64_t* offsets;  // payload offset per scan tile of this chunk
+    const uint32_t* counts;   // outliers per scan tile of this chunk (k_tile_counts)
+    uint32_t* groups;         // outliers per kGroupTiles scan tiles (k_tile_counts; zeroed here)
     uint32_t* status;
     uint64_t n;           // values in this chunk
     uint64_t n_total;
@@ -679,6 +614,9 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
     __shared__ uint32_t s_wpre[2][WORDS];
     __shared__ uint32_t s_jt[2];
     __shared__ uint64_t s_pbase[2];
+    __shared__ uint64_t s_carry;  // outliers of the earlier chunks of the call
+    __shared__ uint32_t s_total;
+    __shared__ bool s_last;
     __shared__ uint32_t s_epoch, s_filled, s_ok;
     __shared__ volatile uint32_t s_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -695,6 +633,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
         }
         mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
+        s_carry = p.first_chunk ? 0ull : p.ws->carry;  // rewritten only by this launch's last CTA
         // decode only a complete, error-free encoding of exactly these arrays
         const bool ok = p.hdr->magic == LCQ_MAGIC && p.hdr->dtype == p.dtype &&
                         p.hdr->n == p.n_total && p.hdr->status == 0u && p.hdr->mode <= 1u &&
@@ -856,13 +795,39 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
             const uint32_t t = s_jt[b];
             if (t == kNoTile) break;
             scan_mask_words<WPL>(s_mask[b], s_wpre[b], nullptr, 0, 0, false);
-            if (lane == 0) s_pbase[b] = p.offsets[t];
+            // payload offset of tile t: the earlier chunks, the whole groups
+            // before t, the tiles of t's group before t
+            const uint32_t g0 = t / kGroupTiles;
+            uint32_t before = 0;
+            for (uint32_t g = (uint32_t)lane; g < g0; g += 32) before += p.groups[g];
+            for (uint32_t u = g0 * kGroupTiles + (uint32_t)lane; u < t; u += 32) before += p.counts[u];
+            before = __reduce_add_sync(0xFFFFFFFFu, before);
+            if (lane == 0) s_pbase[b] = s_carry + before;
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_done[b]);
         }
     }
     __syncthreads();
-    if (tid == 0) finish_launch(p.ws, s_epoch, p.status, p.first_chunk != 0);
+    if (tid == 0) s_last = finish_launch(p.ws, s_epoch, p.status, p.first_chunk != 0);
+    __syncthreads();
+    if (!s_last) return;
+    // last CTA (every scan warp has read the group counts): the running
+    // outlier count for the next chunk, and zero group counts for the next call
+    if (tid == 0) s_total = 0;
+    __syncthreads();
+    const uint32_t ng = (p.num_tiles + kGroupTiles - 1) / kGroupTiles;
+    uint32_t tot = 0;
+    for (uint32_t g = (uint32_t)tid; g < ng; g += kSpecThreads) {
+        tot += p.groups[g];
+        p.groups[g] = 0u;
+    }
+    tot = __reduce_add_sync(0xFFFFFFFFu, tot);
+    if (lane == 0) atomicAdd(&s_total, tot);
+    __syncthreads();
+    if (tid == 0) {
+        p.ws->carry = s_carry + s_total;
+        __threadfence();
+    }
 }
 
 __global__ void k_status_only(uint32_t* status, uint32_t bits) {
@@ -906,9 +871,8 @@ static lcq_status with_dtype(lcq_dtype dtype, Fn&& f) {
 static uint64_t tiles_of(uint64_t n, int tile) { return (n + tile - 1) / tile; }
 
 
-// Tile table of a quantize chunk: outlier counts (uint32) and payload
-// offsets (uint64) per scan tile; every tile shape has at least
-// kTileValuesMin values per scan tile.
+// Tile table of a chunk: outlier counts (uint32) per scan tile; every tile
+// shape has at least kTileValuesMin values per scan tile.
 constexpr uint64_t kTileValuesMin = 16384;
 
 static uint64_t table_tiles(uint64_t n) {
@@ -919,17 +883,15 @@ static uint64_t table_tiles(uint64_t n) {
 static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Workspace of the single-array calls: the head, the range-reduction
-// partials, the compaction's group counts, and the tile table (counts, the
-// decoder's offsets).  The group counts must be zero when a quantize call
-// starts, so they sit at a fixed place, sized for the largest chunk: the
-// table's place depends on n, and a call on a larger array writes offsets
-// where a smaller array's table would end.
+// partials, the group counts, and the tile counts.  The group counts must be
+// zero when a call starts, so every call leaves them zero, and they sit at a
+// fixed place sized for the largest chunk, whatever the n of the call.
 constexpr size_t kGroupBytes = (kChunk / kTileValuesMin + kGroupTiles - 1) / kGroupTiles * 4;  // 8 KB
 static_assert(kGroupBytes % 256 == 0, "256-byte aligned regions");
 
 static size_t ws_size(uint64_t n) {
     const uint64_t tt = table_tiles(n);
-    return kWsHeadBytes + kMinmaxPartialBytes + kGroupBytes + up256(tt * 4) + up256(tt * 8);
+    return kWsHeadBytes + kMinmaxPartialBytes + kGroupBytes + up256(tt * 4);
 }
 
 static uint64_t* ws_partials(void* ws) {
@@ -941,10 +903,6 @@ static uint32_t* ws_groups(void* ws) {
 static uint32_t* ws_counts(void* ws) {
     return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes +
                                        kGroupBytes);
-}
-static uint64_t* ws_offsets(void* ws, uint64_t n) {
-    return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes + kMinmaxPartialBytes +
-                                       kGroupBytes + up256(table_tiles(n) * 4));
 }
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
@@ -1366,7 +1324,7 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
                                   void* ws, cudaStream_t st) {
     WsHead* head = reinterpret_cast<WsHead*>(ws);
     uint32_t* counts = ws_counts(ws);
-    uint64_t* offsets = ws_offsets(ws, n);
+    uint32_t* groups = ws_groups(ws);
     if (n == 0) {
         k_status_only<<<1, 1, 0, st>>>(status, 0u);
         return cudaPeekAtLastError() == cudaSuccess ? LCQ_OK : LCQ_ERR_CUDA;
@@ -1376,20 +1334,17 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
     for (uint64_t off = 0; off < n; off += kChunk) {
         const uint64_t len = (n - off) < kChunk ? (n - off) : kChunk;
         const int var = g_variant[1][Ty<T>::kDtype][0];
-        // payload offset of every scan tile: outlier counts from the mask, then their scan
+        // outlier counts of the scan tiles (and their groups) from the mask
         const uint64_t tile = (uint64_t)kComputeThreads * 4 * kVariants[var].vpt * kVariants[var].sub;
         const uint32_t tiles = (uint32_t)tiles_of(len, (int)tile);
         uint32_t grid = (uint32_t)device_sms(dev) * 8u;
         if (grid > (tiles + 7) / 8) grid = (tiles + 7) / 8;
         const uint32_t* cmask = mask + off / 32;
         cudaError_t e;
-        if (tile == 32768) e = launch_pdl(k_tile_counts<1024>, grid, 256, 0, st, cmask, len, tiles, counts);
-        else if (tile == 16384) e = launch_pdl(k_tile_counts<512>, grid, 256, 0, st, cmask, len, tiles, counts);
+        if (tile == 32768) e = launch_pdl(k_tile_counts<1024>, grid, 256, 0, st, cmask, len, tiles, counts, groups);
+        else if (tile == 16384) e = launch_pdl(k_tile_counts<512>, grid, 256, 0, st, cmask, len, tiles, counts, groups);
         else return LCQ_ERR_ARG;
         if (e != cudaSuccess) return LCQ_ERR_CUDA;
-        if (launch_pdl(k_tile_offsets, 1, kOffsetsThreads, 0, st, (const uint32_t*)counts, tiles, offsets,
-                       &head->carry, off == 0 ? 1u : 0u) != cudaSuccess)
-            return LCQ_ERR_CUDA;
         DParams<T> p;
         p.bins = bins + off;
         p.mask = mask + off / 32;
@@ -1397,7 +1352,8 @@ static lcq_status dequantize_impl(uint64_t n, const lcq_header* hdr, const int32
         p.out = out + off;
         p.hdr = hdr;
         p.ws = head;
-        p.offsets = offsets;
+        p.counts = counts;
+        p.groups = groups;
         p.status = status;
         p.n = len;
         p.n_total = n;
