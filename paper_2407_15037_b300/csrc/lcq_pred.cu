@@ -88,15 +88,13 @@ __device__ __forceinline__ int32_t interp(const int32_t* p, int N, int i, int j,
     const int j1 = (pt.cls & 2) ? axis_off(clampc(j + s, last), j, N) : 0;
     const int k0 = (pt.cls & 4) ? clampc(k - s, last) - k : 0;
     const int k1 = (pt.cls & 4) ? clampc(k + s, last) - k : 0;
-    const int c = __popc(pt.cls);
+    // all 8 end combinations: along an even axis both ends are the point's own
+    // coordinate, so each of the 2^c distinct corners (c odd axes) is added
+    // 2^(3 - c) times and the mean (sum + 2^(c-1)) >> c is (acc + 4) >> 3
     long long acc = 0;
-    // enumerate the 2^c distinct corners: along an even axis both ends coincide
 #pragma unroll
-    for (int q = 0; q < 8; q++) {
-        if ((q & ~pt.cls) != 0) continue;
-        acc += p[((q & 1) ? i1 : i0) + ((q & 2) ? j1 : j0) + ((q & 4) ? k1 : k0)];
-    }
-    return (int32_t)((acc + (1ll << (c - 1))) >> c);
+    for (int q = 0; q < 8; q++) acc += p[((q & 1) ? i1 : i0) + ((q & 2) ? j1 : j0) + ((q & 4) ? k1 : k0)];
+    return (int32_t)((acc + 4) >> 3);
 }
 
 // The 27 stencil inputs packed 4 per int32 (byte 3 of word 6 is 0);
