@@ -17,8 +17,8 @@
 //     over the 3x3x3 coarse points f + 2s (di, dj, dk) around the floor-aligned
 //     coarse point f; h_u = clamp((W1 x + b1 + 2^(s1-1)) >> s1, 0, 127);
 //     o = (W2 h + b2 + 2^(s2-1)) >> s2; pred = base + o.  The W1 x products
-//     run on the tensor cores (bf16 operands, float32 accumulators, exact
-//     for these integers), the rest in integers.
+//     run on the tensor cores (binary16 operands, float32 accumulators,
+//     exact for these integers), the rest in integers.
 //   * Residual = bin - pred modulo 2^32; reconstruction adds it back level by
 //     level.
 //   * Training: shadow parameters in float32 (integer units), forward pass =
@@ -26,10 +26,11 @@
 //     integer below 2^24, so float32 holds it exactly), loss = mean squared
 //     residual, straight-through gradients; per-CTA partial gradients are
 //     summed in a fixed order (deterministic), then Adam.
+#include <climits>
 #include <cmath>
 #include <cstring>
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lcq.h"
@@ -130,16 +131,20 @@ __device__ __forceinline__ int32_t interp_point(const int32_t* b, int N, int i, 
 //
 // A warp evaluates the network for 32 points of one (level, class) at once:
 // hidden = W1 x as a [32 points x 32 inputs] x [32 inputs x 16 hidden]
-// product on the tensor cores (mma.sync m16n8k16, bf16 operands, float32
-// accumulators), the rest in integers.  This is exact: the inputs and
-// weights are integers in [-128, 127], exact in bf16; every product is an
-// integer of magnitude <= 2^14 and every partial sum of the 27 products an
-// integer below 2^24, exact in float32 whatever the order of the additions.
-// So each accumulator equals the integer dot product of the definition.
+// product on the tensor cores (mma.sync m16n8k16, binary16 operands, float32
+// accumulators), the rest in integers.  The A operand holds 640 + x_t rather
+// than x_t: for x_t in [-128, 127] that is an integer in [512, 767], where
+// binary16 values are spaced 1/2 apart, so its bit pattern is just
+// 0x6100 + 2 x_t (no conversion); the extra 640 sum_t W1[u][t] is taken off
+// with the bias.  This is exact: the weights are integers in [-128, 127] and
+// the inputs integers below 768, all exact in binary16; every product has
+// magnitude below 2^17 and every partial sum of the 27 products is an
+// integer below 27 * 128 * 767 < 2^22, exact in float32 whatever the order
+// of the additions.  So each accumulator equals the integer dot product.
 
 struct MmaParams {
     uint32_t bfrag[kNets][32][8];  // W1 as B fragments: [net][lane][n-tile * 4 + k-step * 2 + reg]
-    uint32_t zk[kNets][kNhid];     // b1 + 2^(s1-1) - bits(1.5 2^23), mod 2^32 (see network_mma)
+    uint32_t zk[kNets][kNhid];     // b1 + 2^(s1-1) - 640 sum_t W1[u][t] - bits(1.5 2^23), mod 2^32
     int32_t w2[kNets][kNhid];
     int32_t b2[kNets];
     int32_t s_in[3];
@@ -148,12 +153,16 @@ struct MmaParams {
 
 constexpr int kArow = 20;  // words per point row of the A staging tile (16 used; 80 B rows: no bank conflicts)
 
-__device__ __forceinline__ uint32_t bf16_pair(int lo, int hi) {
-    // exact floats of small integers by the 1.5 * 2^23 magic, then one packed conversion (exact)
-    const float a = __fsub_rn(__int_as_float(0x4B400000 + lo), 12582912.0f);
-    const float b = __fsub_rn(__int_as_float(0x4B400000 + hi), 12582912.0f);
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);  // .x = a (low half), .y = b
+// Two int8 weights as a binary16 pair (exact; .x = lo in the low half).
+__device__ __forceinline__ uint32_t half_pair(int lo, int hi) {
+    const __half2 v = __floats2half2_rn((float)lo, (float)hi);
     return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Two inputs x in [-128, 127] as the binary16 pair (640 + lo, 640 + hi):
+// bit patterns 0x6100 + 2 x; the low half never borrows from the high one.
+__device__ __forceinline__ uint32_t input_pair(int lo, int hi) {
+    return 0x61006100u + (uint32_t)(2 * lo) + ((uint32_t)hi << 17);
 }
 
 __device__ __forceinline__ void load_mma_params(MmaParams& mp, const lcq_pred_params* gp) {
@@ -164,11 +173,14 @@ __device__ __forceinline__ void load_mma_params(MmaParams& mp, const lcq_pred_pa
         const int k = 16 * ks + 2 * (lane & 3) + 8 * reg;        // first of two inputs
         const int8_t* row = &gp->w1[net / 7][net % 7][n][0];
         const int w0 = k < kNin ? row[k] : 0, w1 = k + 1 < kNin ? row[k + 1] : 0;
-        mp.bfrag[net][lane][slot] = bf16_pair(w0, w1);
+        mp.bfrag[net][lane][slot] = half_pair(w0, w1);
     }
     const uint32_t r1 = 1u << (gp->s1 - 1);
     for (int x = threadIdx.x; x < kNets * kNhid; x += blockDim.x) {
-        (&mp.zk[0][0])[x] = (uint32_t)(&gp->b1[0][0][0])[x] + r1 - 0x4B400000u;
+        const int8_t* row = &gp->w1[x / (7 * kNhid)][(x / kNhid) % 7][x % kNhid][0];
+        int32_t wsum = 0;
+        for (int t = 0; t < kNin; t++) wsum += row[t];
+        (&mp.zk[0][0])[x] = (uint32_t)(&gp->b1[0][0][0])[x] + r1 - 0x4B400000u - 640u * (uint32_t)wsum;
         (&mp.w2[0][0])[x] = (&gp->w2[0][0][0])[x];
     }
     for (int x = threadIdx.x; x < kNets; x += blockDim.x) mp.b2[x] = (&gp->b2[0][0])[x];
@@ -176,8 +188,8 @@ __device__ __forceinline__ void load_mma_params(MmaParams& mp, const lcq_pred_pa
     if (threadIdx.x == 0) { mp.s1 = gp->s1; mp.s2 = gp->s2; }
 }
 
-__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+__device__ __forceinline__ void mma_f16(float c[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
                  "{%0,%1,%2,%3};"
                  : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
                  : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
@@ -203,7 +215,7 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
         for (int ks = 0; ks < 2; ks++) {
             const int mtx = lane >> 3, r = lane & 7;
             const int point = 16 * mt + r + 8 * (mtx & 1);
-            const int col = 16 * ks + 8 * (mtx >> 1);  // bf16 column
+            const int col = 16 * ks + 8 * (mtx >> 1);  // binary16 column
             ldmatrix_x4(a[mt][ks], base + (uint32_t)(point * kArow * 4 + col * 2));
         }
     float c[2][2][4];
@@ -215,13 +227,14 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
             for (int v = 0; v < 4; v++) c[mt][nt][v] = 0.0f;
 #pragma unroll
             for (int ks = 0; ks < 2; ks++)
-                mma_bf16(c[mt][nt], a[mt][ks], mp.bfrag[net][lane][nt * 4 + ks * 2],
+                mma_f16(c[mt][nt], a[mt][ks], mp.bfrag[net][lane][nt * 4 + ks * 2],
                          mp.bfrag[net][lane][nt * 4 + ks * 2 + 1]);
         }
     // hidden units 8 nt + 2 q + {0, 1} of points 16 mt + 8 hf + g (g = lane / 4, q = lane % 4).
-    // Each accumulator is an integer v with |v| <= 27 * 128 * 128 < 2^22, so
-    // RN(v + 1.5 2^23) = 1.5 2^23 + v exactly and its bit pattern minus that
-    // of 1.5 2^23 is v: z + 2^(s1-1) = bits(v + 1.5 2^23) + zk[u] (mod 2^32).
+    // Each accumulator is an integer v = W1 x + 640 sum_t W1[u][t] with
+    // |v| <= 27 * 128 * 767 < 2^22, so RN(v + 1.5 2^23) = 1.5 2^23 + v exactly
+    // and its bit pattern minus that of 1.5 2^23 is v:
+    // z + 2^(s1-1) = bits(v + 1.5 2^23) + zk[u] (mod 2^32).
     const int q = lane & 3, g = lane >> 2;
     const int s1 = mp.s1;
     int32_t o[2][2];
@@ -254,7 +267,8 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
 }
 
 // The 27 stencil inputs of the point (as in `stencil`) written to the lane's
-// row of the staging tile as bf16 pairs (inputs 27..31 are 0); returns the
+// row of the staging tile as binary16 pairs of 640 + x_t (x_t = 0 for the
+// inputs 27..31, whose weights are 0); returns the
 // point's interpolation base (as `interp`) without loads of its own.  The
 // interpolation corners are stencil positions: along an axis where the
 // point's coordinate x is an odd multiple of s, the floor of x to a multiple
@@ -292,22 +306,27 @@ __device__ __forceinline__ int32_t stencil_row(const int32_t* p, int N, int i, i
     }
     const long long acc = rj[0] + (odd_i ? rj[1] : rj[0]);
     const int32_t base = (int32_t)((acc + 4) >> 3);
+    // clamp before the shift: x >> s_in <= 127 iff x <= 128 2^s_in - 1, and
+    // >= -128 iff x >= -128 2^s_in (for s_in >= 24 every |x| < 2^31 already
+    // shifts into [-128, 127])
+    const int32_t lo = s_in >= 24 ? INT_MIN : -(128 << s_in);
+    const int32_t hi = s_in >= 24 ? INT_MAX : (128 << s_in) - 1;
     int dv[32];
 #pragma unroll
     for (int t = 0; t < 32; t++) {
         if (t < kNin) {
-            int32_t d = (c[t] - base) >> s_in;
-            dv[t] = d < -128 ? -128 : (d > 127 ? 127 : d);
+            const int32_t x = __viaddmax_s32(c[t], -base, lo);  // max(c - base, lo); |c|, |base| < 2^30
+            dv[t] = (x < hi ? x : hi) >> s_in;
         } else {
             dv[t] = 0;
         }
     }
 #pragma unroll
     for (int w = 0; w < 16; w += 4)
-        *reinterpret_cast<uint4*>(row + w) = make_uint4(bf16_pair(dv[2 * w], dv[2 * w + 1]),
-                                                        bf16_pair(dv[2 * w + 2], dv[2 * w + 3]),
-                                                        bf16_pair(dv[2 * w + 4], dv[2 * w + 5]),
-                                                        bf16_pair(dv[2 * w + 6], dv[2 * w + 7]));
+        *reinterpret_cast<uint4*>(row + w) = make_uint4(input_pair(dv[2 * w], dv[2 * w + 1]),
+                                                        input_pair(dv[2 * w + 2], dv[2 * w + 3]),
+                                                        input_pair(dv[2 * w + 4], dv[2 * w + 5]),
+                                                        input_pair(dv[2 * w + 6], dv[2 * w + 7]));
     return base;
 }
 
