@@ -130,7 +130,16 @@ __device__ void range_chunk(const Array& A, uint64_t lc, uint64_t* kmin, uint64_
     const uint64_t b0 = lc * kRangeChunk;
     const uint64_t e = A.n < b0 + kRangeChunk ? A.n : b0 + kRangeChunk;
     K lo = ~(K)0, hi = (K)0;
-    for (uint64_t i = b0 + threadIdx.x; i < e; i += kRangeBlock) minmax_accum<T>(in[i], lo, hi);
+    // four values per load (chunks start at multiples of 16384 values, so
+    // every vector is aligned), then the ragged end of the array
+    const uint64_t nv = (e - b0) / 4;
+    for (uint64_t v = threadIdx.x; v < nv; v += kRangeBlock) {
+        T x[4];
+        Vec4<T>::load_cached(in + b0 + 4 * v, x);
+#pragma unroll
+        for (int k = 0; k < 4; k++) minmax_accum<T>(x[k], lo, hi);
+    }
+    for (uint64_t i = b0 + 4 * nv + threadIdx.x; i < e; i += kRangeBlock) minmax_accum<T>(in[i], lo, hi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const K x = __shfl_xor_sync(0xFFFFFFFFu, lo, o);

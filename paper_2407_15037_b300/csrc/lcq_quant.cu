@@ -478,15 +478,33 @@ __global__ void __launch_bounds__(kBlock) k_minmax(MParams<T> p) {
     __shared__ U s_lo[kBlock / 32], s_hi[kBlock / 32];
     __shared__ bool s_last;
     U lo = ~(U)0, hi = (U)0;
-    const uint64_t nvec = p.n / 4;
     const uint64_t stride = (uint64_t)gridDim.x * kBlock;
-    for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < nvec; i += stride) {
-        T x[4];
-        Vec4<T>::load_cached(p.in + 4 * i, x);
+    uint64_t done;  // values covered by whole vectors
+    if constexpr (is16<T>()) {
+        // eight 16-bit values per 16-byte load (four would leave half as many
+        // bytes in flight as the float32 loop)
+        const uint64_t nvec = p.n / 8;
+        for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < nvec; i += stride) {
+            const uint4 a = *reinterpret_cast<const uint4*>(p.in + 8 * i);
+            const uint32_t w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-        for (int k = 0; k < 4; k++) minmax_accum<T>(x[k], lo, hi);
+            for (int k = 0; k < 4; k++) {
+                minmax_accum<T>(T((int)(w[k] & 0xFFFFu)), lo, hi);
+                minmax_accum<T>(T((int)(w[k] >> 16)), lo, hi);
+            }
+        }
+        done = nvec * 8;
+    } else {
+        const uint64_t nvec = p.n / 4;
+        for (uint64_t i = (uint64_t)blockIdx.x * kBlock + threadIdx.x; i < nvec; i += stride) {
+            T x[4];
+            Vec4<T>::load_cached(p.in + 4 * i, x);
+#pragma unroll
+            for (int k = 0; k < 4; k++) minmax_accum<T>(x[k], lo, hi);
+        }
+        done = nvec * 4;
     }
-    if (blockIdx.x == 0 && threadIdx.x < (p.n & 3)) minmax_accum<T>(p.in[nvec * 4 + threadIdx.x], lo, hi);
+    if (blockIdx.x == 0 && threadIdx.x < p.n - done) minmax_accum<T>(p.in[done + threadIdx.x], lo, hi);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const U a = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
