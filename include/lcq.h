@@ -475,17 +475,19 @@ lcq_status lcq_autotune_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header
  * library's callback), so it takes no workspace argument.
  *   - Arguments, outputs and results are those of lcq_quantize.
  *   - The scan workspace is a fixed 1 MiB device array inside the library,
- *     held by every GPU that loads the library until the process exits.  It
- *     limits n to lcq_noalloc_max_values() values (about 5.2e8 at the time of
- *     writing); larger n returns LCQ_ERR_WORKSPACE and enqueues nothing.
+ *     held by every GPU that loads the library until the process exits.
+ *     lcq_noalloc_max_values() is the largest n whose workspace fits it
+ *     (with the current layout every n below 2^40 fits); larger n returns
+ *     LCQ_ERR_WORKSPACE and enqueues nothing.
  *   - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  *     routine.  The first call on each device looks up the device address of
  *     that array (cudaGetSymbolAddress) with the device current; make that
  *     first call before any stream capture.
  *   - Every call on a device shares the one array: calls that can overlap on
  *     the GPU (other streams, other host threads) race and must not be made;
- *     serialise them on one stream.  Each call clears the scan counters it
- *     needs at zero before launching.
+ *     serialise them on one stream.  Each call clears the scan counters and
+ *     the group counts it needs at zero before launching, so a call that was
+ *     cut short leaves nothing behind for the next one.
  */
 uint64_t lcq_noalloc_max_values(void);
 lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, double eb,

@@ -2000,11 +2000,14 @@ lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, doub
     const lcq_status st = noalloc_scratch(&ws);
     if (st != LCQ_OK) return st;
     // Start from a clean scan state even if an earlier call on this device
-    // was cut short: zero the ticket, the finished-CTA counter and the error
-    // bits (the epoch counter must keep counting, so it is left alone).
+    // was cut short: zero the ticket, the finished-CTA counters, the error
+    // bits and the group counts (the epoch counter must keep counting, so it
+    // is left alone).
     WsHead* head = reinterpret_cast<WsHead*>(ws);
     if (cudaMemsetAsync(&head->ticket, 0, 2 * sizeof(uint32_t), stream) != cudaSuccess ||
-        cudaMemsetAsync(&head->err, 0, sizeof(uint32_t), stream) != cudaSuccess)
+        cudaMemsetAsync(&head->err, 0, sizeof(uint32_t), stream) != cudaSuccess ||
+        cudaMemsetAsync(&head->cdone, 0, sizeof(uint32_t), stream) != cudaSuccess ||
+        cudaMemsetAsync(ws_groups(ws), 0, kGroupBytes, stream) != cudaSuccess)
         return LCQ_ERR_CUDA;
     return lcq_quantize(dtype, bound_type, eb, d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
                         d_hdr, ws, kNoAllocWsBytes, stream);
