@@ -379,7 +379,10 @@ lcq_status lcq_autotune_batched(const lcq_batch_info* h_info, const void* d_plan
  * stages).  The error guarantee is untouched: prediction works on the exact
  * integer bins produced and verified by lcq_quantize, and reconstruction
  * gives back exactly those bins.
- *   Grid: N^3 int32 bins, index (i*N + j)*N + k, 1 <= N <= 2048.  Anchors
+ *   Grid: N^3 int32 bins, index (i*N + j)*N + k, 1 <= N <= 2048, every bin
+ *   in (-2^30, 2^30) as lcq_quantize produces them (the kernels add pairs of
+ *   bins in int32; other values give unspecified residuals, never a fault;
+ *   reconstruction of residuals from lcq_pred_residuals stays in range).  Anchors
  *   (coordinates multiples of 8) are kept; a point of stride s = 4, 2, 1
  *   (level 1, 2, 3: multiples of s, not all multiples of 2s) is predicted from
  *   bins of coarser levels: interpolation over the 2^c coarse corners along

@@ -83,18 +83,22 @@ __device__ __forceinline__ int axis_off(int c, int x, int stride) { return (c - 
 // Interpolation base of point (i, j, k) (not an anchor); p = &b[i][j][k].
 __device__ __forceinline__ int32_t interp(const int32_t* p, int N, int i, int j, int k, const Point& pt) {
     const int s = pt.s, last = ((N - 1) >> pt.sh) << pt.sh, NN = N * N;  // 2 s = 1 << sh
-    const int i0 = (pt.cls & 1) ? axis_off(clampc(i - s, last), i, NN) : 0;
-    const int i1 = (pt.cls & 1) ? axis_off(clampc(i + s, last), i, NN) : 0;
-    const int j0 = (pt.cls & 2) ? axis_off(clampc(j - s, last), j, N) : 0;
-    const int j1 = (pt.cls & 2) ? axis_off(clampc(j + s, last), j, N) : 0;
-    const int k0 = (pt.cls & 4) ? clampc(k - s, last) - k : 0;
-    const int k1 = (pt.cls & 4) ? clampc(k + s, last) - k : 0;
+    // ends x - d and x + d with d = s on an odd axis and d = 0 on an even one
+    // (an even coordinate is a multiple of 2s, so it is at most last)
+    const int di = (pt.cls & 1) ? s : 0, dj = (pt.cls & 2) ? s : 0, dk = (pt.cls & 4) ? s : 0;
+    const int i0 = axis_off(clampc(i - di, last), i, NN), i1 = axis_off(clampc(i + di, last), i, NN);
+    const int j0 = axis_off(clampc(j - dj, last), j, N), j1 = axis_off(clampc(j + dj, last), j, N);
+    const int k0 = clampc(k - dk, last) - k, k1 = clampc(k + dk, last) - k;
     // all 8 end combinations: along an even axis both ends are the point's own
     // coordinate, so each of the 2^c distinct corners (c odd axes) is added
-    // 2^(3 - c) times and the mean (sum + 2^(c-1)) >> c is (acc + 4) >> 3
+    // 2^(3 - c) times and the mean (sum + 2^(c-1)) >> c is (acc + 4) >> 3.
+    // Bins lie in (-2^30, 2^30), so the two k ends add up in int32.
     long long acc = 0;
 #pragma unroll
-    for (int q = 0; q < 8; q++) acc += p[((q & 1) ? i1 : i0) + ((q & 2) ? j1 : j0) + ((q & 4) ? k1 : k0)];
+    for (int q = 0; q < 4; q++) {
+        const int32_t* r = p + ((q & 1) ? i1 : i0) + ((q & 2) ? j1 : j0);
+        acc += (long long)(r[k0] + r[k1]);
+    }
     return (int32_t)((acc + 4) >> 3);
 }
 
