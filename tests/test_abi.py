@@ -102,3 +102,22 @@ def test_host_side_argument_errors_need_no_gpu(lib):
     assert lib.lcq_finite_range(0, None, 0, None, p, 4000, None) == 1
     assert lib.lcq_finite_range(0, None, 0, ctypes.c_void_p(p.value + 4), p, 4000, None) == 1
     assert lib.lcq_workspace_size(0, 0, 1 << 31) > lib.lcq_workspace_size(0, 0, 1 << 20)
+
+
+def test_workspace_size_and_allocation_free_limit(lib):
+    """The single-array workspace is the head (256 B), the range partials
+    (1184 blocks x 16 B), the group counts of 64 scan tiles at a fixed place
+    (8 KB: every chunk of up to 2^31 values has at most 2^17 tiles of 16384
+    values), and one uint32 count per 16384-value tile of the largest chunk,
+    each region rounded up to 256 B.  Every n below 2^40 fits the 1 MiB
+    scratch of the allocation-free entry point."""
+    def up256(b):
+        return (b + 255) // 256 * 256
+
+    for n in (0, 1, 16384, 16385, 1 << 20, 134217728, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, 1 << 36):
+        tiles = (min(n, 1 << 31) + 16383) // 16384
+        want = 256 + 1184 * 16 + 8192 + up256(4 * tiles)
+        for dtype in (0, 1, 2, 3):
+            for bound in (0, 1, 2):
+                assert lib.lcq_workspace_size(dtype, bound, n) == want
+    assert lib.lcq_noalloc_max_values() == (1 << 40) - 1
