@@ -56,19 +56,16 @@ def measured_peaks():
 
 
 def ncu_traffic(name):
-    """DRAM bytes per launch recorded by an ncu capture, from the summary in
-    profiles/<name>.md (line 'traffic_bytes_per_launch: B kernel_src_sha: S');
-    None if absent or if the kernel sources changed since the capture."""
-    path = os.path.join(ROOT, "profiles", name + ".md")
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from one ncu capture, as recorded in profiles/traffic.json together with
+    the hash of the kernel sources it was taken on; None if absent or if the
+    kernel sources changed since the capture."""
     try:
-        for line in open(path):
-            if line.startswith("traffic_bytes_per_launch:"):
-                parts = line.split()
-                b, sha = float(parts[1]), parts[3]
-                return b if sha == kernel_sha() else None
-    except (OSError, IndexError, ValueError):
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[name]
+        return float(rec["bytes_per_launch"]) if rec["kernel_src_sha"] == kernel_sha() else None
+    except (OSError, KeyError, TypeError, ValueError):
         return None
-    return None
 
 
 class ClockSampler:
@@ -151,42 +148,70 @@ def max_over_ranks(v, world, device):
 
 # ------------------------------------------------------------ oracle arm --
 
-def oracle_sweep_seconds(xh, passes=None):
-    """Time the CPU oracle (single thread, as it stands) over the sweep."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sweep_seconds(xh, threads=1):
+    """Time the CPU oracle, as it stands, over the 12-pass sweep of xh:
+    quantize_with on one thread, or quantize_parallel (contiguous chunks on
+    `threads` host threads; the C code releases the GIL)."""
     import oracle as O
     t0 = time.perf_counter()
     for bound in BOUNDS:
         for eb in EBS:
             c = O.consts(bound, xh.dtype, eb, x=xh)
-            O.quantize_with(c, xh)
+            if threads == 1:
+                O.quantize_with(c, xh)
+            else:
+                O.quantize_parallel(c, xh, threads=threads)
     return time.perf_counter() - t0
 
 
-def cpu_sample(n):
+def field_prefix(n, local):
+    """The first n values of the benchmark's float32 512^3 field (seed 0):
+    generated on the GPU exactly as the timed arm generates it when one is
+    visible (then copied to the host), else on the host (same recipe, other
+    random draws)."""
     import synth
-    x = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device="cpu") \
-        if n >= np.prod(SHAPE) else synth.smooth_field((n,), dtype=torch.float32, seed=0)
-    return x.numpy()[:n]
+    if torch.cuda.is_available():
+        dev = torch.device("cuda", local)
+        x = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device=dev)
+        xh = x[:n].cpu().numpy()
+        del x
+        torch.cuda.empty_cache()
+        return xh, "the GPU-generated field"
+    x = synth.smooth_field(SHAPE, dtype=torch.float32, seed=0, device="cpu")
+    return x[:n].numpy().copy(), "the field generated on the host (no GPU visible)"
 
 
-def run_reference(args, world, rank):
+REF_SAMPLE = 1 << 24
+
+
+def run_reference(args, world, rank, local):
     if rank != 0:
         return
-    n = 1 << 21
-    xh = cpu_sample(n)
+    cores = host_cores()
+    xh, where = field_prefix(REF_SAMPLE, local)
     for _ in range(args.warmup):
-        oracle_sweep_seconds(xh)
+        oracle_sweep_seconds(xh, cores)
     t = 0.0
     for _ in range(args.steps):
-        t += oracle_sweep_seconds(xh)
+        t += oracle_sweep_seconds(xh, cores)
     gbs = args.steps * len(BOUNDS) * len(EBS) * xh.nbytes / t / 1e9
-    sample = ("2^21 values of a 1-D float32 sinusoid field, the 12-pass sweep, per step; "
-              "oracle single-threaded")
+    sample = ("first 2^24 values (32 of 512 planes) of %s, float32 512^3 sinusoid field; each step the "
+              "12-pass sweep {ABS,REL,NOA} x eb {1e-2,1e-3,1e-4,1e-5} of that sample; oracle over %d host "
+              "threads (contiguous chunks)" % (where, cores))
+    cfg = step_config(world)
+    cfg["timed_sample"] = sample
     line = {"impl": "reference", "metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic", "config": step_config(world),
-            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -451,7 +476,7 @@ def run_ours(args, world, rank, local):
     extra = {}
     pred_res = None
 
-    def time_calls(xx, bound, eb, reps=5):
+    def time_calls(xx, bound, eb, reps=10):
         qq = P.alloc_outputs(xx.numel(), xx.dtype, dev)
         ww = P.new_workspace(xx.numel(), dev)
         P.quantize_into(xx, bound, eb, qq, ww, stream)
@@ -470,15 +495,36 @@ def run_ours(args, world, rank, local):
                 "outliers": int(h.outlier_count)}
 
     if args.extras:
+        # the 1-D sine configuration with planted specials and bin-edge values
+        # (2^20 float32, ABS 1e-3): 4 MiB, about 1.3 us of HBM time, so the
+        # call is bound by launch latency and has no roofline target
+        xc = synth.sine_1d(1 << 20, seed=0, eb=1e-3, device=dev)
+        extra["sine_1d_2^20_abs_1e-3"] = time_calls(xc, "abs", 1e-3, reps=50)
+        extra["sine_1d_2^20_abs_1e-3"]["note"] = ("launch-bound (4 MiB in, ~1.3 us of HBM time); "
+                                                  "mean of 50 back-to-back calls; no roofline target")
+        del xc
         extra["ablations"] = run_ablations(P, x, q, ws, dev, stream)
         extra["lossless"] = run_lossless(P, x, q, ws, dev, stream)
+        # float64: two roofs, HBM bandwidth and the FP64 multiply rate (probe)
+        fp64_rate = P.lcq.fp64_mul_rate(dev)
+        extra["fp64_mul_rate_G_per_s"] = fp64_rate / 1e9
         x64 = synth.smooth_field((256, 256, 256), dtype=torch.float64, seed=0, device=dev)
         q64 = P.alloc_outputs(x64.numel(), x64.dtype, dev)
         w64 = P.new_workspace(x64.numel(), dev)
         for bound in BOUNDS:
             P.lcq.autotune_quantize(x64, bound, 1e-3, q64, w64, reps=3, stream=stream)
-            extra["f64_256_%s_1e-3" % bound] = time_calls(x64, bound, 1e-3)
-            extra["f64_256_%s_1e-3" % bound]["variant"] = P.lcq.get_variant(0, P.F64, bound)
+            for eb in EBS:
+                r = time_calls(x64, bound, eb)
+                r["variant"] = P.lcq.get_variant(0, P.F64, bound)
+                # FP64 operations per value on the common path: the bin's
+                # multiplication (ABS, NOA); REL also log2approx's addition
+                ops = 2 if bound == "rel" else 1
+                r["fp64_ops_per_value"] = ops
+                r["fp64_G_per_s"] = ops * x64.numel() / (r["ms"] / 1e3) / 1e9
+                r["fp64_frac"] = r["fp64_G_per_s"] * 1e9 / fp64_rate
+                r["hbm_frac"] = r["hbm_GBps"] / hbm_peak
+                r["nearer_roof"] = "fp64" if r["fp64_frac"] > r["hbm_frac"] else "hbm"
+                extra["f64_256_%s_%g" % (bound, eb)] = r
         del q64, w64
         del x64
         # the float32 512^3 field rounded to binary16 / bfloat16
@@ -565,13 +611,25 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if rank == 0 and args.cpu_baseline:
-        nb = 1 << 27
-        xs = x.reshape(-1)[:nb].cpu().numpy()
-        tc = oracle_sweep_seconds(xs)
-        cpu = {"value": len(BOUNDS) * len(EBS) * xs.nbytes / tc / 1e9, "unit": "GB/s", "cores": 1,
+        # the oracle on this machine's host cores, median of 3 runs each: over all
+        # cores on the first 2^27 values (half) of the same field, and on one
+        # thread on the first 2^25 values
+        cores = host_cores()
+        xs = x.reshape(-1)[:1 << 27].cpu().numpy()
+        t_all = float(np.median([oracle_sweep_seconds(xs, cores) for _ in range(3)]))
+        x1 = xs[:1 << 25]
+        t_one = float(np.median([oracle_sweep_seconds(x1, 1) for _ in range(3)]))
+        cpu = {"value": len(BOUNDS) * len(EBS) * xs.nbytes / t_all / 1e9, "unit": "GB/s", "cores": cores,
                "kind": "oracle",
-               "sample": "first 2^27 values (half) of the same 512^3 field, the full 12-pass "
-                         "sweep, oracle single-threaded (%.1f s)" % tc}
+               "sample": "first 2^27 values (half) of the same 512^3 field, the full 12-pass sweep, oracle "
+                         "over %d host threads in contiguous chunks, median of 3 runs (%.2f s each)" % (
+                             cores, t_all),
+               "nproc": os.cpu_count(),
+               "single_thread": {"value": len(BOUNDS) * len(EBS) * x1.nbytes / t_one / 1e9, "unit": "GB/s",
+                                 "cores": 1,
+                                 "sample": "first 2^25 values of the same field, the 12-pass sweep, oracle "
+                                           "single-threaded, median of 3 runs (%.2f s each)" % t_one}}
+        del xs, x1
 
     if rank == 0:
         line = {
@@ -646,12 +704,34 @@ def run_batched(P, synth, dev, stream, args):
     outl = 0
     for _, _, _, q in items[:: max(1, len(items) // 256)]:
         outl += q.read_header().outlier_count
+    # a seeded sample of the full batch against single-array calls, bit for
+    # bit: header, bins, mask words and outlier payload
+    rng = np.random.default_rng(12345)
+    pick = sorted(int(i) for i in rng.choice(len(items), 48, replace=False))
+    mism = []
+    sws = P.new_workspace(max(it[0].numel() for it in items), dev)
+    for i in pick:
+        xx, bound, eb, qb = items[i]
+        ref = P.quantize_into(xx, bound, eb, P.alloc_outputs(xx.numel(), xx.dtype, dev), sws, stream)
+        torch.cuda.synchronize(dev)
+        cnt = ref.read_header().outlier_count
+        same = (bytes(qb.header.cpu().numpy()) == bytes(ref.header.cpu().numpy()) and
+                torch.equal(qb.bins, ref.bins) and torch.equal(qb.mask, ref.mask) and
+                torch.equal(qb.outliers[:cnt], ref.outliers[:cnt]))
+        if not same:
+            mism.append(i)
+        del ref
+    del sws
     res = {"arrays": info.count, "noa_arrays": info.noa_count, "values": int(info.total_values),
            "bytes_in": int(info.total_bytes_in), "ms": t * 1e3,
            "in_GBps": info.total_bytes_in / t / 1e9,
            "hbm_GBps_lower_bound": (2 * info.total_bytes_in + 4.125 * info.total_values) / t / 1e9,
            "scale_vs_full_workload": scale, "generation_s": t_gen, "variant": P.lcq.get_batch_variant(),
-           "ms_per_variant": [round(m, 3) for m in ms_var], "launches_per_replay": 4}
+           "ms_per_variant": [round(m, 3) for m in ms_var], "launches_per_replay": 4,
+           "checked_vs_single_calls": {"arrays": len(pick), "values": int(sum(items[i][0].numel() for i in pick)),
+                                       "mismatched": mism, "sample": "48 arrays, numpy seed 12345"}}
+    if mism:
+        print("batched: arrays %s differ from their single-array calls" % mism, file=sys.stderr, flush=True)
     del items, batch, g
     torch.cuda.empty_cache()
     return res
@@ -857,7 +937,7 @@ def main():
         return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
-        run_reference(args, world, rank)
+        run_reference(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -481,7 +481,11 @@ lcq_status lcq_autotune_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header
  *     held by every GPU that loads the library until the process exits.
  *     lcq_noalloc_max_values() is the largest n whose workspace fits it
  *     (with the current layout every n below 2^40 fits); larger n returns
- *     LCQ_ERR_WORKSPACE and enqueues nothing.
+ *     LCQ_ERR_WORKSPACE.  Every argument is checked before anything is
+ *     enqueued: a rejected call (LCQ_ERR_ARG, LCQ_ERR_BOUND,
+ *     LCQ_ERR_WORKSPACE) enqueues nothing and leaves the array as it was.
+ *   - The array used is the current device's: `stream` must belong to the
+ *     current device (LCQ_ERR_ARG otherwise).
  *   - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
  *     routine.  The first call on each device looks up the device address of
  *     that array (cudaGetSymbolAddress) with the device current; make that
@@ -497,6 +501,18 @@ lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, doub
                                 const void* d_in, uint64_t n, int32_t* d_bins, uint32_t* d_mask,
                                 void* d_outliers, uint64_t outlier_capacity, lcq_header* d_hdr,
                                 cudaStream_t stream);
+
+/*
+ * Measurement probe (no counterpart in the paper): enqueue a kernel that
+ * issues float64 multiplications as fast as the GPU allows, so that the
+ * float64 quantizers can be reported against their FP64 roof as well as
+ * HBM bandwidth.  ctas_per_sm (1..64) CTAs of 256 threads per SM, each thread
+ * `iters` (1..2^24) rounds of eight independent multiplications; the number
+ * of multiplications is written to *h_mults (host, may be NULL) at once, and
+ * one double to d_sink (device).  Time it with CUDA events on `stream`.
+ */
+lcq_status lcq_probe_fp64_mul(uint32_t ctas_per_sm, uint32_t iters, double* d_sink, uint64_t* h_mults,
+                              cudaStream_t stream);
 
 /*
  * Test hook for the bounded waits inside the quantize kernel (no counterpart

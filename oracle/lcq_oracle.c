@@ -17,7 +17,7 @@
  * floating-point expression below is one IEEE-754 operation in the data type
  * (float for float32 data, double for float64 data).
  *
- * Readings of points the paper leaves open (each is also listed in the design doc):
+ * Readings of points the paper leaves open, numbered R1-R11:
  *  R1  "round to the nearest bin" (Sec. 2.2) = round half to even (rint), and
  *      the range test |q| < maxbin is made on the float q BEFORE converting to
  *      an integer, written so that NaN fails it.  The paper's two-sided integer

@@ -10,6 +10,7 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -41,14 +42,18 @@ def build(force=False, verbose=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
-    objs = []
-    for src in sources():
-        obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
+    objs = [os.path.join(BUILD_DIR, os.path.basename(src) + ".o") for src in sources()]
+
+    def compile_one(src, obj):
         cmd = ["nvcc", *NVCC_FLAGS, "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.run(cmd, check=True)
-        objs.append(obj)
+
+    # one nvcc per translation unit, run side by side
+    with ThreadPoolExecutor(max_workers=max(1, min(len(objs), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(compile_one, s, o) for s, o in zip(sources(), objs)]:
+            f.result()
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp,
                     *objs, "-lcudart"], check=True)

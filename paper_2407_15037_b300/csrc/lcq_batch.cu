@@ -421,6 +421,11 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_batch_quantize(BParams p
                 mbar_arrive(&s_full[j & 1u]);
             }
         }
+        // no bulk copy outstanding at CTA exit (also after an abort)
+        if (tid == 0 &&
+            !drain_stages<STAGES>(s_stage_bar, s_filled,
+                                  [&](uint32_t f) { return s_st_tile[f % STAGES] != kNoTile; }, kMbarLimit))
+            atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
     } else {
         // --------------------------------------------------- scan warp --
         for (uint32_t jj = 0;; jj++) {
@@ -538,27 +543,14 @@ constexpr BVariant kBVariants[] = {
 constexpr int kNumBVariants = sizeof(kBVariants) / sizeof(kBVariants[0]);
 static int g_bvariant = 0;
 
-struct BGridCache {
-    int per_sm[16];
-    bool set[16];
-};
-
 template <int SB, int STAGES, int MINB>
 static cudaError_t launch_batch(const BParams& p, cudaStream_t st) {
-    static BGridCache cache{};
+    static OccupancyCache cache{};
     auto kern = k_batch_quantize<SB, STAGES, MINB>;
     const size_t smem = (size_t)STAGES * SB;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int slot = (dev >= 0 && dev < 16) ? dev : 0;
-    if (!cache.set[slot]) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, kSpecThreads, smem);
-        cache.per_sm[slot] = b > 0 ? b : 1;
-        cache.set[slot] = true;
-    }
-    uint64_t grid = (uint64_t)cache.per_sm[slot] * device_sm_count();
+    uint64_t grid = (uint64_t)cached_blocks_per_sm(cache, dev, kern, kSpecThreads, smem) * device_sm_count();
     if (grid > p.total_tiles) grid = p.total_tiles;
     if (grid == 0) return cudaSuccess;
     kern<<<(unsigned)grid, kSpecThreads, smem, st>>>(p);

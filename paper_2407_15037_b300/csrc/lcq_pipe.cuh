@@ -60,6 +60,25 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// Invariant: no bulk copy is outstanding when a CTA leaves the kernel; a copy
+// still in flight would land in shared memory that the SM may already have
+// handed to another CTA.  Thread 0, the only thread that issues copies into a
+// ring of STAGES stage buffers, calls this on every way out of its loop (also
+// after a timeout or an abort): `filled` stages were issued, the last STAGES
+// of them sit in distinct slots (older ones were consumed before their slot
+// was refilled), and armed(f) says whether stage f was armed (an arrive, with
+// or without a copy).  Waiting on a phase that has already completed returns
+// at once, so consumed stages cost one poll each.  Returns false if a wait
+// gave up (the copy engine never finished; the caller records an error).
+template <int STAGES, typename Armed>
+__device__ __forceinline__ bool drain_stages(uint64_t* bars, uint32_t filled, Armed&& armed, uint32_t limit) {
+    const uint32_t lo = filled > (uint32_t)STAGES ? filled - (uint32_t)STAGES : 0u;
+    bool ok = true;
+    for (uint32_t f = lo; f < filled; f++)
+        if (armed(f) && !mbar_wait(&bars[f % STAGES], (f / STAGES) & 1u, limit)) ok = false;
+    return ok;
+}
+
 // Order this thread's earlier generic-proxy shared-memory accesses before
 // later asynchronous-proxy writes (a buffer is refilled after it was read).
 __device__ __forceinline__ void fence_proxy_async_smem() {

@@ -34,6 +34,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lcq.h"
+#include "lcq_host.h"
 
 namespace lcq {
 namespace pred {
@@ -743,11 +744,10 @@ lcq_status lcq_train_gradients(const int32_t* d_bins, uint32_t N, const uint64_t
     p.s2 = s2;
     p.partial = d_partial;
     const size_t smem = sizeof(float) * ((size_t)kTrainBlock * (2 + 2 * kNhid + kNin) + 2 * kNparam);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_train_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    static lcq::OccupancyCache opt_in{};  // the shared-memory opt-in, once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    lcq::cached_blocks_per_sm(opt_in, dev, k_train_partial, kTrainBlock, smem);
     if (num_items) k_train_partial<<<num_items, kTrainBlock, smem, stream>>>(p);
     if (cudaPeekAtLastError() != cudaSuccess) return LCQ_ERR_CUDA;
     k_train_reduce<<<kNets, 256, 0, stream>>>(d_partial, d_item_begin, d_grad, d_loss);

@@ -225,6 +225,12 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                 mbar_arrive(&s_full[J & 1u]);
             }
         }
+        // no bulk copy outstanding at CTA exit (also after an abort)
+        if (tid == 0 &&
+            !drain_stages<STAGES>(s_stage_bar, s_filled,
+                                  [&](uint32_t f) { return s_stage_ticket[f % STAGES] < p.num_tiles; },
+                                  kMbarLimit))
+            atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
     } else {
         // --------------------------------------------------- scan warp --
         const uint64_t nwords = (p.n + 31) / 32;
@@ -801,6 +807,12 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_dequantize(DParams<T> p)
                 mbar_arrive(&s_full[J & 1u]);
             }
         }
+        // no bulk copy outstanding at CTA exit (also after an abort)
+        if (tid == 0 &&
+            !drain_stages<STAGES>(s_stage_bar, s_filled,
+                                  [&](uint32_t f) { return s_stage_ticket[f % STAGES] < p.num_tiles; },
+                                  kMbarLimit))
+            atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
         if (overrun) atomicOr(&p.ws->err, LCQ_STATUS_HEADER);
     } else if (s_ok) {
         // --------------------------------------------------- scan warp --
@@ -925,31 +937,30 @@ static uint32_t* ws_counts(void* ws) {
 
 // Persistent grid: as many CTAs as fit on the device at once (cached per
 // kernel instantiation and device), never more than there are tiles.
-struct GridCache {
-    int blocks_per_sm[16];
-    bool set[16];
-};
+static std::atomic<int> g_sms[kMaxDevices];
+
+std::mutex& launch_setup_mutex() {
+    static std::mutex mu;
+    return mu;
+}
 
 static int device_sms(int dev) {
-    static int sms[16] = {0};
-    if (dev < 0 || dev >= 16) return 148;
-    if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-    return sms[dev] ? sms[dev] : 148;
+    if (dev < 0 || dev >= kMaxDevices) return 148;
+    int v = g_sms[dev].load(std::memory_order_acquire);
+    if (!v) {
+        int q = 0;
+        if (cudaDeviceGetAttribute(&q, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || q <= 0) return 148;
+        g_sms[dev].store(q, std::memory_order_release);  // every thread stores the same value
+        v = q;
+    }
+    return v;
 }
 
 template <typename K>
-static int persistent_blocks(K kernel, size_t dyn_smem, int threads, GridCache& cache) {
+static int persistent_blocks(K kernel, size_t dyn_smem, int threads, OccupancyCache& cache) {
     int dev = 0;
     cudaGetDevice(&dev);
-    const int slot = (dev >= 0 && dev < 16) ? dev : 0;
-    if (!cache.set[slot]) {
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem);
-        int b = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, dyn_smem);
-        cache.blocks_per_sm[slot] = b > 0 ? b : 1;
-        cache.set[slot] = true;
-    }
-    return cache.blocks_per_sm[slot] * device_sms(dev);
+    return cached_blocks_per_sm(cache, dev, kernel, threads, dyn_smem) * device_sms(dev);
 }
 
 // Launch with programmatic stream serialisation (the kernel starts with
@@ -974,7 +985,7 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), unsigned grid, unsigned bl
 
 template <typename T, int MODE, int VPT, int STAGES, int SUB, int MINB>
 static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
-    static GridCache cache{};
+    static OccupancyCache cache{};
     constexpr int STILE = kComputeThreads * 4 * VPT;
     const size_t smem = (size_t)STAGES * STILE * sizeof(T);
     auto kern = k_quantize<T, MODE, VPT, STAGES, SUB, MINB>;
@@ -987,7 +998,7 @@ static cudaError_t launch_quantize(const QParams<T>& p, cudaStream_t st) {
 
 template <typename T, int VPT, int STAGES, int SUB, int MINB>
 static cudaError_t launch_dequantize(const DParams<T>& p, cudaStream_t st) {
-    static GridCache cache{};
+    static OccupancyCache cache{};
     constexpr int STILE = kComputeThreads * 4 * VPT;
     const size_t smem = (size_t)STAGES * (STILE + STILE / 32) * 4;
     auto kern = k_dequantize<T, VPT, STAGES, SUB, MINB>;
@@ -1995,9 +2006,21 @@ lcq_status lcq_quantize_noalloc(lcq_dtype dtype, lcq_bound_type bound_type, doub
                                 const void* d_in, uint64_t n, int32_t* d_bins, uint32_t* d_mask,
                                 void* d_outliers, uint64_t outlier_capacity, lcq_header* d_hdr,
                                 cudaStream_t stream) {
+    // The size limit, then every check lcq_quantize makes, before anything
+    // is enqueued on the shared scratch: a rejected call leaves it untouched.
     if (n > lcq_noalloc_max_values()) return LCQ_ERR_WORKSPACE;
+    lcq_status st = check_quantize_args(dtype, bound_type, eb, d_in, n, d_bins, d_mask, d_outliers,
+                                        outlier_capacity, d_hdr);
+    if (st != LCQ_OK) return st;
+    uint64_t bits[4];
+    if (bound_type != LCQ_NOA && !host_consts(dtype, bound_type, eb, bits)) return LCQ_ERR_BOUND;
+    // The scratch is the current device's; the stream must belong to it.
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cudaStreamGetDevice(stream, &sdev) != cudaSuccess)
+        return LCQ_ERR_CUDA;
+    if (sdev != cur) return LCQ_ERR_ARG;
     void* ws = nullptr;
-    const lcq_status st = noalloc_scratch(&ws);
+    st = noalloc_scratch(&ws);
     if (st != LCQ_OK) return st;
     // Start from a clean scan state even if an earlier call on this device
     // was cut short: zero the ticket, the finished-CTA counters, the error

@@ -285,8 +285,8 @@ __device__ __forceinline__ void for_each_outlier(const uint32_t* s_words, const 
 // lanes): the raw bits of the tile's outliers (tcount of them, tcount > 0) to
 // out[pbase + rank], ranks in index order, writes stopping at cap.  tin: the
 // tile's first value; tmask: its first mask word, of which words_left are
-// valid (the rest count as 0).  The warp reads the mask in parts of 512
-// words, 16 per lane, and a warp scan of the lanes' bit counts gives each
+// valid (the rest count as 0).  The warp reads the mask in parts of up to
+// 512 words, up to 16 per lane, and a warp scan of the lanes' bit counts gives each
 // lane its first rank.  In a sparse tile each lane walks its own words in
 // index order and issues the loads of up to eight outliers (across words)
 // before their stores, so that the latencies overlap.  In a dense tile (more
@@ -298,8 +298,9 @@ __device__ __forceinline__ void compact_tile(const T* tin, const uint32_t* tmask
                                              uint32_t tcount, uint64_t pbase, typename Ty<T>::U* out,
                                              uint64_t cap) {
     using U = typename Ty<T>::U;
-    constexpr int TILE = WORDS * 32, PART = 512, WPL = PART / 32;  // 16 words per lane and part
-    static_assert(WORDS % PART == 0, "whole parts");
+    // parts of up to 512 words: 16 (or, for smaller tiles, 4 or 8) words per lane
+    constexpr int TILE = WORDS * 32, PART = WORDS < 512 ? WORDS : 512, WPL = PART / 32;
+    static_assert(WORDS % PART == 0 && WPL % 4 == 0, "whole parts of whole uint4 loads per lane");
     const int lane = threadIdx.x & 31;
     const uint32_t below = (1u << lane) - 1u;
     const bool dense = tcount > (uint32_t)(TILE / 8);

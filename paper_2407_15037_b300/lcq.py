@@ -123,6 +123,7 @@ SIGNATURES = {
     "lcq_batch_tune_set": ([ctypes.c_int], ctypes.c_int),
     "lcq_batch_tune_get": ([], ctypes.c_int),
     "lcq_autotune_batched": ([_vp, _vp, _vp, _sz, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "lcq_probe_fp64_mul": ([ctypes.c_uint32, ctypes.c_uint32, _vp, ctypes.POINTER(_u64), _vp], ctypes.c_int),
     "lcq_noalloc_max_values": ([], _u64),
     "lcq_quantize_noalloc": ([ctypes.c_int, ctypes.c_int, _dbl, _vp, _u64, _vp, _vp, _vp, _u64, _vp,
                               _vp], ctypes.c_int),
@@ -245,12 +246,14 @@ def quantize(x, bound, eb, outlier_capacity=None, ws=None, stream=None):
 
 def quantize_noalloc_into(x, bound, eb, q, stream=None):
     """Enqueue lcq_quantize_noalloc (no workspace argument; the library's
-    built-in scratch is used).  Calls on one device must not overlap."""
+    built-in scratch of x's device is used, so the call runs with that device
+    current).  Calls on one device must not overlap."""
     _require_cuda(x)
-    code = lib().lcq_quantize_noalloc(
-        _dtype_code(x), _bound_code(bound), float(eb), _ptr(x), x.numel(), _ptr(q.bins),
-        _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header),
-        _stream_ptr(stream, x.device))
+    with torch.cuda.device(x.device):
+        code = lib().lcq_quantize_noalloc(
+            _dtype_code(x), _bound_code(bound), float(eb), _ptr(x), x.numel(), _ptr(q.bins),
+            _ptr(q.mask), _ptr(q.outliers), q.outliers.numel(), _ptr(q.header),
+            _stream_ptr(stream, x.device))
     _check(code, "lcq_quantize_noalloc")
     return q
 
@@ -454,6 +457,27 @@ def set_batch_variant(v):
 
 def get_batch_variant():
     return int(lib().lcq_batch_tune_get())
+
+
+def fp64_mul_rate(device, ctas_per_sm=8, iters=1 << 14, reps=5):
+    """Float64 multiplications per second of this GPU, measured by
+    lcq_probe_fp64_mul with CUDA events (best of `reps` launches)."""
+    sink = torch.empty(1, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    cnt = _u64(0)
+    _check(lib().lcq_probe_fp64_mul(ctas_per_sm, iters, _ptr(sink), ctypes.byref(cnt), _vp(stream.cuda_stream)),
+           "lcq_probe_fp64_mul")
+    best = None
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _check(lib().lcq_probe_fp64_mul(ctas_per_sm, iters, _ptr(sink), None, _vp(stream.cuda_stream)),
+               "lcq_probe_fp64_mul")
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return cnt.value / (best / 1e3)
 
 
 def debug_set_scan(spin_limit=0, drop_tile=(1 << 64) - 1):
