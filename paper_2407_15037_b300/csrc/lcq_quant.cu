@@ -379,18 +379,100 @@ __device__ __forceinline__ uint32_t cta_sum(uint32_t v, uint32_t* s_red) {
     return t;
 }
 
+// Dense tiles (at least 1/16 outliers, whole) stream through a stage of
+// shared memory per warp, kCompactChunk values and their 32 mask words at a
+// time, by bulk asynchronous copies (the CTA's other warps keep the memory
+// busy meanwhile); the warp then writes each word's outliers with one
+// coalesced store.  The bytes of one stage.
+constexpr int kCompactChunk = 1024;
+template <typename T>
+__host__ __device__ constexpr size_t compact_stage_bytes() {
+    return (size_t)kCompactChunk * sizeof(T) + kCompactChunk / 8;
+}
+constexpr int kCompactStages = 1;
+
 template <typename T, int WORDS>
 __global__ void __launch_bounds__(kCompactThreads, sizeof(T) == 8 ? 3 : 4) k_compact(CParams<T> p) {
+    using F = Ty<T>;
     pdl_wait();
     pdl_trigger();
     constexpr int TILE = WORDS * 32;
+    constexpr size_t SB = compact_stage_bytes<T>();
+    static_assert(TILE % kCompactChunk == 0 && SB % 16 == 0, "whole chunks, 16-byte stages");
+    extern __shared__ __align__(128) unsigned char dsmem[];
     __shared__ uint32_t s_red[kCompactWarps];
     __shared__ uint32_t s_wsum[kCompactWarps];
     __shared__ uint32_t s_cnt[kCompactThreads];
     __shared__ uint64_t s_off[kCompactThreads];
+    __shared__ __align__(8) uint64_t s_cbar[kCompactWarps][kCompactStages];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t nwords = (p.n + 31) / 32;
+    if (tid == 0) {
+        for (int w = 0; w < kCompactWarps; w++)
+            for (int s = 0; s < kCompactStages; s++) mbar_init(&s_cbar[w][s], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // this warp's stages; issued / used count its copies (uniform in the warp)
+    unsigned char* wbuf = dsmem + (size_t)warp * kCompactStages * SB;
+    uint64_t* wbar = s_cbar[warp];
+    uint32_t issued = 0, used = 0;
+    bool failed = false;
+    auto cissue = [&](const T* tin, const uint32_t* tmask, int c) {
+        if (lane == 0) {
+            uint64_t* bar = &wbar[issued % kCompactStages];
+            unsigned char* dst = wbuf + (issued % kCompactStages) * SB;
+            mbar_arrive_expect_tx(bar, (uint32_t)SB);
+            bulk_g2s(dst, tin + (size_t)c * kCompactChunk, kCompactChunk * sizeof(T), bar);
+            bulk_g2s(dst + kCompactChunk * sizeof(T), tmask + (size_t)c * (kCompactChunk / 32), kCompactChunk / 8, bar);
+        }
+        issued++;
+    };
+    // One dense whole tile: its outliers to out[pbase + rank], rank in index order.
+    auto compact_dense = [&](const T* tin, const uint32_t* tmask, uint64_t pbase) {
+        constexpr int NCH = TILE / kCompactChunk;
+        // one chunk in flight per stage: a stage's barrier takes one arrival per phase
+#pragma unroll
+        for (int c0 = 0; c0 < kCompactStages && c0 < NCH; c0++) cissue(tin, tmask, c0);
+        uint64_t run = pbase;
+        for (int c = 0; c < NCH; c++) {
+            const uint32_t u = used;
+            const bool arrived = mbar_wait(&wbar[u % kCompactStages], (u / kCompactStages) & 1u, kMbarLimit);
+            if (!__all_sync(0xFFFFFFFFu, arrived)) {  // uniform in the warp
+                failed = true;
+                return;
+            }
+            used = u + 1;
+            const unsigned char* src = wbuf + (u % kCompactStages) * SB;
+            const T* vals = reinterpret_cast<const T*>(src);
+            const uint32_t w = reinterpret_cast<const uint32_t*>(src + kCompactChunk * sizeof(T))[lane];
+            const uint32_t cnt = (uint32_t)__popc(w);
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t ex = incl - cnt, below = (1u << lane) - 1u;
+            // word by word, lane i the word's value i: the outliers of a word
+            // go to consecutive payload entries, one coalesced store
+#pragma unroll 8
+            for (int j = 0; j < 32; j++) {
+                const uint32_t m = __shfl_sync(0xFFFFFFFFu, w, j);
+                const uint32_t pre = __shfl_sync(0xFFFFFFFFu, ex, j);
+                if ((m >> lane) & 1u) {
+                    const uint64_t r = run + pre + (uint32_t)__popc(m & below);
+                    if (r < p.cap) p.out[r] = F::bits(vals[j * 32 + lane]);
+                }
+            }
+            run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            fence_proxy_async_smem();  // the stage is read; it may be refilled
+            __syncwarp();
+            if (c + kCompactStages < NCH) cissue(tin, tmask, c + kCompactStages);
+        }
+    };
+
     // outliers of the earlier chunks (the header's count, written by the
     // last CTA of the previous chunk's compaction)
     const uint64_t carry = p.first_chunk ? 0ull : p.hdr->outlier_count;
@@ -429,11 +511,21 @@ __global__ void __launch_bounds__(kCompactThreads, sizeof(T) == 8 ? 3 : 4) k_com
             const uint64_t pbase = s_off[i];
             if (tcount == 0u || pbase >= p.cap) continue;  // the same in every lane
             const uint64_t t = b + i;
-            compact_tile<T, WORDS>(p.in + t * TILE, p.mask + t * WORDS, nwords - t * WORDS, tcount, pbase, p.out,
-                                   p.cap);
+            if (!failed && (t + 1) * TILE <= p.n && tcount >= (uint32_t)(TILE / 16))
+                compact_dense(p.in + t * TILE, p.mask + t * WORDS, pbase);
+            else
+                compact_tile<T, WORDS>(p.in + t * TILE, p.mask + t * WORDS, nwords - t * WORDS, tcount, pbase,
+                                       p.out, p.cap);
         }
         base += pass;
         __syncthreads();  // s_wsum, s_cnt and s_off are rewritten by the next pass
+    }
+    // no bulk copy outstanding at CTA exit; a stage that never arrived is a
+    // timeout of the call
+    if (lane == 0) {
+        for (uint32_t u = used; u < issued; u++)
+            if (!mbar_wait(&wbar[u % kCompactStages], (u / kCompactStages) & 1u, kMbarLimit)) failed = true;
+        if (failed) atomicOr(&p.hdr->status, LCQ_STATUS_TIMEOUT);
     }
     if (tid == 0) {
         __threadfence();
@@ -1072,6 +1164,15 @@ static cudaError_t launch_ablation(const QParams<T>& p, cudaStream_t st) {
     return launch_quantize<T, MODE, v.vpt, v.stages, v.sub, v.minb>(p, st);
 }
 
+template <typename T, int WORDS>
+static cudaError_t launch_compact_words(uint32_t grid, size_t smem, const CParams<T>& p, cudaStream_t st) {
+    static OccupancyCache cache{};  // the shared-memory opt-in, once per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cached_blocks_per_sm(cache, dev, k_compact<T, WORDS>, kCompactThreads, smem);
+    return launch_pdl(k_compact<T, WORDS>, grid, kCompactThreads, smem, st, p);
+}
+
 // The compaction kernel for scan tiles of `words` mask words (every tile
 // shape has 512 or 1024): runs of about kCompactWarps tiles per CTA, at most
 // 8 CTAs per SM.
@@ -1084,8 +1185,9 @@ static cudaError_t launch_compact(int words, CParams<T> p, cudaStream_t st) {
     if (grid < 1) grid = 1;
     p.per = (p.tiles + grid - 1) / grid;
     grid = (p.tiles + p.per - 1) / p.per;
-    if (words == 1024) return launch_pdl(k_compact<T, 1024>, grid, kCompactThreads, 0, st, p);
-    if (words == 512) return launch_pdl(k_compact<T, 512>, grid, kCompactThreads, 0, st, p);
+    const size_t smem = (size_t)kCompactWarps * kCompactStages * compact_stage_bytes<T>();
+    if (words == 1024) return launch_compact_words<T, 1024>(grid, smem, p, st);
+    if (words == 512) return launch_compact_words<T, 512>(grid, smem, p, st);
     return cudaErrorInvalidValue;
 }
 
