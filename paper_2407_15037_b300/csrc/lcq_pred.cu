@@ -27,6 +27,7 @@
 //     residual, straight-through gradients; per-CTA partial gradients are
 //     summed in a fixed order (deterministic), then Adam.
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 
@@ -341,16 +342,8 @@ __device__ __forceinline__ int32_t stencil_row(const int32_t* p, int N, int i, i
 // level when reconstructing), the threads along k, so that every load and
 // store of a warp is one coalesced row segment.
 //
-// With the network, residuals and reconstruction walk the grid by point
-// groups instead: the anchors, then for each level (stride s = 4, 2, 1) and
-// class the sub-lattice of its points (on an odd axis of the class the
-// coordinates s, 3s, 5s, ..., on an even axis 0, 2s, 4s, ...; together they
-// partition the grid).  A warp takes 32 consecutive points of one lattice
-// row, so its lanes share the class and the network: the weights are read
-// from shared memory as broadcasts.  A persistent grid of a few CTAs per SM
-// loads the network parameters once per CTA.  (For interpolation alone this
-// order is slower: the strided rows of the sub-lattices waste half of every
-// line they touch.)
+// With the network, residuals and reconstruction walk each level by boxes
+// of coarse cells staged in shared memory (k_net_boxes below).
 
 __global__ void __launch_bounds__(256) k_interp_residuals(const int32_t* __restrict__ bins, int N,
                                                           int32_t* __restrict__ res) {
@@ -385,87 +378,165 @@ __global__ void __launch_bounds__(256) k_interp_reconstruct(const int32_t* __res
     }
 }
 
-constexpr int kMaxGroups = 22;  // anchors + 3 levels x 7 classes
+// ------------------------------------------------ boxes of coarse cells --
+//
+// The network kernels walk each level (stride s, coarse spacing 2s) by boxes
+// of coarse cells: cell (ci, cj, ck) is the 2s-cube whose lowest corner is
+// the coarse point 2s (ci, cj, ck); it holds the level's point of class
+// (a, b, c) at 2s (ci, cj, ck) + s (a, b, c), and that point's stencil is the
+// coarse points of cells ci-1..ci+1 (and likewise along j, k), each index
+// clamped to [0, L], L = last / 2s.  A CTA copies a box's coarse points,
+// clamped, with a halo of one cell on every side, into shared memory once
+// (BI x BJ x BK cells: (BI+2)(BJ+2)(BK+2) values); then each warp takes the
+// 32 cells of one box row along k for one class, so that every stencil input
+// is a shared-memory load at a fixed offset from the lane's cell and the 32
+// lanes share the class and the network.  Persistent CTAs load the network
+// parameters once.
+constexpr int kBI = 2, kBJ = 4, kBK = 32;
+constexpr int kHI = kBI + 2, kHJ = kBJ + 2, kHK = kBK + 2;
+constexpr int kHalo = kHI * kHJ * kHK;
 
-struct Group {
-    int s, cls, level, step;  // anchors: s = 8, cls = level = 0, step 8; else step 2s
-    int o[3];                 // first coordinate on each axis (s or 0)
-    int n[3];                 // positions on each axis
-    int kchunks;              // ceil(n[2] / 32)
-    uint32_t first_job;       // jobs (lattice rows) of the groups before this one
+struct BoxLevel {
+    int s, sh, L;          // stride, log2(2s), largest coarse index
+    int nb[3];             // boxes along i, j, k
+    uint32_t first_box;    // boxes of the levels before this one in the launch
 };
 
-struct GroupTable {
-    Group g[kMaxGroups];
+struct BoxTable {
+    BoxLevel lv[3];
     int count;
-    uint32_t total_jobs;
+    uint32_t total;
 };
 
-// The groups of `level` (0: anchors only, 1..3: that level's classes, -1:
-// everything), jobs counted from 0.
-static GroupTable group_table(int N, int level) {
-    GroupTable t{};
-    uint32_t jobs = 0;
-    auto add = [&](int s, int cls, int lv, int step) {
-        Group& G = t.g[t.count++];
-        G.s = s; G.cls = cls; G.level = lv; G.step = step;
-        for (int a = 0; a < 3; a++) {
-            G.o[a] = ((cls >> a) & 1) ? s : 0;
-            G.n[a] = G.o[a] < N ? (N - 1 - G.o[a]) / step + 1 : 0;
-        }
-        G.kchunks = (G.n[2] + 31) / 32;
-        G.first_job = jobs;
-        jobs += G.n[2] > 0 ? (uint32_t)G.n[0] * (uint32_t)G.n[1] : 0u;
-    };
-    if (level <= 0) add(8, 0, 0, 8);
-    for (int lv = 1; lv <= 3; lv++)
-        if (level < 0 || level == lv)
-            for (int c = 1; c <= 7; c++) add(8 >> lv, c, lv, 16 >> lv);
-    t.total_jobs = jobs;
+// The levels of one launch: level > 0 that level only, -1 levels 1..3.
+static BoxTable box_table(int N, int level) {
+    BoxTable t{};
+    uint32_t boxes = 0;
+    for (int l = 1; l <= 3; l++) {
+        if (level > 0 && level != l) continue;
+        BoxLevel& B = t.lv[t.count++];
+        B.s = 8 >> l;
+        B.sh = 4 - l;  // log2(2s)
+        const int last = ((N - 1) >> B.sh) << B.sh;
+        B.L = last >> B.sh;
+        const int cells = B.L + 1;
+        B.nb[0] = (cells + kBI - 1) / kBI;
+        B.nb[1] = (cells + kBJ - 1) / kBJ;
+        B.nb[2] = (cells + kBK - 1) / kBK;
+        B.first_box = boxes;
+        boxes += (uint32_t)B.nb[0] * B.nb[1] * B.nb[2];
+    }
+    t.total = boxes;
     return t;
 }
 
-// RECON = false: res = bins - prediction (anchors: res = bins).
-// RECON = true: bins = prediction + res for the groups of one level, whose
-// predictions read only coarser levels, already reconstructed.
-template <bool RECON>
-__global__ void __launch_bounds__(256) k_net_groups(const int32_t* __restrict__ in, int N,
-                                                    const lcq_pred_params* params, int32_t* out,
-                                                    const GroupTable gt) {
-    __shared__ MmaParams mp;
-    __shared__ __align__(16) uint32_t s_a[8][32 * kArow];  // per-warp staging tiles
-    load_mma_params(mp, params);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* arow = &s_a[warp][0];
-    const uint32_t wstride = gridDim.x * (blockDim.x / 32);
-    int g = 0;  // jobs only grow, so the group search resumes where it stopped
-    for (uint32_t job = blockIdx.x * (blockDim.x / 32) + (uint32_t)warp; job < gt.total_jobs; job += wstride) {
-        while (g + 1 < gt.count && job >= gt.g[g + 1].first_job) g++;  // the same in every lane
-        const Group& G = gt.g[g];
-        const uint32_t r = job - G.first_job;  // one lattice row (ii, jj)
-        const int jj = (int)(r % (uint32_t)G.n[1]), ii = (int)(r / (uint32_t)G.n[1]);
-        for (int kc = 0; kc < G.kchunks; kc++) {
-        const int kk = kc * 32 + lane;
-        const bool valid = kk < G.n[2];
-        const int i = G.o[0] + ii * G.step, j = G.o[1] + jj * G.step, k = G.o[2] + (valid ? kk : 0) * G.step;
-        const size_t e = ((size_t)i * N + j) * N + k;
-        if (G.level == 0) {  // anchors (uniform in the warp)
-            if (valid) out[e] = in[e];
-            continue;
+// The base and the 27 stencil inputs of a point from its coarse bins c[t],
+// t = 9 di + 3 dj + dk (d = 0, 1, 2 for the cells before, at and after the
+// point's own), written to the lane's row of the warp's staging tile as in
+// stencil_row; returns the interpolation base.
+__device__ __forceinline__ int32_t stencil_inputs(const int32_t c[kNin], int cls, int s_in, uint32_t* row) {
+    const bool odd_i = cls & 1, odd_j = cls & 2, odd_k = cls & 4;
+    long long rj[2];
+#pragma unroll
+    for (int a = 0; a < 2; a++) {
+        long long rk[2];
+#pragma unroll
+        for (int b = 0; b < 2; b++) {
+            const int32_t v1 = c[(a + 1) * 9 + (b + 1) * 3 + 1], v2 = c[(a + 1) * 9 + (b + 1) * 3 + 2];
+            rk[b] = (long long)(v1 + (odd_k ? v2 : v1));
         }
+        rj[a] = rk[0] + (odd_j ? rk[1] : rk[0]);
+    }
+    const long long acc = rj[0] + (odd_i ? rj[1] : rj[0]);
+    const int32_t base = (int32_t)((acc + 4) >> 3);
+    int dv[32];
+#pragma unroll
+    for (int t = 0; t < 32; t++) {
+        if (t < kNin) {
+            const int32_t d = (c[t] - base) >> s_in;  // |c|, |base| < 2^30: no overflow
+            dv[t] = d < -128 ? -128 : (d > 127 ? 127 : d);
+        } else {
+            dv[t] = 0;
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < 16; w += 4)
+        *reinterpret_cast<uint4*>(row + w) = make_uint4(input_pair(dv[2 * w], dv[2 * w + 1]),
+                                                        input_pair(dv[2 * w + 2], dv[2 * w + 3]),
+                                                        input_pair(dv[2 * w + 4], dv[2 * w + 5]),
+                                                        input_pair(dv[2 * w + 6], dv[2 * w + 7]));
+    return base;
+}
 
-        Point pt;
-        pt.level = G.level; pt.s = G.s; pt.cls = G.cls; pt.sh = __ffs(G.s);
-        const int32_t* bins = RECON ? out : in;
-        const int32_t* pp = bins + e;
-        // k is a valid point of the group in every lane
-        const int32_t base = stencil_row(pp, N, i, j, k, pt, mp.s_in[pt.level - 1], arow + lane * kArow);
-        const int net = (pt.level - 1) * 7 + (pt.cls - 1);
-        const int32_t pr = (int32_t)((uint32_t)base + (uint32_t)network_mma(mp, net, arow));
-        __syncwarp();  // the staging tile is rewritten by the next chunk
-        if (valid) out[e] = RECON ? (int32_t)((uint32_t)pr + (uint32_t)in[e]) : (int32_t)((uint32_t)in[e] - (uint32_t)pr);
+// RECON = false: res = bins - prediction for the levels of the table.
+// RECON = true: bins = prediction + res for one level, whose predictions
+// read only coarser levels, already reconstructed (anchors by k_anchors).
+// Warp w of the CTA takes jobs w, w + 8, ...: job = (class - 1) * 8 + box row.
+struct NetSmem {
+    MmaParams mp;
+    alignas(16) uint32_t a[8][32 * kArow];  // per-warp staging tiles (16-byte rows: vector stores, ldmatrix)
+    int32_t halo[kHalo];
+};
+static_assert(offsetof(NetSmem, a) % 16 == 0 && (kArow * 4) % 16 == 0, "16-byte aligned staging rows");
+
+template <bool RECON>
+__global__ void __launch_bounds__(256) k_net_boxes(const int32_t* __restrict__ in, int N,
+                                                   const lcq_pred_params* params, int32_t* out, const BoxTable bt) {
+    extern __shared__ __align__(16) unsigned char net_smem[];
+    NetSmem& S = *reinterpret_cast<NetSmem*>(net_smem);
+    load_mma_params(S.mp, params);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* arow = &S.a[warp][0];
+    const int32_t* src = RECON ? out : in;  // where the coarse bins are read
+    const size_t NN = (size_t)N * N;
+    int l = 0;  // boxes only grow, so the level search resumes where it stopped
+    for (uint32_t box = blockIdx.x; box < bt.total; box += gridDim.x) {
+        while (l + 1 < bt.count && box >= bt.lv[l + 1].first_box) l++;
+        const BoxLevel& B = bt.lv[l];
+        const uint32_t r = box - B.first_box;
+        const int bk = (int)(r % (uint32_t)B.nb[2]);
+        const int bj = (int)((r / (uint32_t)B.nb[2]) % (uint32_t)B.nb[1]);
+        const int bi = (int)(r / ((uint32_t)B.nb[2] * (uint32_t)B.nb[1]));
+        const int ci0 = bi * kBI, cj0 = bj * kBJ, ck0 = bk * kBK;
+        __syncthreads();  // the previous box's halo is no longer read (and the parameters are loaded)
+        for (int x = threadIdx.x; x < kHalo; x += blockDim.x) {
+            const int hk = x % kHK, hj = (x / kHK) % kHJ, hi = x / (kHK * kHJ);
+            const int ci = clampc(ci0 - 1 + hi, B.L), cj = clampc(cj0 - 1 + hj, B.L), ck = clampc(ck0 - 1 + hk, B.L);
+            S.halo[x] = src[((size_t)(ci << B.sh) * N + (size_t)(cj << B.sh)) * N + (size_t)(ck << B.sh)];
         }
+        __syncthreads();
+        const int s = B.s, net0 = (3 - B.sh) * 7;  // level - 1 = 3 - sh
+        const int s_in = S.mp.s_in[3 - B.sh];
+        for (int job = warp; job < 7 * kBI * kBJ; job += 8) {
+            const int cls = job / (kBI * kBJ) + 1, row = job % (kBI * kBJ);
+            const int ri = row / kBJ, rj = row % kBJ;
+            const int i = ((ci0 + ri) << B.sh) + ((cls & 1) ? s : 0);
+            const int j = ((cj0 + rj) << B.sh) + ((cls & 2) ? s : 0);
+            const int k = ((ck0 + lane) << B.sh) + ((cls & 4) ? s : 0);
+            const bool valid = i < N && j < N && k < N;
+            const int32_t* h = &S.halo[((ri + 1) * kHJ + (rj + 1)) * kHK + lane + 1];
+            int32_t c[kNin];
+#pragma unroll
+            for (int t = 0; t < kNin; t++) c[t] = h[(t / 9 - 1) * kHJ * kHK + ((t / 3) % 3 - 1) * kHK + (t % 3 - 1)];
+            const int32_t base = stencil_inputs(c, cls, s_in, arow + lane * kArow);
+            const int32_t pr = (int32_t)((uint32_t)base + (uint32_t)network_mma(S.mp, net0 + cls - 1, arow));
+            __syncwarp();  // the staging tile is rewritten by the next job
+            if (valid) {
+                const size_t e = (size_t)i * NN + (size_t)j * N + (size_t)k;
+                out[e] = RECON ? (int32_t)((uint32_t)pr + (uint32_t)in[e]) : (int32_t)((uint32_t)in[e] - (uint32_t)pr);
+            }
+        }
+    }
+}
+
+// Anchors (all coordinates multiples of 8) are kept as they are.
+__global__ void __launch_bounds__(256) k_anchors(const int32_t* __restrict__ in, int N, int32_t* __restrict__ out) {
+    const int m = (N + 7) / 8;
+    const uint32_t total = (uint32_t)m * m * m;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < total; x += gridDim.x * blockDim.x) {
+        const int k = (int)(x % m) * 8, j = (int)((x / m) % m) * 8, i = (int)(x / ((uint32_t)m * m)) * 8;
+        const size_t e = ((size_t)i * N + j) * N + k;
+        out[e] = in[e];
     }
 }
 
@@ -655,18 +726,22 @@ __global__ void k_freeze(const float* shadow, lcq_pred_params* out) {
 
 static bool n_ok(int N) { return N >= 1 && N <= 2048; }
 
-// Persistent grid for `jobs` warp jobs (lattice rows): the CTAs (8 warps)
-// that fit on the device at once, at most one per 8 jobs.
-template <typename K>
-static unsigned jobs_grid(K kernel, uint32_t jobs) {
-    int dev = 0, sms = 148, per_sm = 1;
+// Launch of k_net_boxes: a persistent grid of the CTAs that fit on the
+// device at once, at most one per box, with the shared-memory opt-in made
+// once per device.
+template <bool RECON>
+static cudaError_t launch_net_boxes(const int32_t* in, int N, const lcq_pred_params* params, int32_t* out,
+                                    const BoxTable& bt, cudaStream_t stream) {
+    static lcq::OccupancyCache cache{};
+    int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, 0);
-    uint64_t g = (uint64_t)(per_sm > 0 ? per_sm : 1) * (uint64_t)(sms > 0 ? sms : 148);
-    const uint64_t need = ((uint64_t)jobs + 7) / 8;
-    if (g > need) g = need;
-    return (unsigned)(g < 1 ? 1 : g);
+    const int per_sm = lcq::cached_blocks_per_sm(cache, dev, k_net_boxes<RECON>, 256, sizeof(NetSmem));
+    uint64_t g = (uint64_t)per_sm * (uint64_t)(sms > 0 ? sms : 148);
+    if (g > bt.total) g = bt.total;
+    if (g < 1) g = 1;
+    k_net_boxes<RECON><<<(unsigned)g, 256, sizeof(NetSmem), stream>>>(in, N, params, out, bt);
+    return cudaPeekAtLastError();
 }
 
 }  // namespace pred
@@ -680,9 +755,10 @@ lcq_status lcq_pred_residuals(const int32_t* d_bins, uint32_t N, const lcq_pred_
                               cudaStream_t stream) {
     if (!n_ok((int)N) || !d_bins || !d_res) return LCQ_ERR_ARG;
     if (d_params) {
-        const GroupTable gt = group_table((int)N, -1);
-        k_net_groups<false><<<jobs_grid(k_net_groups<false>, gt.total_jobs), 256, 0, stream>>>(d_bins, (int)N,
-                                                                                            d_params, d_res, gt);
+        const BoxTable bt = box_table((int)N, -1);
+        const uint32_t m = (N + 7) / 8;
+        k_anchors<<<(m * m * m + 255) / 256, 256, 0, stream>>>(d_bins, (int)N, d_res);
+        if (launch_net_boxes<false>(d_bins, (int)N, d_params, d_res, bt, stream) != cudaSuccess) return LCQ_ERR_CUDA;
     } else {
         const dim3 grid((N + 255) / 256, N, N);
         k_interp_residuals<<<grid, 256, 0, stream>>>(d_bins, (int)N, d_res);
@@ -694,10 +770,12 @@ lcq_status lcq_pred_reconstruct(const int32_t* d_res, uint32_t N, const lcq_pred
                                 cudaStream_t stream) {
     if (!n_ok((int)N) || !d_bins || !d_res) return LCQ_ERR_ARG;
     for (int level = 0; level <= 3; level++) {
-        if (d_params) {
-            const GroupTable gt = group_table((int)N, level);
-            k_net_groups<true><<<jobs_grid(k_net_groups<true>, gt.total_jobs), 256, 0, stream>>>(d_res, (int)N,
-                                                                                              d_params, d_bins, gt);
+        if (d_params && level == 0) {
+            const uint32_t m = (N + 7) / 8;
+            k_anchors<<<(m * m * m + 255) / 256, 256, 0, stream>>>(d_res, (int)N, d_bins);
+        } else if (d_params) {
+            const BoxTable bt = box_table((int)N, level);
+            if (launch_net_boxes<true>(d_res, (int)N, d_params, d_bins, bt, stream) != cudaSuccess) return LCQ_ERR_CUDA;
         } else {
             const int s = 8 >> level;
             const unsigned m = (N + s - 1) / s;

@@ -39,8 +39,10 @@ def _random_params(rng, s_in=(2, 1, 0)):
                      rng.integers(-128, 128, (3, 7, 16)), rng.integers(-5000, 5000, (3, 7)), s_in, 8, 6)
 
 
-@pytest.mark.parametrize("N", [9, 16, 33, 64])
+@pytest.mark.parametrize("N", [9, 16, 33, 64, 100, 130])
 def test_residuals_and_reconstruct_match_oracle(N):
+    """Grids of one to several boxes of coarse cells per axis (32 cells
+    along k, 4 along j, 2 along i), ragged ones included."""
     rng = np.random.default_rng(N)
     bins = rng.integers(-(1 << 30) + 1, 1 << 30, N ** 3).astype(np.int32)
     bins[: N ** 3 // 2] = rng.integers(-3000, 3000, N ** 3 // 2)  # a smooth-ish part and an extreme part
