@@ -16,9 +16,9 @@
 //     x_t = clamp((bin of coarse stencil point t - base) >> s_in, -128, 127)
 //     over the 3x3x3 coarse points f + 2s (di, dj, dk) around the floor-aligned
 //     coarse point f; h_u = clamp((W1 x + b1 + 2^(s1-1)) >> s1, 0, 127);
-//     o = (W2 h + b2 + 2^(s2-1)) >> s2; pred = base + o.  The W1 x products
-//     run on the tensor cores (binary16 operands, float32 accumulators,
-//     exact for these integers), the rest in integers.
+//     o = (W2 h + b2 + 2^(s2-1)) >> s2; pred = base + o.  Both products,
+//     W1 x and W2 h, run on the tensor cores (binary16 operands, float32
+//     accumulators, exact for these integers), the rest in integers.
 //   * Residual = bin - pred modulo 2^32; reconstruction adds it back level by
 //     level.
 //   * Training: shadow parameters in float32 (integer units), forward pass =
@@ -138,8 +138,10 @@ __device__ __forceinline__ int32_t interp_point(const int32_t* b, int N, int i, 
 // A warp evaluates the network for 32 points of one (level, class) at once:
 // hidden = W1 x as a [32 points x 32 inputs] x [32 inputs x 16 hidden]
 // product on the tensor cores (mma.sync m16n8k16, binary16 operands, float32
-// accumulators), the rest in integers.  The A operand holds 640 + x_t rather
-// than x_t: for x_t in [-128, 127] that is an integer in [512, 767], where
+// accumulators), then W2 h as a [32 points x 16 hidden] x [16 hidden x 8]
+// product whose column 0 is W2; the shifts and clamps in integers.  The A
+// operand holds 640 + x_t rather than x_t: for x_t in [-128, 127] that is an
+// integer in [512, 767], where
 // binary16 values are spaced 1/2 apart, so its bit pattern is just
 // 0x6100 + 2 x_t (no conversion); the extra 640 sum_t W1[u][t] is taken off
 // with the bias.  This is exact: the weights are integers in [-128, 127] and
@@ -151,8 +153,8 @@ __device__ __forceinline__ int32_t interp_point(const int32_t* b, int N, int i, 
 struct MmaParams {
     uint32_t bfrag[kNets][32][8];  // W1 as B fragments: [net][lane][n-tile * 4 + k-step * 2 + reg]
     uint32_t zk[kNets][kNhid];     // b1 + 2^(s1-1) - 640 sum_t W1[u][t] - bits(1.5 2^23), mod 2^32
-    int32_t w2[kNets][kNhid];
-    int32_t b2[kNets];
+    uint32_t w2frag[kNets][32][2]; // W2 as the B fragment of a 16 x 8 matrix whose column 0 is W2
+    uint32_t b2k[kNets];           // b2 + 2^(s2-1) - 1024 sum_u W2[u] - bits(1.5 2^23), mod 2^32
     int32_t s_in[3];
     int32_t s1, s2;
 };
@@ -187,9 +189,23 @@ __device__ __forceinline__ void load_mma_params(MmaParams& mp, const lcq_pred_pa
         int32_t wsum = 0;
         for (int t = 0; t < kNin; t++) wsum += row[t];
         (&mp.zk[0][0])[x] = (uint32_t)(&gp->b1[0][0][0])[x] + r1 - 0x4B400000u - 640u * (uint32_t)wsum;
-        (&mp.w2[0][0])[x] = (&gp->w2[0][0][0])[x];
     }
-    for (int x = threadIdx.x; x < kNets; x += blockDim.x) mp.b2[x] = (&gp->b2[0][0])[x];
+    // W2 as B fragments (rows k = hidden units, column 0 = W2, the other
+    // columns 0): lane = 4 g + q holds rows 2q, 2q+1 (reg 0) and 2q+8, 2q+9
+    // (reg 1) of column g
+    for (int x = threadIdx.x; x < kNets * 32 * 2; x += blockDim.x) {
+        const int net = x >> 6, lane = (x >> 1) & 31, reg = x & 1;
+        const int g = lane >> 2, k = 2 * (lane & 3) + 8 * reg;
+        const int8_t* w2 = &gp->w2[net / 7][net % 7][0];
+        mp.w2frag[net][lane][reg] = g == 0 ? half_pair(w2[k], w2[k + 1]) : 0u;
+    }
+    const uint32_t r2 = 1u << (gp->s2 - 1);
+    for (int x = threadIdx.x; x < kNets; x += blockDim.x) {
+        const int8_t* w2 = &gp->w2[x / 7][x % 7][0];
+        int32_t wsum = 0;
+        for (int u = 0; u < kNhid; u++) wsum += w2[u];
+        mp.b2k[x] = (uint32_t)(&gp->b2[0][0])[x] + r2 - 1024u * (uint32_t)wsum - 0x4B400000u;
+    }
     if (threadIdx.x < 3) mp.s_in[threadIdx.x] = gp->s_in[threadIdx.x];
     if (threadIdx.x == 0) { mp.s1 = gp->s1; mp.s2 = gp->s2; }
 }
@@ -209,7 +225,9 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t a[4], uint32_t saddr) {
 
 // The network output o of the point of this lane (all 32 lanes take part;
 // the stencil inputs of the lane's point are already in its row of the
-// warp's staging tile `arow`, 32 rows of kArow words).
+// warp's staging tile `arow`, 32 rows of kArow words).  Both layers run on
+// the tensor cores; the first layer's accumulators, turned into the hidden
+// values, are the second layer's A fragments without leaving the registers.
 __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, const uint32_t* arow) {
     const int lane = threadIdx.x & 31;
     __syncwarp();
@@ -224,52 +242,62 @@ __device__ __forceinline__ int32_t network_mma(const MmaParams& mp, int net, con
             const int col = 16 * ks + 8 * (mtx >> 1);  // binary16 column
             ldmatrix_x4(a[mt][ks], base + (uint32_t)(point * kArow * 4 + col * 2));
         }
-    float c[2][2][4];
+    const int q = lane & 3;
+    uint32_t bf[8];
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++)
+    for (int x = 0; x < 8; x++) bf[x] = mp.bfrag[net][lane][x];
+    int32_t zk[2][2];  // hidden unit 8 nt + 2 q + e
+#pragma unroll
+    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+        for (int e = 0; e < 2; e++) zk[nt][e] = (int32_t)mp.zk[net][8 * nt + 2 * q + e];
+    const uint32_t w2b0 = mp.w2frag[net][lane][0], w2b1 = mp.w2frag[net][lane][1];
+    const int s1 = mp.s1;
+    // (z >> s1) <= 127 iff z <= hmax; for s1 >= 24 every int32 z >= 0 passes
+    const int32_t hmax = s1 >= 24 ? INT_MAX : (int32_t)((128u << s1) - 1u);
+    float d[2][4];  // second layer, column 0: the output of each point
+#pragma unroll
+    for (int mt = 0; mt < 2; mt++) {
+        float c[2][4];
 #pragma unroll
         for (int nt = 0; nt < 2; nt++) {
 #pragma unroll
-            for (int v = 0; v < 4; v++) c[mt][nt][v] = 0.0f;
+            for (int v = 0; v < 4; v++) c[nt][v] = 0.0f;
 #pragma unroll
-            for (int ks = 0; ks < 2; ks++)
-                mma_f16(c[mt][nt], a[mt][ks], mp.bfrag[net][lane][nt * 4 + ks * 2],
-                         mp.bfrag[net][lane][nt * 4 + ks * 2 + 1]);
+            for (int ks = 0; ks < 2; ks++) mma_f16(c[nt], a[mt][ks], bf[nt * 4 + ks * 2], bf[nt * 4 + ks * 2 + 1]);
         }
-    // hidden units 8 nt + 2 q + {0, 1} of points 16 mt + 8 hf + g (g = lane / 4, q = lane % 4).
-    // Each accumulator is an integer v = W1 x + 640 sum_t W1[u][t] with
-    // |v| <= 27 * 128 * 767 < 2^22, so RN(v + 1.5 2^23) = 1.5 2^23 + v exactly
-    // and its bit pattern minus that of 1.5 2^23 is v:
-    // z + 2^(s1-1) = bits(v + 1.5 2^23) + zk[u] (mod 2^32).
-    const int q = lane & 3, g = lane >> 2;
-    const int s1 = mp.s1;
-    int32_t o[2][2];
+        // c[nt][2 hf + e]: point 16 mt + 8 hf + lane / 4, hidden unit 8 nt + 2 q + e.
+        // Each accumulator is an integer v = W1 x + 640 sum_t W1[u][t] with
+        // |v| <= 27 * 128 * 767 < 2^22, so RN(v + 1.5 2^23) = 1.5 2^23 + v
+        // exactly and its bit pattern minus that of 1.5 2^23 is v; with zk,
+        // z = W1 x + b1 + 2^(s1-1) (mod 2^32).  h = clamp(z >> s1, 0, 127) =
+        // clamp(z, 0, hmax) >> s1, one add-min-max and one shift.  The
+        // second layer takes 1024 + h, whose binary16 bit pattern is
+        // 0x6400 + h (binary16 values in [1024, 2048) are the integers).
+        uint32_t ha[4];  // A fragment: [nt * 2 + hf]
 #pragma unroll
-    for (int mt = 0; mt < 2; mt++)
+        for (int nt = 0; nt < 2; nt++)
 #pragma unroll
-        for (int hf = 0; hf < 2; hf++) {
-            int32_t acc = 0;
+            for (int hf = 0; hf < 2; hf++) {
+                const int32_t z0 = (int32_t)__float_as_uint(__fadd_rn(c[nt][2 * hf], 12582912.0f));
+                const int32_t z1 = (int32_t)__float_as_uint(__fadd_rn(c[nt][2 * hf + 1], 12582912.0f));
+                const uint32_t h0 = (uint32_t)(__viaddmin_s32_relu(z0, zk[nt][0], hmax) >> s1);
+                const uint32_t h1 = (uint32_t)(__viaddmin_s32_relu(z1, zk[nt][1], hmax) >> s1);
+                ha[nt * 2 + hf] = 0x64006400u + h0 + (h1 << 16);
+            }
 #pragma unroll
-            for (int nt = 0; nt < 2; nt++)
-#pragma unroll
-                for (int e = 0; e < 2; e++) {
-                    const int u = 8 * nt + 2 * q + e;
-                    const uint32_t zb = __float_as_uint(__fadd_rn(c[mt][nt][2 * hf + e], 12582912.0f));
-                    int32_t h = (int32_t)(zb + mp.zk[net][u]) >> s1;
-                    h = h < 0 ? 0 : (h > 127 ? 127 : h);
-                    acc += mp.w2[net][u] * h;
-                }
-            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
-            acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
-            o[mt][hf] = acc;
-        }
-    (void)g;
-    // the point of this lane: m-tile lane / 16, half (lane % 16) / 8, row lane % 8 (held by quad lane % 8)
-    const int src = 4 * (lane & 7);
-    const int32_t v00 = __shfl_sync(0xFFFFFFFFu, o[0][0], src), v01 = __shfl_sync(0xFFFFFFFFu, o[0][1], src);
-    const int32_t v10 = __shfl_sync(0xFFFFFFFFu, o[1][0], src), v11 = __shfl_sync(0xFFFFFFFFu, o[1][1], src);
-    const int32_t mine = (lane < 16) ? ((lane & 8) ? v01 : v00) : ((lane & 8) ? v11 : v10);
-    return (mine + mp.b2[net] + (1 << (mp.s2 - 1))) >> mp.s2;
+        for (int v = 0; v < 4; v++) d[mt][v] = 0.0f;
+        mma_f16(d[mt], ha, w2b0, w2b1);
+    }
+    // Column 0 of the output tile sits in the lanes with q = 0: point 16 mt + r
+    // in lane 4 (r % 8), register 0 (r < 8) or 2.  Its value is the integer
+    // W2 h + 1024 sum_u W2[u], of magnitude below 16 * 128 * 1151 < 2^22, so
+    // exact in float32 in any order of the additions.
+    const int r = lane & 15, holder = 4 * (r & 7);
+    const float v00 = __shfl_sync(0xFFFFFFFFu, d[0][0], holder), v02 = __shfl_sync(0xFFFFFFFFu, d[0][2], holder);
+    const float v10 = __shfl_sync(0xFFFFFFFFu, d[1][0], holder), v12 = __shfl_sync(0xFFFFFFFFu, d[1][2], holder);
+    const float mine = lane < 16 ? (r < 8 ? v00 : v02) : (r < 8 ? v10 : v12);
+    return (int32_t)(__float_as_uint(__fadd_rn(mine, 12582912.0f)) + mp.b2k[net]) >> mp.s2;
 }
 
 // The 27 stencil inputs of the point (as in `stencil`) written to the lane's
@@ -449,12 +477,15 @@ __device__ __forceinline__ int32_t stencil_inputs(const int32_t c[kNin], int cls
     }
     const long long acc = rj[0] + (odd_i ? rj[1] : rj[0]);
     const int32_t base = (int32_t)((acc + 4) >> 3);
+    // clamp before the shift (as in stencil_row): one add-max, one min, one shift
+    const int32_t lo = s_in >= 24 ? INT_MIN : -(128 << s_in);
+    const int32_t hi = s_in >= 24 ? INT_MAX : (128 << s_in) - 1;
     int dv[32];
 #pragma unroll
     for (int t = 0; t < 32; t++) {
         if (t < kNin) {
-            const int32_t d = (c[t] - base) >> s_in;  // |c|, |base| < 2^30: no overflow
-            dv[t] = d < -128 ? -128 : (d > 127 ? 127 : d);
+            const int32_t x = __viaddmax_s32(c[t], -base, lo);  // max(c - base, lo); |c|, |base| < 2^30
+            dv[t] = (x < hi ? x : hi) >> s_in;
         } else {
             dv[t] = 0;
         }
