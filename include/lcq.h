@@ -393,7 +393,10 @@ lcq_status lcq_autotune_batched(const lcq_batch_info* h_info, const void* d_plan
  *     h_u = clamp((W1 x + b1 + 2^(s1-1)) >> s1, 0, 127),
  *     o   = (W2 h + b2 + 2^(s2-1)) >> s2,
  *   one weight set per (level, class of odd axes).  Residual = bin - pred
- *   modulo 2^32 (anchors: the bin).
+ *   modulo 2^32 (anchors: the bin).  Supported parameters (lcq_pred_freeze
+ *   produces them): |b1|, |b2| <= 2^22, 1 <= s1, s2 <= 24, 0 <= s_in <= 30;
+ *   then every sum above fits int32 and the tensor-core products are exact
+ *   (other values give unspecified predictions, never a fault).
  * lcq_pred_residuals   bins -> residuals (d_params NULL: interpolation only).
  * lcq_pred_reconstruct residuals -> bins, level by level (exact inverse).
  * lcq_pred_histogram   counts of residual values in [-2^20, 2^20):

@@ -56,6 +56,34 @@ def test_residuals_and_reconstruct_match_oracle(N):
         assert np.array_equal(back.cpu().numpy(), bins)
 
 
+@pytest.mark.parametrize("s1,s2,s_in", [(1, 1, (0, 0, 0)), (24, 24, (30, 30, 30)), (8, 24, (0, 13, 30)),
+                                         (24, 1, (30, 1, 0))])
+def test_network_extreme_parameters_match_oracle(s1, s2, s_in):
+    """Weights at -128 / 127, biases at +-2^22 and the shifts at the ends of
+    their supported ranges: the sums of both layers stay exact (binary16
+    operands, float32 accumulators) and the clamps (before the shifts) agree
+    with the oracle's int64 arithmetic."""
+    N = 33
+    rng = np.random.default_rng(s1 * 100 + s2)
+    bins = rng.integers(-(1 << 30) + 1, 1 << 30, N ** 3).astype(np.int32)
+    bins[: N ** 3 // 2] = rng.integers(-600, 600, N ** 3 // 2)
+    ext = np.array([-128, 127])
+    W1 = ext[rng.integers(0, 2, (3, 7, 16, 27))]
+    W1[0, 0] = 127                     # one network with every product at its largest
+    W1[0, 1] = -128
+    b1 = np.where(rng.integers(0, 2, (3, 7, 16)) == 1, 1 << 22, -(1 << 22))
+    b1[1] = rng.integers(-(1 << 22), (1 << 22) + 1, (7, 16))
+    W2 = ext[rng.integers(0, 2, (3, 7, 16))]
+    b2 = np.where(rng.integers(0, 2, (3, 7)) == 1, 1 << 22, -(1 << 22))
+    params = PR.Params(W1, b1, W2, b2, s_in, s1, s2)
+    dp = PD.params_to_device(_params_struct(params), DEV)
+    db = torch.from_numpy(bins).to(DEV)
+    res = PD.residuals(db, N, dp)
+    assert np.array_equal(res.cpu().numpy(), PR.residuals(bins, N, params))
+    back = PD.reconstruct(res, N, dp)
+    assert np.array_equal(back.cpu().numpy(), bins)
+
+
 def test_histogram_counts_match():
     N = 40
     rng = np.random.default_rng(7)
