@@ -587,8 +587,9 @@ __device__ __forceinline__ uint32_t abs_quant4_f32(const float x[4], const Const
 //    ways (lo chk >= FLT_MIN, so RN(lo 2^64 chk) = RN(lo chk) 2^64 and
 //    d 2^64 <= t <=> d <= RN(lo chk)), so skipping it changes nothing;
 //  * a warp whose only tiny values are zeros and denormals (a < FLT_MIN, all
-//    outliers) or NaN still takes the straight-line code, which then rejects
-//    a < FLT_MIN explicitly (NaN fails that comparison too);
+//    outliers) or NaN still takes the straight-line code, which rejects them
+//    without a test of their own: RN(lo chk) <= RN(a / 2) < FLT_MIN for
+//    a < FLT_MIN, and d is NaN for a NaN a;
 //  * in a warp without tiny values (every lo = min(a, m) >= T, apart from
 //    the rejected a < FLT_MIN) and with RATIO = false, the special-value and
 //    bb-range tests are implied as well: a zero or denormal a is rejected
@@ -635,26 +636,24 @@ __device__ __forceinline__ uint32_t rel_fast4_f32(const float x[4], const float 
     }
     uint32_t nb = 0;
     if (!RATIO) {
-        if (!__any_sync(0xFFFFFFFFu, tiny)) {
+        // Straight-line code unless a tiny value other than a zero, a
+        // denormal or NaN needs the rescale.  A zero or denormal a (a <
+        // FLT_MIN) is rejected there without a test of its own: lo <= a and
+        // chk <= 1/2 give RN(lo chk) <= FLT_MIN / 2 < FLT_MIN; a NaN a makes
+        // d NaN.
+        bool fast = !__any_sync(0xFFFFFFFFu, tiny);
+        if (!fast) {
+            bool tiny2 = false;
+#pragma unroll
+            for (int k = 0; k < 4; k++) tiny2 |= lo[k] < T && a[k] >= FLT_MIN;
+            fast = !__any_sync(0xFFFFFFFFu, tiny2);
+        }
+        if (fast) {
 #pragma unroll
             for (int k = 0; k < 4; k++) {
                 const float d = fabsf(__fsub_rn(a[k], m[k]));  // exact (Sterbenz) when accepted
                 const float tt = __fmul_rn(lo[k], c.chk);
                 const bool ok = inr[k] && (tt >= FLT_MIN) && (d <= tt);
-                b[k] = ok ? bin[k] : 0;
-                nb |= ok ? 0u : (1u << k);
-            }
-            return nb;
-        }
-        bool tiny2 = false;  // tiny values other than zeros, denormals and NaN
-#pragma unroll
-        for (int k = 0; k < 4; k++) tiny2 |= lo[k] < T && a[k] >= FLT_MIN;
-        if (!__any_sync(0xFFFFFFFFu, tiny2)) {
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const float d = fabsf(__fsub_rn(a[k], m[k]));
-                const float tt = __fmul_rn(lo[k], c.chk);
-                const bool ok = inr[k] && (a[k] >= FLT_MIN) && (tt >= FLT_MIN) && (d <= tt);
                 b[k] = ok ? bin[k] : 0;
                 nb |= ok ? 0u : (1u << k);
             }
