@@ -113,7 +113,13 @@ typedef struct lcq_header {
     uint32_t reserved;
 } lcq_header;
 
-/* Bytes of workspace needed by lcq_quantize / lcq_dequantize for n values. */
+/* Bytes of workspace for lcq_quantize / lcq_dequantize on n values.  For
+ * LCQ_F32 with LCQ_REL this includes room for staging outliers: the quantize
+ * kernel then copies the outliers of each shared-memory stage out as it
+ * streams, and the compaction copies them instead of reading the input a
+ * second time.  Any workspace of at least lcq_workspace_size(dtype,
+ * LCQ_ABS, n) bytes is accepted for every bound type; with less than this
+ * size a float32 REL call simply does not stage (same results). */
 size_t lcq_workspace_size(lcq_dtype dtype, lcq_bound_type bound_type, uint64_t n);
 
 /* Zero-fill a workspace on `stream` (needed once before first use). */

@@ -34,6 +34,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -50,6 +51,8 @@ constexpr uint64_t kChunk = 1ull << 31;         // values per launch at most
 constexpr uint32_t kDefaultSpin = 1u << 20;     // default of the test hook's poll limit
 constexpr uint32_t kMbarLimit = 1u << 22;       // bulk-copy completion polls (seconds)
 constexpr uint32_t kGroupTiles = 64;            // scan tiles per group count of the compaction
+constexpr uint64_t kMaxSub = 8;                 // ring stages per scan tile, at most (staging table)
+constexpr uint64_t kStageNone = ~0ull;          // staging table: a stage left to k_compact's walk
 
 // Tile shapes: 4-value vectors per thread (tile = 256 x 4 x VPT values) and
 // the depth of the shared-memory stage ring.
@@ -85,6 +88,9 @@ struct QParams {
     uint32_t* mask;       // chunk start (chunk offsets are multiples of 32)
     uint32_t* counts;     // outliers per scan tile of this chunk
     uint32_t* groups;     // outliers per kGroupTiles scan tiles (added up; zero on entry)
+    uint64_t* stab;       // float32 REL outlier staging: entry per stage (null: no staging)
+    uint32_t* stg;        // staging area (raw bits), stage_cap values
+    uint64_t scap;        // staging area capacity in values
     lcq_header* hdr;
     WsHead* ws;
     uint64_t n;           // values in this chunk
@@ -118,6 +124,7 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
     constexpr int WORDS = TILE / 32;
     constexpr int WPL = WORDS / 32;
     static_assert(WPL % 4 == 0, "whole uint4 mask stores per lane");
+    static_assert(SUB <= (int)kMaxSub, "staging table: at most kMaxSub stages per scan tile");
     extern __shared__ __align__(128) unsigned char dsmem[];
     T* sbuf = reinterpret_cast<T*>(dsmem);
     __shared__ __align__(8) uint64_t s_stage_bar[STAGES];
@@ -129,9 +136,17 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
     __shared__ uint32_t s_jt[2];
     __shared__ uint32_t s_epoch, s_filled;
     __shared__ volatile uint32_t s_abort;
+    // float32 REL outlier staging: the compute warps hand each consumed stage
+    // to the scan warp (s_cons), which copies its outliers out and refills
+    // the slot itself; s_cons_end = k + 1 marks that the stages end before
+    // stage k (a lagging scan warp must not stop early).
+    constexpr bool STG = MODE == LCQ_REL && std::is_same<T, float>::value;
+    __shared__ __align__(8) uint64_t s_cons[STG ? STAGES : 1];
+    __shared__ volatile uint32_t s_cons_end;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t full_sub = p.n / STILE;
+    const bool stg = STG && p.stab != nullptr;  // uniform over the launch
     pdl_wait();  // the compaction is let in only when this CTA's tiles are done (below)
 
     if (tid == 0) {
@@ -140,33 +155,45 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             mbar_init(&s_full[b], 1);
             mbar_init(&s_done[b], 1);
         }
+        if constexpr (STG) {
+            for (int s = 0; s < STAGES; s++) mbar_init(&s_cons[s], 1);
+        }
         mbar_init_fence();
         s_epoch = ld_relaxed_u32(&p.ws->epoch);
         s_abort = 0;
         s_filled = 0;
+        s_cons_end = 0;
     }
     const Consts<CT<T>> c = p.consts_from_hdr ? consts_from_header<CT<T>>(p.hdr) : p.c;
     __syncthreads();
 
+    // One thread: the next sub-tile of this CTA into the next stage (f:
+    // stages issued so far).  Without staging, thread 0 issues every stage
+    // and a stage past the last tile arms nothing (the compute warps read its
+    // ticket first and stop); with staging, lane 0 of the scan warp issues
+    // every stage and a stage past the last tile completes its barrier
+    // phase, as the compute warps read its ticket after the wait.
+    auto issue = [&](uint32_t& f, bool arm_end) {
+        const int s = (int)(f % STAGES);
+        const uint32_t sub = f % SUB;
+        const uint32_t t = sub == 0 ? atomicAdd(&p.ws->ticket, 1u) : s_stage_ticket[(f - 1) % STAGES];
+        s_stage_ticket[s] = t;
+        f = f + 1;
+        if (t < p.num_tiles) {
+            const uint64_t g = (uint64_t)t * SUB + sub;
+            if (g < full_sub) {
+                mbar_arrive_expect_tx(&s_stage_bar[s], STILE * sizeof(T));
+                bulk_g2s(sbuf + (size_t)s * STILE, p.in + g * STILE, STILE * sizeof(T), &s_stage_bar[s]);
+            } else {
+                mbar_arrive(&s_stage_bar[s]);  // ragged or empty sub-tile: global reads
+            }
+        } else if (arm_end) {
+            mbar_arrive(&s_stage_bar[s]);
+        }
+    };
+
     if (warp < kComputeThreads / 32) {
         // ------------------------------------------------ compute warps --
-        auto issue = [&]() {  // thread 0: the next sub-tile of this CTA into the next stage
-            const uint32_t f = s_filled;
-            const int s = (int)(f % STAGES);
-            const uint32_t sub = f % SUB;
-            const uint32_t t = sub == 0 ? atomicAdd(&p.ws->ticket, 1u) : s_stage_ticket[(f - 1) % STAGES];
-            s_stage_ticket[s] = t;
-            s_filled = f + 1;
-            if (t < p.num_tiles) {
-                const uint64_t g = (uint64_t)t * SUB + sub;
-                if (g < full_sub) {
-                    mbar_arrive_expect_tx(&s_stage_bar[s], STILE * sizeof(T));
-                    bulk_g2s(sbuf + (size_t)s * STILE, p.in + g * STILE, STILE * sizeof(T), &s_stage_bar[s]);
-                } else {
-                    mbar_arrive(&s_stage_bar[s]);  // ragged or empty sub-tile: global reads
-                }
-            }
-        };
         // Wait until the scan warp has taken scan tile jj's mask words, so
         // that its buffer may be reused.  Returns true if the kernel must
         // stop (uniform over the compute warps).
@@ -181,7 +208,11 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             return named_barrier_or(1, kComputeThreads, !ok);
         };
 
-        if (tid == 0) issue();
+        if (tid == 0 && !stg) {
+            uint32_t f = s_filled;
+            issue(f, false);
+            s_filled = f;
+        }
         named_barrier_sync(1, kComputeThreads);
         uint32_t k = 0;
         for (;; k++) {
@@ -189,22 +220,43 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             const uint32_t sub = k % SUB;
             const uint32_t j = k / SUB;
             const int b = (int)(j & 1u);
-            if (tid == 0 && s_filled < k + STAGES) issue();  // ring fill
-            const uint32_t t = s_stage_ticket[s];
-            if (t >= p.num_tiles) break;
-            const uint64_t g = (uint64_t)t * SUB + sub;
-            const bool from_smem = g < full_sub;
+            uint32_t t;
+            bool end = false;  // with staging: no stage k (decided at the consumed barrier)
+            if (!stg) {
+                if (tid == 0 && s_filled < k + STAGES) {  // ring fill
+                    uint32_t f = s_filled;
+                    issue(f, false);
+                    s_filled = f;
+                }
+                t = s_stage_ticket[s];  // written stages ago, before a barrier
+                if (t >= p.num_tiles) break;
+            }
             if (!mbar_wait_or_abort(&s_stage_bar[s], (k / STAGES) & 1u, kMbarLimit, &s_abort)) {
                 if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
             }
-            const T* st = sbuf + (size_t)s * STILE;
-            const uint64_t sbase = g * STILE;
-            quantize_subtile<T, MODE, VPT>(st, p.in + sbase, from_smem, p.n > sbase ? p.n - sbase : 0,
-                                           p.bins + sbase, s_mask[b], (int)sub * SWORDS, c);
+            if (stg) {
+                // written by the scan warp before the stage's barrier phase
+                // completed; a thread whose wait gave up has set the abort
+                // flag, so the stop below is uniform either way
+                t = s_stage_ticket[s];
+                end = t >= p.num_tiles;
+            }
+            if (!end) {
+                const uint64_t g = (uint64_t)t * SUB + sub;
+                const T* st = sbuf + (size_t)s * STILE;
+                const uint64_t sbase = g * STILE;
+                quantize_subtile<T, MODE, VPT>(st, p.in + sbase, g < full_sub, p.n > sbase ? p.n - sbase : 0,
+                                               p.bins + sbase, s_mask[b], (int)sub * SWORDS, c);
+            }
             fence_proxy_async_smem();
-            bool stop = named_barrier_or(1, kComputeThreads, s_abort != 0);  // stage s consumed
+            bool stop = named_barrier_or(1, kComputeThreads, s_abort != 0 || end);  // stage s consumed
             if (stop) break;
-            if (tid == 0 && s_filled < k + 1 + STAGES) issue();  // refill stage s
+            if (stg && tid == 0) mbar_arrive(&s_cons[s]);  // to the scan warp: outliers, then refill
+            if (!stg && tid == 0 && s_filled < k + 1 + STAGES) {  // refill stage s
+                uint32_t f = s_filled;
+                issue(f, false);
+                s_filled = f;
+            }
             if (sub == SUB - 1) {
                 if (tid == 0) {
                     s_jt[b] = t;
@@ -221,6 +273,15 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
         if (!named_barrier_or(1, kComputeThreads, s_abort != 0)) {
             const uint32_t J = k / SUB;  // scan tiles handled by this CTA
             if (!(J >= 1 && release_tile(J - 1)) && tid == 0) {
+                // With staging: no stage k, the stages end here.  Only now, once
+                // the scan warp has finished tile J - 1 (and so taken in every
+                // stage before k), may slot k % STAGES take this extra arrival:
+                // earlier, its barrier could run two phases ahead of the scan
+                // warp's wait for the slot's previous stage.
+                if (stg) {
+                    s_cons_end = k + 1;
+                    mbar_arrive(&s_cons[k % STAGES]);
+                }
                 s_jt[J & 1u] = kNoTile;
                 mbar_arrive(&s_full[J & 1u]);
             }
@@ -234,8 +295,80 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
     } else {
         // --------------------------------------------------- scan warp --
         const uint64_t nwords = (p.n + 31) / 32;
+        // Staging (float32 REL): this CTA's share of the staging area, and
+        // how much of it is used.  Each consumed stage comes here before its
+        // slot is refilled: its outliers, read from the stage in shared
+        // memory, go to the staging area in index order; the stage's table
+        // entry records where (k_compact then copies them to the payload).
+        // A stage read from global memory (ragged), with more than half of
+        // its values outliers, or that would overflow the CTA's share is left
+        // to k_compact's own walk (entry kStageNone).  Lane 0 issues every
+        // stage: the first STAGES here, each later one into the slot of the
+        // stage just taken out.
+        constexpr int SWPL = SWORDS / 32;  // mask words per lane of a stage
+        const uint64_t region = stg ? p.scap / gridDim.x : 0;
+        const uint64_t sbeg = (uint64_t)blockIdx.x * region;
+        uint64_t sused = 0;
+        uint32_t kk = 0;      // the next stage to take in
+        uint32_t filled = 0;  // stages issued (lane 0)
+        if (stg && lane == 0)
+            while (filled < (uint32_t)STAGES) issue(filled, true);
+        auto stage_out = [&](int sl, uint32_t sub, int b) {
+            const uint64_t g = (uint64_t)s_stage_ticket[sl] * SUB + sub;
+            uint32_t w[SWPL], cnt = 0;
+#pragma unroll
+            for (int i = 0; i < SWPL; i++) {
+                w[i] = s_mask[b][sw((int)sub * SWORDS + lane * SWPL + i)];
+                cnt += __popc(w[i]);
+            }
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            uint64_t entry = 0;
+            if (total != 0u) {
+                if (g >= full_sub || total > (uint32_t)(STILE / 2) || sused + total > region) {
+                    entry = kStageNone;
+                } else {
+                    const uint32_t* stv = reinterpret_cast<const uint32_t*>(sbuf + (size_t)sl * STILE);
+                    uint64_t r = sbeg + sused + (incl - cnt);
+#pragma unroll
+                    for (int i = 0; i < SWPL; i++) {
+                        uint32_t m = w[i];
+                        const uint32_t v0 = (uint32_t)(lane * SWPL + i) * 32u;
+                        while (m) {
+                            p.stg[r++] = stv[v0 + (uint32_t)(__ffs(m) - 1)];
+                            m &= m - 1u;
+                        }
+                    }
+                    entry = ((uint64_t)total << 32) | (sbeg + sused);
+                    sused += total;
+                }
+            }
+            if (lane == 0) p.stab[g] = entry;
+            fence_proxy_async_smem();  // the stage was read; it may be refilled
+            __syncwarp();
+            if (lane == 0) issue(filled, true);  // stage kk + STAGES into slot sl
+        };
         for (uint32_t j = 0;; j++) {
             const int b = (int)(j & 1u);
+            if (stg) {  // the stages of tile j first
+                bool out = false;
+                for (uint32_t sub = 0; sub < (uint32_t)SUB; sub++, kk++) {
+                    const int sl = (int)(kk % STAGES);
+                    if (!mbar_wait_or_abort(&s_cons[sl], (kk / STAGES) & 1u, kMbarLimit, &s_abort)) {
+                        if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
+                        out = true;
+                        break;
+                    }
+                    if (s_cons_end == kk + 1) break;  // no stage kk: the next handover is the end
+                    stage_out(sl, sub, b);
+                }
+                if (out) break;
+            }
             if (!mbar_wait_or_abort(&s_full[b], (j >> 1) & 1u, kMbarLimit, &s_abort)) {
                 if (!s_abort) { atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT); s_abort = 1; }
                 break;
@@ -270,6 +403,12 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
             __syncwarp();
             if (lane == 0 && (uint64_t)t != p.hook.drop_tile) mbar_arrive(&s_done[b]);  // test hook: never handed back
         }
+        // with staging, no bulk copy of this warp's outstanding at CTA exit
+        if (stg && lane == 0 &&
+            !drain_stages<STAGES>(s_stage_bar, filled,
+                                  [&](uint32_t f) { return s_stage_ticket[f % STAGES] < p.num_tiles; },
+                                  kMbarLimit))
+            atomicOr(&p.ws->err, LCQ_STATUS_TIMEOUT);
     }
     pdl_trigger();
     __syncthreads();
@@ -358,6 +497,9 @@ struct CParams {
     uint64_t n;                // values in this chunk
     const uint32_t* counts;    // outliers per scan tile
     uint32_t* groups;          // outliers per kGroupTiles scan tiles
+    const uint64_t* stab;      // staged outliers per ring stage (null: none staged)
+    const uint32_t* stg;       // the staging area
+    uint32_t sub;              // ring stages per scan tile
     uint32_t tiles, per;       // scan tiles of the chunk; consecutive tiles per CTA
     typename Ty<T>::U* out;    // payload
     uint64_t cap;              // payload capacity
@@ -511,6 +653,35 @@ __global__ void __launch_bounds__(kCompactThreads, sizeof(T) == 8 ? 3 : 4) k_com
             const uint64_t pbase = s_off[i];
             if (tcount == 0u || pbase >= p.cap) continue;  // the same in every lane
             const uint64_t t = b + i;
+            if constexpr (sizeof(T) == 4 && !is16<T>()) {
+                // every stage of the tile staged by k_quantize: copy the runs
+                if (p.stab) {
+                    const uint64_t e = lane < (int)p.sub ? p.stab[t * p.sub + lane] : 0ull;
+                    if (!__any_sync(0xFFFFFFFFu, e == kStageNone)) {
+                        uint64_t run = pbase;
+                        for (uint32_t q = 0; q < p.sub; q++) {
+                            const uint64_t eq = __shfl_sync(0xFFFFFFFFu, e, (int)q);
+                            const uint32_t cnt = (uint32_t)(eq >> 32);
+                            const uint32_t* src = p.stg + (uint32_t)eq;
+                            for (uint32_t x0 = 0; x0 < cnt; x0 += 128u) {
+                                uint32_t v[4];
+#pragma unroll
+                                for (int u = 0; u < 4; u++) {
+                                    const uint32_t x = x0 + 32u * u + (uint32_t)lane;
+                                    if (x < cnt) v[u] = src[x];
+                                }
+#pragma unroll
+                                for (int u = 0; u < 4; u++) {
+                                    const uint32_t x = x0 + 32u * u + (uint32_t)lane;
+                                    if (x < cnt && run + x < p.cap) p.out[run + x] = v[u];
+                                }
+                            }
+                            run += cnt;
+                        }
+                        continue;
+                    }
+                }
+            }
             if (!failed && (t + 1) * TILE <= p.n && tcount >= (uint32_t)(TILE / 16))
                 compact_dense(p.in + t * TILE, p.mask + t * WORDS, pbase);
             else
@@ -1016,6 +1187,30 @@ static size_t ws_size(uint64_t n) {
     return kWsHeadBytes + kMinmaxPartialBytes + kGroupBytes + up256(tt * 4);
 }
 
+// Outlier staging for float32 REL, in a workspace of lcq_workspace_size(
+// LCQ_F32, LCQ_REL, n) bytes: one uint64 entry per ring stage (outlier
+// count << 32 | first staging index; 0 for a stage without outliers;
+// kStageNone for a stage left to k_compact's own walk), then a staging area
+// for a quarter of a chunk's values, split evenly among the quantize CTAs.
+static uint64_t stage_entries(uint64_t n) {
+    // every stage of every scan tile, empty stages of a ragged last tile
+    // included: at most kMaxSub stages per tile of at least kTileValuesMin values
+    return table_tiles(n) * kMaxSub;
+}
+static uint64_t stage_cap(uint64_t n) {
+    const uint64_t per_chunk = n < kChunk ? n : kChunk;
+    return (per_chunk + 3) / 4;
+}
+static size_t ws_size_staged(uint64_t n) {
+    return ws_size(n) + up256(stage_entries(n) * 8) + up256(stage_cap(n) * 4);
+}
+static uint64_t* ws_stage_table(void* ws, uint64_t n) {
+    return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + ws_size(n));
+}
+static uint32_t* ws_staging(void* ws, uint64_t n) {
+    return reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(ws_stage_table(ws, n)) + up256(stage_entries(n) * 8));
+}
+
 static uint64_t* ws_partials(void* ws) {
     return reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(ws) + kWsHeadBytes);
 }
@@ -1344,7 +1539,7 @@ static bool host_io_download(const HostIO& io, uint64_t i, uint64_t off, uint64_
 template <typename T>
 static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint64_t n, int32_t* bins,
                                 uint32_t* mask, void* outl, uint64_t cap, lcq_header* hdr, void* ws,
-                                cudaStream_t st, const double* given = nullptr, int ablation = 0,
+                                size_t ws_bytes, cudaStream_t st, const double* given = nullptr, int ablation = 0,
                                 const HostIO* io = nullptr) {
     Consts<CT<T>> c{};
     const bool noa = bt == LCQ_NOA;
@@ -1358,6 +1553,9 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
     uint64_t* partial = ws_partials(ws);
     uint32_t* counts = ws_counts(ws);
     uint32_t* groups = ws_groups(ws);
+    // float32 REL stages its outliers when the workspace has room for it
+    const bool staged = std::is_same<T, float>::value && bt == LCQ_REL && ablation == 0 && !io &&
+                        ws_bytes >= ws_size_staged(n);
 
     if (io) {
         // NOA needs the whole input for its range before any binning
@@ -1398,6 +1596,9 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         p.mask = mask + off / 32;
         p.counts = counts;
         p.groups = groups;
+        p.stab = staged ? ws_stage_table(ws, n) : nullptr;
+        p.stg = staged ? ws_staging(ws, n) : nullptr;
+        p.scap = staged ? stage_cap(n) : 0;
         p.hdr = hdr;
         p.ws = head;
         p.n = len;
@@ -1437,6 +1638,9 @@ static lcq_status quantize_impl(lcq_bound_type bt, double eb, const T* in, uint6
         cp.n = len;
         cp.counts = counts;
         cp.groups = groups;
+        cp.stab = p.stab;
+        cp.stg = p.stg;
+        cp.sub = (uint32_t)kVariants[var].sub;
         cp.tiles = tiles;
         cp.per = 0;  // set at launch
         cp.out = reinterpret_cast<typename Ty<T>::U*>(outl);
@@ -1568,9 +1772,7 @@ using namespace lcq;
 extern "C" {
 
 size_t lcq_workspace_size(lcq_dtype dtype, lcq_bound_type bound_type, uint64_t n) {
-    (void)dtype;
-    (void)bound_type;
-    return ws_size(n);
+    return dtype == LCQ_F32 && bound_type == LCQ_REL ? ws_size_staged(n) : ws_size(n);
 }
 
 lcq_status lcq_workspace_init(void* d_ws, size_t ws_bytes, cudaStream_t stream) {
@@ -1594,7 +1796,7 @@ lcq_status lcq_quantize(lcq_dtype dtype, lcq_bound_type bound_type, double eb, c
     return with_dtype(dtype, [&](auto tag) {
         using T = decltype(tag);
         return quantize_impl<T>(bound_type, eb, (const T*)d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
-                                d_hdr, d_ws, stream);
+                                d_hdr, d_ws, ws_bytes, stream);
     });
 }
 
@@ -1629,9 +1831,9 @@ lcq_status lcq_quantize_ablation(lcq_ablation kind, lcq_dtype dtype, double eb, 
     const int mode = kind == LCQ_ABL_REL_LIBRARY ? kModeRelLib : kModeAbsNoCheck;
     if (dtype == LCQ_F32)
         return quantize_impl<float>(bt, eb, (const float*)d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
-                                    d_hdr, d_ws, stream, nullptr, mode);
+                                    d_hdr, d_ws, ws_bytes, stream, nullptr, mode);
     return quantize_impl<double>(bt, eb, (const double*)d_in, n, d_bins, d_mask, d_outliers, outlier_capacity,
-                                 d_hdr, d_ws, stream, nullptr, mode);
+                                 d_hdr, d_ws, ws_bytes, stream, nullptr, mode);
 }
 
 int lcq_ablation_variant(lcq_dtype dtype, lcq_ablation kind) {
@@ -1685,7 +1887,7 @@ lcq_status lcq_quantize_noa_range(lcq_dtype dtype, double eb, int has_finite, do
     return with_dtype(dtype, [&](auto tag) {
         using T = decltype(tag);
         return quantize_impl<T>(LCQ_NOA, eb, (const T*)d_in, n, d_bins, d_mask, d_outliers, outlier_capacity, d_hdr,
-                                d_ws, stream, given);
+                                d_ws, ws_bytes, stream, given);
     });
 }
 
@@ -1766,7 +1968,7 @@ lcq_status enqueue_host_item(lcq_dtype dtype, lcq_bound_type bt, double eb, uint
     void* d_outl = cap ? t.d_out : nullptr;
     const lcq_status s = with_dtype(dtype, [&](auto tag) {
         using T = decltype(tag);
-        return quantize_impl<T>(bt, eb, (const T*)t.d_in, n, t.d_bins, t.d_mask, d_outl, cap, t.d_hdr, d_ws, st,
+        return quantize_impl<T>(bt, eb, (const T*)t.d_in, n, t.d_bins, t.d_mask, d_outl, cap, t.d_hdr, d_ws, 0, st,
                                 nullptr, 0, &io);
     });
     const bool ok = cudaEventRecord(end_ev, st) == cudaSuccess &&

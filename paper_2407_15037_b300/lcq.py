@@ -183,9 +183,12 @@ def workspace_size(dtype_code, bound, n):
     return int(lib().lcq_workspace_size(dtype_code, _bound_code(bound), int(n)))
 
 
-def new_workspace(n, device, dtype_code=F32, bound=ABS):
-    """A zero-filled workspace for arrays of up to n values."""
-    nbytes = max(workspace_size(dtype_code, bound, n), 256)
+def new_workspace(n, device, dtype_code=F32, bound=None):
+    """A zero-filled workspace for arrays of up to n values (bound None:
+    large enough for every bound type of this data type, so that float32
+    REL stages its outliers)."""
+    bounds = (ABS, REL, NOA) if bound is None else (bound,)
+    nbytes = max(max(workspace_size(dtype_code, b, n) for b in bounds), 256)
     return torch.zeros(nbytes, dtype=torch.uint8, device=device)
 
 

@@ -109,15 +109,21 @@ def test_workspace_size_and_allocation_free_limit(lib):
     (1184 blocks x 16 B), the group counts of 64 scan tiles at a fixed place
     (8 KB: every chunk of up to 2^31 values has at most 2^17 tiles of 16384
     values), and one uint32 count per 16384-value tile of the largest chunk,
-    each region rounded up to 256 B.  Every n below 2^40 fits the 1 MiB
-    scratch of the allocation-free entry point."""
+    each region rounded up to 256 B.  Float32 REL adds the outlier staging
+    table (one uint64 per ring stage: at most 8 stages per tile) and a
+    staging area for a quarter of the largest chunk's values.  Every n below
+    2^40 fits the 1 MiB scratch of the allocation-free entry point, which
+    does not stage."""
     def up256(b):
         return (b + 255) // 256 * 256
 
     for n in (0, 1, 16384, 16385, 1 << 20, 134217728, (1 << 31) - 1, 1 << 31, (1 << 31) + 1, 1 << 36):
-        tiles = (min(n, 1 << 31) + 16383) // 16384
+        per_chunk = min(n, 1 << 31)
+        tiles = (per_chunk + 16383) // 16384
         want = 256 + 1184 * 16 + 8192 + up256(4 * tiles)
+        staged = want + up256(8 * 8 * tiles) + up256(4 * ((per_chunk + 3) // 4))
         for dtype in (0, 1, 2, 3):
             for bound in (0, 1, 2):
-                assert lib.lcq_workspace_size(dtype, bound, n) == want
+                got = lib.lcq_workspace_size(dtype, bound, n)
+                assert got == (staged if (dtype, bound) == (0, 1) else want)
     assert lib.lcq_noalloc_max_values() == (1 << 40) - 1
