@@ -333,15 +333,26 @@ __global__ void __launch_bounds__(kSpecThreads, MINB) k_quantize(QParams<T> p) {
                 if (g >= full_sub || total > (uint32_t)(STILE / 2) || sused + total > region) {
                     entry = kStageNone;
                 } else {
-                    const uint32_t* stv = reinterpret_cast<const uint32_t*>(sbuf + (size_t)sl * STILE);
-                    uint64_t r = sbeg + sused + (incl - cnt);
+                    // each word from both ends: its lowest outlier to the next
+                    // slot of its run, its highest to the last free one, so a
+                    // word takes ceil(bits / 2) steps
+                    const uint32_t* sv = reinterpret_cast<const uint32_t*>(sbuf + (size_t)sl * STILE) +
+                                         (size_t)lane * SWPL * 32;
+                    uint32_t* dst = p.stg + (sbeg + sused + (incl - cnt));
 #pragma unroll
                     for (int i = 0; i < SWPL; i++) {
                         uint32_t m = w[i];
-                        const uint32_t v0 = (uint32_t)(lane * SWPL + i) * 32u;
+                        const uint32_t* svi = sv + i * 32;
+                        uint32_t* lo = dst;
+                        uint32_t* hi = dst + __popc(m);  // one past the word's run
+                        dst = hi;
                         while (m) {
-                            p.stg[r++] = stv[v0 + (uint32_t)(__ffs(m) - 1)];
+                            const int bl = __ffs(m) - 1;
+                            const int bh = 31 - __clz(m);
+                            *lo++ = svi[bl];
+                            if (bh != bl) *--hi = svi[bh];
                             m &= m - 1u;
+                            m &= ~(1u << bh);
                         }
                     }
                     entry = ((uint64_t)total << 32) | (sbeg + sused);
@@ -654,29 +665,30 @@ __global__ void __launch_bounds__(kCompactThreads, sizeof(T) == 8 ? 3 : 4) k_com
             if (tcount == 0u || pbase >= p.cap) continue;  // the same in every lane
             const uint64_t t = b + i;
             if constexpr (sizeof(T) == 4 && !is16<T>()) {
-                // every stage of the tile staged by k_quantize: copy the runs
+                // Every stage of the tile staged by k_quantize: its stages are
+                // consecutive stages of one quantize CTA, whose staged runs
+                // follow one another, so the tile's outliers are one run of
+                // tcount values starting at its first non-empty stage's run.
                 if (p.stab) {
                     const uint64_t e = lane < (int)p.sub ? p.stab[t * p.sub + lane] : 0ull;
-                    if (!__any_sync(0xFFFFFFFFu, e == kStageNone)) {
-                        uint64_t run = pbase;
-                        for (uint32_t q = 0; q < p.sub; q++) {
-                            const uint64_t eq = __shfl_sync(0xFFFFFFFFu, e, (int)q);
-                            const uint32_t cnt = (uint32_t)(eq >> 32);
-                            const uint32_t* src = p.stg + (uint32_t)eq;
-                            for (uint32_t x0 = 0; x0 < cnt; x0 += 128u) {
-                                uint32_t v[4];
+                    const uint32_t nz = __ballot_sync(0xFFFFFFFFu, (e >> 32) != 0ull);
+                    if (!__any_sync(0xFFFFFFFFu, e == kStageNone) && nz != 0u) {
+                        const uint64_t e0 = __shfl_sync(0xFFFFFFFFu, e, __ffs(nz) - 1);
+                        const uint32_t* src = p.stg + (uint32_t)e0;
+                        typename Ty<T>::U* dst = p.out + pbase;
+                        const uint32_t len = p.cap - pbase < tcount ? (uint32_t)(p.cap - pbase) : tcount;
+                        for (uint32_t x0 = 0; x0 < len; x0 += 256u) {
+                            uint32_t v[8];
 #pragma unroll
-                                for (int u = 0; u < 4; u++) {
-                                    const uint32_t x = x0 + 32u * u + (uint32_t)lane;
-                                    if (x < cnt) v[u] = src[x];
-                                }
-#pragma unroll
-                                for (int u = 0; u < 4; u++) {
-                                    const uint32_t x = x0 + 32u * u + (uint32_t)lane;
-                                    if (x < cnt && run + x < p.cap) p.out[run + x] = v[u];
-                                }
+                            for (int u = 0; u < 8; u++) {
+                                const uint32_t x = x0 + 32u * u + (uint32_t)lane;
+                                if (x < len) v[u] = __ldcs(src + x);
                             }
-                            run += cnt;
+#pragma unroll
+                            for (int u = 0; u < 8; u++) {
+                                const uint32_t x = x0 + 32u * u + (uint32_t)lane;
+                                if (x < len) dst[x] = v[u];
+                            }
                         }
                         continue;
                     }
