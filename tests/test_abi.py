@@ -127,3 +127,15 @@ def test_workspace_size_and_allocation_free_limit(lib):
                 got = lib.lcq_workspace_size(dtype, bound, n)
                 assert got == (staged if (dtype, bound) == (0, 1) else want)
     assert lib.lcq_noalloc_max_values() == (1 << 40) - 1
+
+
+def test_default_workspace_fits_every_bound(lib):
+    """new_workspace without a bound is sized for every bound type of the
+    data type, so a float32 REL call on it stages its outliers; with a bound
+    it is exactly that bound's size (no device needed: a host tensor)."""
+    n = (1 << 20) + 3
+    for code in (P.lcq.F32, P.lcq.F64, P.lcq.F16, P.lcq.BF16):
+        sizes = [P.workspace_size(code, b, n) for b in ("abs", "rel", "noa")]
+        assert P.new_workspace(n, "cpu", code).numel() == max(sizes)
+        assert P.new_workspace(n, "cpu", code, "abs").numel() == sizes[0]
+    assert P.new_workspace(n, "cpu").numel() == P.workspace_size(P.lcq.F32, "rel", n)
