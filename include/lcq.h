@@ -490,7 +490,9 @@ lcq_status lcq_autotune_dequantize(lcq_dtype dtype, uint64_t n, const lcq_header
  *     held by every GPU that loads the library until the process exits.
  *     lcq_noalloc_max_values() is the largest n whose workspace fits it
  *     (with the current layout every n below 2^40 fits); larger n returns
- *     LCQ_ERR_WORKSPACE.  Every argument is checked before anything is
+ *     LCQ_ERR_WORKSPACE.  The array has no room for float32 REL outlier
+ *     staging, so such a call compacts without it (same results, the
+ *     compaction reads the input again).  Every argument is checked before anything is
  *     enqueued: a rejected call (LCQ_ERR_ARG, LCQ_ERR_BOUND,
  *     LCQ_ERR_WORKSPACE) enqueues nothing and leaves the array as it was.
  *   - The array used is the current device's: `stream` must belong to the
